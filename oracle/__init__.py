@@ -1,0 +1,35 @@
+"""Plain CPU FP64 oracle of the H^2 Hessian construction and matvec.
+
+TEST INFRASTRUCTURE.  This package is the slow, obviously-correct reference
+that the CUDA library is checked against.  Only the tests, the smoke check
+(`__graft_entry__.smoke`) and the benchmark's CPU-baseline leg may import it;
+the library never does, and it shares no code with the library.  It is
+written from the paper (arXiv 2003.10173): Section 3.1 (representation),
+Section 3.2 (matvec, recompression, norms), Section 3.3 (construction from
+Hessian-vector products), with numpy library primitives (QR, SVD, matmul)
+as steps.
+"""
+from .h2 import H2Matrix, assemble, expand_dense, frobenius_norm, matvec, power_norm, storage_entries
+from .heat import DenseOperator, HeatHessian
+from .peel import PeelResult, TreeOperator, apply_pieces, norm2_estimate, peel
+from .tree import ADM_STRONG, ADM_WEAK, ClusterTree, Partition
+
+
+def basis_threshold(tol: float, norm_est: float, n_leaves: int) -> float:
+    """Absolute truncation threshold of the nested bases.
+
+    Reading (the paper fixes only the overall target): the leaf block rows partition
+    the rows, so independent per-row truncation errors add in quadrature in the
+    2-norm; the bases are truncated at 2 tol ||H|| / sqrt(#leaves), which keeps the
+    measured relative 2-norm error near 0.4 tol on the heat Hessians (n = 32..256)."""
+    return 2.0 * tol * norm_est / (n_leaves ** 0.5)
+
+
+def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None):
+    """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result)."""
+    tree = ClusterTree(coords, leaf)
+    part = Partition(tree, adm, eta)
+    res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est)
+    res.tau_basis = basis_threshold(tol, res.norm_est, 1 << tree.L)
+    h = assemble(tree, part, res, res.tau_basis, kmax)
+    return h, res

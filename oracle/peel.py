@@ -1,0 +1,194 @@
+"""Randomized peeling construction from Hessian-vector products (oracle side).
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU
+baseline use this module.
+
+Follows Section 3.3 (Figure 2) with the weak-admissibility sampling structure
+the paper's implementation uses:
+
+* Levels are processed coarse to fine.  At level l the sampled blocks are the
+  off-diagonal sibling blocks H[b, a] of every pair (a, b) = (child 0,
+  child 1) of a level-(l-1) box.  One probe block serves all pairs of a level
+  at once: Gaussian on the rows of every child-0 box, zero elsewhere.
+* The blocks of coarser levels already sampled are removed from the samples
+  (Y = H Omega - K Omega, K = sum of the coarser pieces), so that
+  Y[b] = H[b, a] Omega[a].
+* A QR factorisation of Y[b] gives the column basis Q_b; the product of the
+  matrix with [0; Q_b] (the projection pass, Psi) gives the row factor
+  Z[a] = H[a, b] Q_b, and the piece H[b, a] ~ Q_b Z[a]^T is stored as a local
+  low-rank update.  Sampling is repeated until the approximation of every
+  sampled block meets the threshold: adaptive probes, grown by b_inc columns
+  until the new columns' residuals (I - Q Q^T) y are all below
+  tau / (10 sqrt(2/pi)) (the a-posteriori range test of the randomized
+  range finder, halko11, cited in Section 3.3).
+* If a level's boxes are no larger than the probe count, the range of H[b, a]
+  is the whole of R^|b| and Q_b = I (no range pass is spent).
+* Finally identity probes on every leaf give the dense diagonal leaf blocks,
+  after removing all sampled pieces; they are symmetrised.
+
+Pieces of level l are stored in one N x q_l array P_l (tree order): rows of
+child-1 boxes hold Q_b, rows of child-0 boxes hold Z[a], so that for every
+pair H[b, a] ~ P_l[b] P_l[a]^T and H[a, b] ~ P_l[a] P_l[b]^T.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import rng
+from .tree import ClusterTree
+
+
+class TreeOperator:
+    """Wraps an operator acting in original node order so that it acts in tree order."""
+
+    def __init__(self, op, tree: ClusterTree):
+        self.op, self.tree = op, tree
+        self.samples = 0
+
+    def __call__(self, Om_tree: np.ndarray) -> np.ndarray:
+        perm = self.tree.perm
+        X = np.zeros_like(Om_tree)
+        X[perm] = Om_tree
+        self.samples += Om_tree.shape[1]
+        return np.asarray(self.op(X))[perm]
+
+
+def norm2_estimate(opt: TreeOperator, N: int, seed: int, maxit: int = 50, rtol: float = 1e-3):
+    """2-norm of the symmetric PSD operator by power iteration (Section 3.2: p-norms by
+    matrix-vector products).  Start vector: Gaussian from the `power` stream.  Stops when
+    the estimate changes by at most rtol relative, or after maxit products."""
+    v = rng.gaussian_block(seed, rng.STREAM_POWER, 0, N, 0, 1)
+    v /= np.linalg.norm(v)
+    lam_prev = 0.0
+    lam = 0.0
+    it = 0
+    for it in range(1, maxit + 1):
+        w = opt(v)
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            break
+        v = w / lam
+        if it > 1 and abs(lam - lam_prev) <= rtol * lam:
+            break
+        lam_prev = lam
+    return lam, it
+
+
+def apply_pieces(pieces, levels, tree: ClusterTree, Om: np.ndarray) -> np.ndarray:
+    """K Om for K = sum over the given levels of the sampled sibling pieces (flat low rank)."""
+    out = np.zeros_like(Om)
+    for l in levels:
+        P = pieces[l]
+        for i in range(1 << (l - 1)):
+            a, b = tree.rows(l, 2 * i), tree.rows(l, 2 * i + 1)
+            out[b] += P[b] @ (P[a].T @ Om[a])
+            out[a] += P[a] @ (P[b].T @ Om[b])
+    return out
+
+
+class PeelResult:
+    def __init__(self):
+        self.pieces = {}          # level -> N x q_l array (tree order)
+        self.rank = {}            # level -> per-pair number of columns of Q_b
+        self.range_probes = {}    # level -> range-pass probes spent
+        self.proj_probes = {}     # level -> projection-pass probes spent
+        self.test_err = {}        # level -> list of max residual per pair of each adaptive test
+        self.D_diag = []          # dense leaf diagonal blocks, per leaf
+        self.samples = 0
+        self.norm_est = 0.0
+        self.norm_its = 0
+        self.tau = 0.0
+
+
+def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, adaptive: bool,
+         seed: int, norm_est: float | None = None) -> PeelResult:
+    """Construct the sibling pieces and the leaf diagonal blocks from products with op."""
+    N = tree.N
+    opt = TreeOperator(op, tree)
+    res = PeelResult()
+    if norm_est is None:
+        res.norm_est, res.norm_its = norm2_estimate(opt, N, seed)
+    else:
+        res.norm_est, res.norm_its = float(norm_est), 0
+    tau = tol * res.norm_est
+    res.tau = tau
+    thr = tau / (10.0 * math.sqrt(2.0 / math.pi))
+
+    for l in range(1, tree.L + 1):
+        npairs = 1 << (l - 1)
+        A = [tree.rows(l, 2 * i) for i in range(npairs)]
+        B = [tree.rows(l, 2 * i + 1) for i in range(npairs)]
+        mb = max(b.stop - b.start for b in B)
+        below = range(1, l)
+        Qs = []
+        res.test_err[l] = []
+        if q0 >= mb:
+            # the range of H[b, a] is all of R^|b|
+            for b in B:
+                Qs.append(np.eye(b.stop - b.start))
+            res.range_probes[l] = 0
+        else:
+            def probe(col0, ncols):
+                Om = np.zeros((N, ncols))
+                for a in A:
+                    r = np.arange(a.start, a.stop, dtype=np.uint64)[:, None]
+                    c = np.arange(col0, col0 + ncols, dtype=np.uint64)[None, :]
+                    Om[a] = rng.gaussian(seed, rng.STREAM_PROBE, l, r, c)
+                return opt(Om) - apply_pieces(res.pieces, below, tree, Om)
+
+            q = q0
+            Y = probe(0, q)
+            Ys = [Y[b] for b in B]
+            Qs = [np.linalg.qr(y)[0] for y in Ys]
+            while adaptive and q < q_max and q < mb:
+                c = min(b_inc, q_max - q)
+                Yn = probe(q, c)
+                errs = []
+                for i, b in enumerate(B):
+                    yb = Yn[b]
+                    if Qs[i].shape[1] >= yb.shape[0]:
+                        errs.append(0.0)
+                    else:
+                        r = yb - Qs[i] @ (Qs[i].T @ yb)
+                        errs.append(float(np.linalg.norm(r, axis=0).max()))
+                    Ys[i] = np.hstack([Ys[i], yb])
+                    Qs[i] = np.linalg.qr(Ys[i])[0]
+                res.test_err[l].append(errs)
+                q += c
+                if max(errs) <= thr:
+                    break
+            res.range_probes[l] = q
+        ranks = [Q.shape[1] for Q in Qs]
+        qp = max(ranks)
+        Psi = np.zeros((N, qp))
+        for b, Q in zip(B, Qs):
+            Psi[b, :Q.shape[1]] = Q
+        Z = opt(Psi) - apply_pieces(res.pieces, below, tree, Psi)
+        P = np.zeros((N, qp))
+        for a, b, Q in zip(A, B, Qs):
+            k = Q.shape[1]
+            P[b, :k] = Q
+            P[a, :k] = Z[a, :k]
+        res.pieces[l] = P
+        res.rank[l] = ranks
+        res.proj_probes[l] = qp
+
+    # leaf diagonal blocks from identity probes
+    L = tree.L
+    lm = tree.leaf_max
+    Om = np.zeros((N, lm))
+    nleaf = 1 << L
+    for t in range(nleaf):
+        r = tree.rows(L, t)
+        m = r.stop - r.start
+        Om[r.start + np.arange(m), np.arange(m)] = 1.0
+    Y = opt(Om) - apply_pieces(res.pieces, range(1, L + 1), tree, Om)
+    for t in range(nleaf):
+        r = tree.rows(L, t)
+        m = r.stop - r.start
+        D = Y[r, :m]
+        res.D_diag.append(0.5 * (D + D.T))
+    res.samples = opt.samples
+    return res
