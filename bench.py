@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: H^2 construction from Hessian-vector products + multi-RHS H^2 matvec on GB300.
+
+One step = the whole hot path on the 256 x 256 heat-equation Hessian (N = 65,536,
+4,096 sensors, kappa 0.01, T 0.5, sigma 0.01, KD leaves of 64, strong admissibility
+0.7, rank cap 32, adaptive peeling to relative tolerance 1e-6), i.e. one FP64
+construction followed by FP64 matvecs with nrhs = 1, 32 and 256 resident in HBM.
+`value` is the matvec throughput in algorithmic GB/s (stored factor bytes + X and Y
+bytes per matvec, summed over the three matvecs, divided by their device time);
+the construction time per step is reported as build_s.  The factors (about 0.5 GB)
+are larger than L2, so no flush is needed between matvecs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the oracle (CPU, FP64) is timed on a bounded sample of the
+same workload (see cpu_baseline) and the same JSON line is printed with
+"impl": "reference".  Multi-GPU runs are replicas only (one independent H^2 per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
+CFG = W.MEDIUM_N256
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        hbm, src = float(d["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    fp64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return hbm, src, fp64
+
+
+def matvec_bytes(st: dict, N: int, nrhs: int, elt: int = 8) -> float:
+    stored = st["entries_D"] + st["entries_S"] + st["entries_U"] + st["entries_E"]
+    return stored * elt + N * nrhs * 2 * elt
+
+
+def leaf_near_flops(st: dict, tree_sizes, nrhs: int) -> float:
+    """FP64 flops of the leaf-expansion + near-field stage: every stored off-diagonal
+    near block is applied twice (as D and D^T), diagonal blocks once, leaf bases once."""
+    diag = float(np.sum(np.asarray(tree_sizes, dtype=np.float64) ** 2))
+    off = st["entries_D"] - diag
+    return 2.0 * nrhs * (diag + 2.0 * off + st["entries_U"])
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
+    """The oracle as it stands on a bounded sample of the workload: the same operator family
+    (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
+    then its matvec timed for nrhs 1, 32, 256 (algorithmic bytes as for the GPU)."""
+    import oracle as O
+
+    p = CFG["problem"]
+    b = CFG["build"]
+    n = n_sample
+    m = int(round(p.m * (n * n) / p.N))
+    mask = W.sensor_mask(n * n, m, p.sensor_seed)
+    op = O.HeatHessian(n, p.kappa, p.T, p.sigma, mask)
+    t0 = time.perf_counter()
+    h, res = O.build(op, W.grid_coords(n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
+                     b.adaptive, b.seed)
+    t_build = time.perf_counter() - t0
+    ent = O.storage_entries(h)
+    st = {"entries_D": ent["D"], "entries_S": ent["S"], "entries_U": ent["U"], "entries_E": ent["E"]}
+    tot_bytes, tot_t = 0.0, 0.0
+    for nrhs in nrhs_list:
+        X = W.rhs(n * n, nrhs, 5)
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            O.matvec(h, X)
+            tot_t += time.perf_counter() - t0
+            tot_bytes += matvec_bytes(st, n * n, nrhs)
+    return {"value": tot_bytes / tot_t / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle build of the same heat-Hessian family at n={n} (N={n * n}, {m} sensors) "
+                      f"in {t_build:.1f} s, then oracle matvec with nrhs {list(nrhs_list)} x{reps}",
+            "build_s": t_build, "samples": int(res.samples - res.norm_its)}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    p = CFG["problem"]
+    b = CFG["build"]
+    n = 128
+    m = int(round(p.m * (n * n) / p.N))
+    mask = W.sensor_mask(n * n, m, p.sensor_seed)
+    op = O.HeatHessian(n, p.kappa, p.T, p.sigma, mask)
+    h, res = O.build(op, W.grid_coords(n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
+                     b.adaptive, b.seed)
+    ent = O.storage_entries(h)
+    st = {"entries_D": ent["D"], "entries_S": ent["S"], "entries_U": ent["U"], "entries_E": ent["E"]}
+    Xs = {nr: W.rhs(n * n, nr, 5) for nr in CFG["nrhs"]}
+
+    def step():
+        by, tt = 0.0, 0.0
+        for nr, X in Xs.items():
+            t0 = time.perf_counter()
+            O.matvec(h, X)
+            tt += time.perf_counter() - t0
+            by += matvec_bytes(st, n * n, nr)
+        return by, tt
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tb, tt = 0.0, 0.0
+    for _ in range(args.steps):
+        b_, t_ = step()
+        tb += b_
+        tt += t_
+    wall = time.perf_counter() - t0
+    val = tb / tt / 1e9
+    sample = (f"oracle matvec (nrhs {list(CFG['nrhs'])}) of the oracle-built H^2 of the same heat-Hessian "
+              f"family at n={n} (N={n * n}); the n=256 build does not fit a bounded CPU sample")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CFG["name"], "N": p.N, "nrhs": list(CFG["nrhs"]), "tol": b.tol},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    # CPU baseline before any GPU work of this process (spawned pool not needed: single process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    import paper_2003_10173_gb300 as h2
+    from paper_2003_10173_gb300 import build_lib
+    build_lib.build()
+    h2.lib()
+
+    p, b = CFG["problem"], CFG["build"]
+    N = p.N
+    mask = W.sensor_mask(N, p.m, p.sensor_seed)
+    gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, mask)
+    tree = h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta)
+    stream = torch.cuda.current_stream()
+    opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
+                           seed=b.seed, stream=stream)
+    nrhs_list = list(CFG["nrhs"])
+    Xd = {nr: torch.from_numpy(np.ascontiguousarray(W.rhs(N, nr, CFG["rhs_seed"] + nr).T)).cuda()
+          for nr in nrhs_list}
+    Yd = {nr: torch.empty_like(Xd[nr]) for nr in nrhs_list}
+
+    def step(profile=False):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        G = h2.H2.build(gop, tree, b.tol, opts)
+        ev1.record(stream)
+        mv = {}
+        for nr in nrhs_list:
+            a = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.matvec(Xd[nr], Yd[nr], nr, h2.H2_FP64, stream=stream)
+            c.record(stream)
+            mv[nr] = (a, c)
+        return G, (ev0, ev1), mv
+
+    for _ in range(args.warmup):
+        G, _, _ = step()
+        G.close()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    h2.gemm_profile(True)
+    launches0 = h2.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    results = []
+    for _ in range(args.steps):
+        G, bev, mv = step()
+        results.append((G, bev, mv))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = h2.launch_count() - launches0
+    gemm_ms, gemm_flops, gemm_n = h2.gemm_profile_read()
+    h2.gemm_profile(False)
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    st = results[-1][0].stats()
+    build_ms = [bev[0].elapsed_time(bev[1]) for _, bev, _ in results]
+    mv_ms = {nr: [mv[nr][0].elapsed_time(mv[nr][1]) for _, _, mv in results] for nr in nrhs_list}
+    by = {nr: matvec_bytes(st, N, nr) for nr in nrhs_list}
+    tot_bytes = sum(by[nr] * len(mv_ms[nr]) for nr in nrhs_list)
+    tot_mv_s = sum(sum(mv_ms[nr]) for nr in nrhs_list) / 1e3
+    value = tot_bytes / tot_mv_s / 1e9 * world
+    hbm, hbm_src, fp64 = peaks()
+
+    # roofline of the dominant matvec kernel (leaf expansion + near field) at nrhs = 1, FP64
+    Gp = results[-1][0]
+    Gp.profile(True)
+    for _ in range(5):
+        Gp.matvec(Xd[1], Yd[1], 1, h2.H2_FP64, stream=stream)
+    prof = Gp.profile_read()
+    Gp.profile(False)
+    _, sizes = tree.boxes(tree.L)
+    ln_ms, ln_n = prof["leaf_near"]
+    ln_flops = leaf_near_flops(st, sizes, 1)
+    achieved = ln_flops / (ln_ms / ln_n / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64, "unit": "TFLOP/s", "frac": achieved / fp64,
+                "traffic": None, "kernel": "mv_stage_kernel<double> (leaf expansion + near field), nrhs=1",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+    gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+    roofline_build = {"bound": "alu", "achieved": gemm_tf, "peak": fp64, "unit": "TFLOP/s",
+                      "frac": (gemm_tf / fp64) if gemm_tf else None, "traffic": None,
+                      "kernel": "gemm_tiles_kernel (FP64 batched GEMM: operator DSTs, piece subtraction, Gram)",
+                      "launches": gemm_n, "ms": gemm_ms}
+    near_bytes = st["entries_D"] * 8
+    hbm_view = {"nrhs1_matvec_GBps": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9,
+                "frac_of_hbm": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9 / hbm, "hbm_peak_GBps": hbm,
+                "hbm_peak_source": hbm_src}
+
+    # end to end through the public call with host buffers (pinned) and copies in the timed region
+    Gp2 = results[-1][0]
+    Xh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
+    Yh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
+    for nr in nrhs_list:
+        Xh[nr].copy_(Xd[nr].cpu())
+    Xe = {nr: torch.empty_like(Xd[nr]) for nr in nrhs_list}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for nr in nrhs_list:
+            Xe[nr].copy_(Xh[nr], non_blocking=True)
+            Gp2.matvec(Xe[nr], Yd[nr], nr, h2.H2_FP64, stream=stream)
+            Yh[nr].copy_(Yd[nr], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_bytes = reps * sum(by[nr] for nr in nrhs_list)
+    e2e = {"value": e2e_bytes / e2e_s / 1e9 * world, "unit": "GB/s",
+           "h2d_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list),
+           "d2h_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list)}
+
+    # accuracy of the last build (2-norm, power iteration through the GPU matvec and operator)
+    rel_err = None
+    if rank == 0:
+        v = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+        w1 = torch.empty_like(v)
+        w2 = torch.empty_like(v)
+        lam, prev = 0.0, 0.0
+        v /= v.norm()
+        for it in range(60):
+            gop.apply(v, w1, 1, stream=stream)
+            Gp2.matvec(v, w2, 1, h2.H2_FP64, stream=stream)
+            w = w1 - w2
+            lam = float(w.norm())
+            if lam == 0:
+                break
+            v = w / lam
+            if it > 0 and abs(lam - prev) <= 1e-2 * lam:
+                break
+            prev = lam
+        rel_err = lam / st["norm_est"]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CFG["name"], "N": N, "grid": f"{p.n}x{p.n}", "sensors": p.m, "kappa": p.kappa,
+                       "leaf": b.leaf, "adm": "strong", "eta": b.eta, "kmax": b.kmax, "tol": b.tol,
+                       "nrhs": nrhs_list, "mode": "FP64",
+                       "l2": "H2 factors larger than L2 (no flush needed)", "parallelism": "replicas"},
+            "build_s": float(np.mean(build_ms)) / 1e3,
+            "rel_err_2norm": rel_err,
+            "samples": st["samples"], "norm_products": st["norm_products"], "max_rank": st["max_rank"],
+            "range_probes": st["range_probes"], "proj_probes": st["proj_probes"],
+            "matvec_ms": {str(nr): float(np.mean(mv_ms[nr])) for nr in nrhs_list},
+            "matvec_GBps": {str(nr): by[nr] / (np.mean(mv_ms[nr]) / 1e3) / 1e9 for nr in nrhs_list},
+            "stored_bytes_fp64": (st["entries_D"] + st["entries_S"] + st["entries_U"] + st["entries_E"]) * 8,
+            "hbm_view": hbm_view,
+            "roofline": roofline, "roofline_build": roofline_build,
+            "stage_ms_nrhs1": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+            "build_phase_s": {k: st[k] for k in ("t_norm", "t_op", "t_peel", "t_assemble")},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    for G, _, _ in results:
+        G.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

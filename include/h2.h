@@ -1,0 +1,285 @@
+/*
+ * h2.h - C ABI of the GB300 H^2 Hessian library.
+ *
+ * Builds a hierarchical (H^2) approximation of a symmetric PDE-constrained
+ * Hessian using only Hessian-vector products (randomized peeling, Section 3.3
+ * of Ambartsumyan et al., "Hierarchical matrix approximations of Hessians
+ * arising in inverse problems governed by PDEs", arXiv 2003.10173) and applies
+ * it to many vectors at once (four-stage matvec, Section 3.2, Eq. (3.2)).
+ *
+ * Conventions for every entry point:
+ *   - Return value: H2_OK (0) on success, a negative H2_ERR_* code on error, a
+ *     positive H2_WARN_* code when the call completed with a caveat.  No C++
+ *     exception crosses this boundary.  h2_error_string() names a code and
+ *     h2_last_error() gives the calling thread's last detailed message.
+ *   - Matrices are column-major with an explicit leading dimension.  Vectors and
+ *     right-hand sides are in the caller's (original) node order; the library
+ *     reorders internally.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary CPU memory.
+ *   - The caller owns every buffer it passes; the library owns trees, handles and
+ *     operator contexts it creates and frees them in the matching *_free/destroy.
+ *     Freeing NULL is a no-op.
+ *   - A handle is not thread-safe; distinct handles may be used concurrently on
+ *     distinct streams.
+ *   - Streams are passed as h2_stream_t (a cudaStream_t cast to void*; NULL is the
+ *     legacy default stream).  Calls that launch work are asynchronous with
+ *     respect to the host unless stated otherwise.
+ */
+#ifndef H2_H
+#define H2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* h2_stream_t;
+typedef struct h2_tree_s* h2_tree_t;
+typedef struct h2_handle_s* h2_handle_t;
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    H2_OK = 0,
+    H2_ERR_INVALID_ARG = -1,   /* bad size, pointer, option or unsupported mode */
+    H2_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+    H2_ERR_OP_FAILED = -3,     /* the user's Hessian operator returned nonzero */
+    H2_ERR_NAN = -4,           /* NaN or Inf found in operator samples */
+    H2_ERR_OOM = -5,           /* device allocation failed */
+    H2_ERR_DEVICE_CHECK = -6,  /* a kernel reported an out-of-range index or a bounded wait ran out */
+    H2_WARN_TOL_NOT_MET = 1    /* the rank cap or the probe cap limited a truncation */
+};
+
+/* ---- admissibility (Section 3.1, Table 1) -------------------------------- */
+enum {
+    H2_ADM_WEAK = 0,    /* every off-diagonal sibling block is low rank (HSS partition) */
+    H2_ADM_STRONG = 1   /* (t,s) low rank iff max(diam t, diam s) <= eta * dist(t, s) */
+};
+
+/* ---- matvec arithmetic modes ---------------------------------------------- */
+enum {
+    H2_FP64 = 0,   /* X, Y double; FP64 storage and arithmetic */
+    H2_FP32 = 1,   /* X, Y float; FP32 storage and arithmetic */
+    H2_TF32 = 2,   /* X float, Y float; FP32 storage, TF32 tensor-core products, FP32 accumulation */
+    H2_BF16 = 3    /* X bf16 (uint16 storage), Y float; BF16 storage, tensor-core products, FP32 accumulation */
+};
+
+#define H2_MAX_LEVELS 32
+
+/*
+ * Hessian-vector product callback (the only place where the library leaves its
+ * own code; Section 3.3: the Hessian is available only through products).
+ * Computes Y = H X for nrhs columns; X is n x nrhs (device, leading dimension
+ * ldx), Y is n x nrhs (device, ldy), both in original node order, FP64.  Work
+ * must be enqueued on `stream` (asynchronous is fine).  X and Y are library
+ * scratch: the callback must not keep them after returning.  Return 0 on
+ * success; any other value aborts the build with H2_ERR_OP_FAILED.
+ */
+typedef int (*h2_op_fn)(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx,
+                        double* Y, int64_t ldy, h2_stream_t stream);
+
+/* ---- construction options ------------------------------------------------ */
+typedef struct {
+    int kmax;            /* cap on basis ranks (default 32) */
+    int q0;              /* initial probes per level, or the fixed count if adaptive == 0 (default 32) */
+    int b_inc;           /* probe increment of the adaptive range finder, 1..16 (default 16) */
+    int q_max;           /* probe cap per level (default 256) */
+    int adaptive;        /* 1: grow probes until the a-posteriori range test passes (default 1) */
+    uint64_t seed;       /* seed of the counter-based probe generator (default 7) */
+    double norm_est;     /* > 0: use this value of ||H||_2 instead of estimating it (default 0) */
+    int norm_maxit;      /* power-iteration cap for ||H||_2 (default 50) */
+    double norm_rtol;    /* power-iteration stop: relative change (default 1e-3) */
+    int keep_fp32;       /* also keep an FP32 copy of the factors (enables H2_FP32/H2_TF32), default 0 */
+    int keep_bf16;       /* also keep a BF16 copy of the factors (enables H2_BF16), default 0 */
+    h2_stream_t stream;  /* stream for all build work and operator calls (default NULL) */
+} h2_build_opts;
+
+/* Fill *opts with the defaults above.  Returns H2_ERR_INVALID_ARG if opts is NULL. */
+int h2_build_opts_default(h2_build_opts* opts);
+
+/* ---- statistics (host struct) -------------------------------------------- */
+typedef struct {
+    int64_t n;                              /* matrix size */
+    int levels;                             /* tree depth L (leaves at level L) */
+    int leaf_max;                           /* largest leaf */
+    int64_t samples;                        /* Hessian-vector products of the peeling (excl. norm estimate) */
+    int64_t norm_products;                  /* products spent on the ||H||_2 estimate */
+    int range_probes[H2_MAX_LEVELS];        /* range-pass probes per level (index = level) */
+    int proj_probes[H2_MAX_LEVELS];         /* projection-pass probes per level */
+    int max_rank[H2_MAX_LEVELS];            /* largest basis rank per level */
+    int64_t far_lower;                      /* stored (lower-triangle) far blocks */
+    int64_t near_lower;                     /* stored (lower-triangle + diagonal) near blocks */
+    int64_t entries_D, entries_S, entries_U, entries_E;  /* stored floating-point entries */
+    double norm_est;                        /* ||H||_2 estimate used */
+    double tau_basis;                       /* absolute truncation threshold of the bases */
+    double tau_test;                        /* threshold of the range test */
+    int tol_met;                            /* 0 if a cap limited a truncation */
+    double t_total, t_norm, t_op, t_peel, t_assemble;   /* seconds (host wall clock, synchronised) */
+} h2_stats;
+
+/* ---- cluster tree and partition (host only; no CUDA calls) --------------- */
+
+/*
+ * Build the KD cluster tree (Section 4.2, Section 4.4: binary space partition,
+ * spatial ordering) and the block partition (Section 3.1) for n points of
+ * dimension dim (1..3), coordinates coords_host[i*dim + d] (host, row-major).
+ * Every box of a level is split while the largest box of that level exceeds
+ * leaf_size (>= 2), so all leaves share one depth; the split coordinate is the
+ * longer bounding-box side (ties to the first); points are ordered by
+ * (coordinate, original index) and the first floor(|t|/2) go to child 0.
+ * adm is H2_ADM_WEAK or H2_ADM_STRONG with parameter eta > 0.
+ * Errors: H2_ERR_INVALID_ARG for n < 1, bad dim, leaf_size < 2, bad adm or eta,
+ * NULL pointers, non-finite coordinates or depth above H2_MAX_LEVELS - 1.
+ */
+int h2_tree_create(const double* coords_host, int64_t n, int dim, int leaf_size, int adm,
+                   double eta, h2_tree_t* out);
+void h2_tree_free(h2_tree_t tree);
+
+/* Tree depth L, number of points, number of far blocks (both triangles, all
+ * levels) and near blocks (both triangles).  Any output pointer may be NULL. */
+int h2_tree_info(h2_tree_t tree, int* levels, int64_t* n, int64_t* n_far, int64_t* n_near);
+
+/* Tree-order permutation: perm_host[i] = original index of tree position i (n entries). */
+int h2_tree_perm(h2_tree_t tree, int64_t* perm_host);
+
+/* Box ranges of one level: starts_host/sizes_host get 2^level entries (tree order). */
+int h2_tree_boxes(h2_tree_t tree, int level, int64_t* starts_host, int64_t* sizes_host);
+
+/* Far blocks of one level (both triangles, sorted by (t, s)): pairs_host[2*i], pairs_host[2*i+1].
+ * *count receives the number of blocks; pairs_host may be NULL to query the count. */
+int h2_tree_far(h2_tree_t tree, int level, int64_t* count, int32_t* pairs_host);
+
+/* Near (leaf-level dense) blocks, both triangles, sorted by (t, s). */
+int h2_tree_near(h2_tree_t tree, int64_t* count, int32_t* pairs_host);
+
+/* ---- construction --------------------------------------------------------- */
+
+/*
+ * Construct the H^2 approximation of the symmetric operator `op` on `tree` to
+ * relative accuracy tol (> 0) by randomized peeling (Section 3.3, Figure 2):
+ * ||H||_2 estimate by power iteration (Section 3.2); per level, Gaussian probes on
+ * child-0 boxes, removal of the coarser pieces, orthonormal range of every
+ * child-1 sample block with an adaptive a-posteriori test, projection pass;
+ * identity probes for the dense diagonal leaf blocks; then recompression into
+ * nested orthonormal bases, couplings and dense near blocks (Section 3.2).
+ * The tree may be freed after this call.  opts may be NULL (defaults).
+ * Synchronises the stream before returning.  Errors: INVALID_ARG, CUDA, OOM,
+ * OP_FAILED, NAN, DEVICE_CHECK; H2_WARN_TOL_NOT_MET leaves a valid handle.
+ */
+int h2_build(h2_op_fn op, void* ctx, h2_tree_t tree, double tol, const h2_build_opts* opts,
+             h2_handle_t* out);
+
+/*
+ * Create a handle from explicit H^2 factors given in host memory (checkpoint
+ * load, and test input).  Layout, all column-major FP64 and in tree order:
+ *   ranks_host: k of every box, levels 0..L in order, 2^l boxes per level;
+ *   U_host: leaf bases, leaf 0..2^L-1 in order, |t| x k_t each;
+ *   E_host: transfer matrices of every box c at levels 1..L (in order), k_c x k_parent(c);
+ *   S_host: couplings of the lower far blocks (t > s), levels 1..L, each level in
+ *           h2_tree_far order, k_t x k_s each;
+ *   D_host: near blocks with t >= s in h2_tree_near order, |t| x |s| each.
+ * The representation is A = D + U S U^T with the upper blocks the transposes of the
+ * lower ones (symmetric).  Errors: INVALID_ARG (sizes inconsistent with the tree),
+ * CUDA, OOM.
+ */
+int h2_import(h2_tree_t tree, const int32_t* ranks_host, const double* U_host, const double* E_host,
+              const double* S_host, const double* D_host, int keep_fp32, int keep_bf16,
+              h2_handle_t* out);
+
+/* Sizes of the arrays of h2_import/h2_export for handle h (entries, not bytes). */
+int h2_factor_sizes(h2_handle_t h, int64_t* n_ranks, int64_t* n_U, int64_t* n_E, int64_t* n_S,
+                    int64_t* n_D);
+
+/* Copy the FP64 factors of h to host arrays in the h2_import layout (checkpoint save).
+ * Any pointer may be NULL to skip that array.  Synchronous. */
+int h2_export(h2_handle_t h, int32_t* ranks_host, double* U_host, double* E_host, double* S_host,
+              double* D_host);
+
+/* ---- application ----------------------------------------------------------- */
+
+/*
+ * Y = A X for nrhs right-hand sides by the four stages of Section 3.2, Eq. (3.2):
+ * leaf bases and transfer matrices up the tree, couplings per level, transfer
+ * matrices and leaf bases down the tree, plus the dense near blocks.  X (n x nrhs,
+ * leading dimension ldx >= n) and Y (n x nrhs, ldy >= n) are device buffers in
+ * original node order; their element types follow `mode` (see H2_FP64..H2_BF16).
+ * X and Y must not overlap.  Enqueued on `stream`; returns before completion.
+ * Errors: INVALID_ARG (sizes, NULL pointers, a mode whose storage copy was not
+ * kept), CUDA, OOM.
+ */
+int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+              int mode, h2_stream_t stream);
+
+/* Stage kinds of the matvec, for h2_profile_read. */
+enum {
+    H2_STAGE_LEAF_UP = 0,   /* xh_t = U_t^T X_t */
+    H2_STAGE_UP = 1,        /* transfer upsweep, all levels */
+    H2_STAGE_COUPLE = 2,    /* couplings, all levels */
+    H2_STAGE_DOWN = 3,      /* transfer downsweep, all levels */
+    H2_STAGE_LEAF_NEAR = 4, /* Y_t = U_t yh_t + sum_s D_ts X_s */
+    H2_STAGE_COUNT = 5
+};
+
+/* Enable (1) or disable (0) per-stage timing of h2_matvec on handle h: CUDA events
+ * are recorded on the caller's stream around every stage launch.  Diagnostics only. */
+int h2_profile(h2_handle_t h, int enable);
+
+/* Synchronise the device, then return and reset the accumulated per-kind stage times
+ * (milliseconds, ms_out[H2_STAGE_COUNT]) and launch counts (launches_out[H2_STAGE_COUNT]).
+ * Either pointer may be NULL. */
+int h2_profile_read(h2_handle_t h, double* ms_out, int64_t* launches_out);
+
+/* Process-wide timing of the batched FP64 GEMM kernel used by the construction and
+ * by the shipped operators: when enabled (1), CUDA events are recorded around every
+ * GEMM launch on its stream.  h2_gemm_profile_read synchronises the device, returns the
+ * accumulated milliseconds, algorithmic flops (sum of 2 m n k) and launches, and resets. */
+int h2_gemm_profile(int enable);
+int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out);
+
+/* Statistics of the construction of h (host struct). */
+int h2_get_stats(h2_handle_t h, h2_stats* out);
+
+/* Release a handle and its device memory.  NULL is a no-op. */
+void h2_free(h2_handle_t h);
+
+/* ---- synthetic Hessians shipped with the library ------------------------- */
+
+/*
+ * Misfit Hessian of 2-D heat-equation initial-condition inversion on the unit
+ * square: H = F diag(mask) F / sigma^2, F = exp(T kappa Lap_h) with the 5-point
+ * Dirichlet Laplacian on the n x n interior grid (node p = i*n + j at ((i+1)h,
+ * (j+1)h), h = 1/(n+1)), applied exactly through the orthonormal DST-I.  mask_host
+ * holds n*n entries (1 at sensor nodes, 0 elsewhere).  Creates device state on the
+ * current device.  Errors: INVALID_ARG, CUDA, OOM.
+ */
+int h2_heat2d_create(int n, double kappa, double T, double sigma, const double* mask_host,
+                     void** ctx_out);
+/* h2_op_fn implementation for a context from h2_heat2d_create. */
+int h2_heat2d_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y,
+                    int64_t ldy, h2_stream_t stream);
+void h2_heat2d_destroy(void* ctx);
+
+/* Dense symmetric operator Y = A X with A an n x n device matrix (leading dimension
+ * lda) that the caller keeps alive while the context is used. */
+int h2_dense_op_create(const double* A_device, int64_t n, int64_t lda, void** ctx_out);
+int h2_dense_op_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y,
+                      int64_t ldy, h2_stream_t stream);
+void h2_dense_op_destroy(void* ctx);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+const char* h2_error_string(int status);
+/* Detailed message of the calling thread's last failing call ("" if none). */
+const char* h2_last_error(void);
+/* Number of kernels the library has launched in this process. */
+int64_t h2_launch_count(void);
+/* Library version string. */
+const char* h2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2_H */

@@ -77,6 +77,7 @@ def block_row_weights(tree: ClusterTree, part: Partition, pieces):
     [R_lp(parent); P_lp[s] for the far blocks (t, s) of t itself with pair level lp]."""
     L = tree.L
     R = [dict() for _ in range(L + 1)]
+    R[0][0] = {}                      # the root has no far blocks
     for l in range(1, L + 1):
         for t in range(1 << l):
             groups = {lp: [Rp] for lp, Rp in R[l - 1].get(t >> 1, {}).items()}

@@ -1,0 +1,385 @@
+"""Python binding of the GB300 H^2 Hessian library (libh2hess.so, C ABI in include/h2.h).
+
+The binding only marshals arguments: every step of construction and application
+runs in the library's CUDA kernels.  Device buffers are passed as torch tensors
+(or raw integer device pointers); torch is used for device memory and streams.
+If the shared library is missing, importing the binding's entry points raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libh2hess.so")
+
+H2_OK = 0
+H2_ERR_INVALID_ARG = -1
+H2_ERR_CUDA = -2
+H2_ERR_OP_FAILED = -3
+H2_ERR_NAN = -4
+H2_ERR_OOM = -5
+H2_ERR_DEVICE_CHECK = -6
+H2_WARN_TOL_NOT_MET = 1
+
+H2_ADM_WEAK = 0
+H2_ADM_STRONG = 1
+
+H2_FP64 = 0
+H2_FP32 = 1
+H2_TF32 = 2
+H2_BF16 = 3
+
+H2_MAX_LEVELS = 32
+
+OP_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [
+        ("kmax", ctypes.c_int), ("q0", ctypes.c_int), ("b_inc", ctypes.c_int), ("q_max", ctypes.c_int),
+        ("adaptive", ctypes.c_int), ("seed", ctypes.c_uint64), ("norm_est", ctypes.c_double),
+        ("norm_maxit", ctypes.c_int), ("norm_rtol", ctypes.c_double), ("keep_fp32", ctypes.c_int),
+        ("keep_bf16", ctypes.c_int), ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("levels", ctypes.c_int), ("leaf_max", ctypes.c_int),
+        ("samples", ctypes.c_int64), ("norm_products", ctypes.c_int64),
+        ("range_probes", ctypes.c_int * H2_MAX_LEVELS), ("proj_probes", ctypes.c_int * H2_MAX_LEVELS),
+        ("max_rank", ctypes.c_int * H2_MAX_LEVELS),
+        ("far_lower", ctypes.c_int64), ("near_lower", ctypes.c_int64),
+        ("entries_D", ctypes.c_int64), ("entries_S", ctypes.c_int64), ("entries_U", ctypes.c_int64),
+        ("entries_E", ctypes.c_int64),
+        ("norm_est", ctypes.c_double), ("tau_basis", ctypes.c_double), ("tau_test", ctypes.c_double),
+        ("tol_met", ctypes.c_int),
+        ("t_total", ctypes.c_double), ("t_norm", ctypes.c_double), ("t_op", ctypes.c_double),
+        ("t_peel", ctypes.c_double), ("t_assemble", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        L = self.levels
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        for k in ("range_probes", "proj_probes", "max_rank"):
+            d[k] = [int(x) for x in getattr(self, k)[: L + 1]]
+        return d
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "h2_build_opts_default": (_I, [ctypes.POINTER(BuildOpts)]),
+    "h2_tree_create": (_I, [_P, _I64, _I, _I, _I, _D, ctypes.POINTER(_P)]),
+    "h2_tree_free": (None, [_P]),
+    "h2_tree_info": (_I, [_P, _P, _P, _P, _P]),
+    "h2_tree_perm": (_I, [_P, _P]),
+    "h2_tree_boxes": (_I, [_P, _I, _P, _P]),
+    "h2_tree_far": (_I, [_P, _I, _P, _P]),
+    "h2_tree_near": (_I, [_P, _P, _P]),
+    "h2_build": (_I, [_P, _P, _P, _D, ctypes.POINTER(BuildOpts), ctypes.POINTER(_P)]),
+    "h2_import": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, ctypes.POINTER(_P)]),
+    "h2_factor_sizes": (_I, [_P, _P, _P, _P, _P, _P]),
+    "h2_export": (_I, [_P, _P, _P, _P, _P, _P]),
+    "h2_matvec": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
+    "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "h2_profile": (_I, [_P, _I]),
+    "h2_profile_read": (_I, [_P, _P, _P]),
+    "h2_gemm_profile": (_I, [_I]),
+    "h2_gemm_profile_read": (_I, [_P, _P, _P]),
+    "h2_free": (None, [_P]),
+    "h2_heat2d_create": (_I, [_I, _D, _D, _D, _P, ctypes.POINTER(_P)]),
+    "h2_heat2d_apply": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P]),
+    "h2_heat2d_destroy": (None, [_P]),
+    "h2_dense_op_create": (_I, [_P, _I64, _I64, ctypes.POINTER(_P)]),
+    "h2_dense_op_apply": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P]),
+    "h2_dense_op_destroy": (None, [_P]),
+    "h2_error_string": (ctypes.c_char_p, [_I]),
+    "h2_last_error": (ctypes.c_char_p, []),
+    "h2_launch_count": (_I64, []),
+    "h2_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    """Load libh2hess.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2003_10173_gb300.build_lib.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, allow_warn: bool = False) -> int:
+    if status < 0 or (status > 0 and not allow_warn):
+        L = lib()
+        raise H2Error(status, f"{L.h2_error_string(status).decode()}: {L.h2_last_error().decode()}")
+    return status
+
+
+def _ptr(x) -> int:
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_opts(**kw) -> BuildOpts:
+    o = BuildOpts()
+    _check(lib().h2_build_opts_default(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "stream":
+            v = _stream_ptr(v)
+        setattr(o, k, v)
+    return o
+
+
+class Tree:
+    """KD cluster tree + block partition (host data)."""
+
+    def __init__(self, coords: np.ndarray, leaf: int, adm: int = H2_ADM_STRONG, eta: float = 0.7):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        if coords.ndim != 2:
+            raise ValueError("coords must be (n, dim)")
+        h = ctypes.c_void_p()
+        _check(lib().h2_tree_create(coords.ctypes.data, coords.shape[0], coords.shape[1], leaf, adm, eta,
+                                    ctypes.byref(h)))
+        self._h = h
+        lv, n, nf, nn = _I(), _I64(), _I64(), _I64()
+        _check(lib().h2_tree_info(h, ctypes.byref(lv), ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nn)))
+        self.L, self.N, self.n_far, self.n_near = lv.value, n.value, nf.value, nn.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def perm(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.int64)
+        _check(lib().h2_tree_perm(self._h, out.ctypes.data))
+        return out
+
+    def boxes(self, level: int):
+        st = np.empty(1 << level, dtype=np.int64)
+        sz = np.empty(1 << level, dtype=np.int64)
+        _check(lib().h2_tree_boxes(self._h, level, st.ctypes.data, sz.ctypes.data))
+        return st, sz
+
+    def far(self, level: int) -> np.ndarray:
+        c = _I64()
+        _check(lib().h2_tree_far(self._h, level, ctypes.byref(c), None))
+        out = np.empty((c.value, 2), dtype=np.int32)
+        _check(lib().h2_tree_far(self._h, level, ctypes.byref(c), out.ctypes.data))
+        return out
+
+    def near(self) -> np.ndarray:
+        c = _I64()
+        _check(lib().h2_tree_near(self._h, ctypes.byref(c), None))
+        out = np.empty((c.value, 2), dtype=np.int32)
+        _check(lib().h2_tree_near(self._h, ctypes.byref(c), out.ctypes.data))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().h2_tree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HeatOperator:
+    """The library's heat-equation misfit Hessian H = F diag(mask) F / sigma^2 (device state)."""
+
+    def __init__(self, n: int, kappa: float, T: float, sigma: float, mask: np.ndarray):
+        mask = np.ascontiguousarray(mask, dtype=np.float64)
+        if mask.size != n * n:
+            raise ValueError("mask must have n*n entries")
+        h = ctypes.c_void_p()
+        _check(lib().h2_heat2d_create(n, kappa, T, sigma, mask.ctypes.data, ctypes.byref(h)))
+        self.ctx = h
+        self.N = n * n
+        self.fn = ctypes.cast(lib().h2_heat2d_apply, ctypes.c_void_p)
+        self._mask = mask
+
+    def apply(self, X, Y, nrhs: int, stream=None, ldx: int | None = None, ldy: int | None = None):
+        _check(lib().h2_heat2d_apply(self.ctx, self.N, nrhs, _ptr(X), ldx or self.N, _ptr(Y), ldy or self.N,
+                                     _stream_ptr(stream)))
+
+    def close(self):
+        if self.ctx:
+            lib().h2_heat2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DenseOperator:
+    """Y = A X with a caller-owned dense FP64 device matrix (kept alive by this object)."""
+
+    def __init__(self, A):
+        self.A = A
+        n = A.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().h2_dense_op_create(_ptr(A), n, n, ctypes.byref(h)))
+        self.ctx = h
+        self.N = n
+        self.fn = ctypes.cast(lib().h2_dense_op_apply, ctypes.c_void_p)
+
+    def close(self):
+        if self.ctx:
+            lib().h2_dense_op_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PyOperator:
+    """Wraps a Python callable f(X_ptr, ldx, Y_ptr, ldy, nrhs, stream_ptr) -> int as an h2_op_fn."""
+
+    def __init__(self, N: int, fn):
+        self.N = N
+
+        def tramp(ctx, n, nrhs, X, ldx, Y, ldy, stream):
+            try:
+                return int(fn(X, ldx, Y, ldy, nrhs, stream) or 0)
+            except Exception:
+                return 99
+
+        self._cb = OP_FN(tramp)
+        self.fn = ctypes.cast(self._cb, ctypes.c_void_p)
+        self.ctx = None
+
+
+class H2:
+    """A built H^2 approximation (device factors owned by the library)."""
+
+    def __init__(self, handle, status: int = 0):
+        self._h = handle
+        self.status = status
+
+    @classmethod
+    def build(cls, op, tree: Tree, tol: float, opts: BuildOpts | None = None) -> "H2":
+        h = ctypes.c_void_p()
+        st = lib().h2_build(op.fn, op.ctx, tree.handle, tol, ctypes.byref(opts) if opts is not None else None,
+                            ctypes.byref(h))
+        _check(st, allow_warn=True)
+        return cls(h, st)
+
+    @classmethod
+    def from_factors(cls, tree: Tree, ranks, U, E, S, D, keep_fp32=False, keep_bf16=False) -> "H2":
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (U, E, S, D)]
+        rk = np.ascontiguousarray(ranks, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().h2_import(tree.handle, rk.ctypes.data, *[a.ctypes.data if a.size else None for a in arrs],
+                               int(keep_fp32), int(keep_bf16), ctypes.byref(h)))
+        return cls(h)
+
+    def factor_sizes(self):
+        v = [_I64() for _ in range(5)]
+        _check(lib().h2_factor_sizes(self._h, *[ctypes.byref(x) for x in v]))
+        return [x.value for x in v]
+
+    def export(self):
+        nr, nu, ne, ns, nd = self.factor_sizes()
+        rk = np.empty(nr, dtype=np.int32)
+        out = [np.empty(max(n, 1)) for n in (nu, ne, ns, nd)]
+        _check(lib().h2_export(self._h, rk.ctypes.data, *[a.ctypes.data for a in out]))
+        return (rk,) + tuple(a[:n] for a, n in zip(out, (nu, ne, ns, nd)))
+
+    def matvec(self, X, Y, nrhs: int, mode: int = H2_FP64, stream=None, ldx: int | None = None,
+               ldy: int | None = None):
+        n = self.stats()["n"]
+        _check(lib().h2_matvec(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode, _stream_ptr(stream)))
+
+    STAGES = ("leaf_up", "up", "couple", "down", "leaf_near")
+
+    def profile(self, enable: bool = True):
+        _check(lib().h2_profile(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
+        _check(lib().h2_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().h2_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().h2_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_profile(enable: bool = True):
+    _check(lib().h2_gemm_profile(int(enable)))
+
+
+def gemm_profile_read():
+    ms, fl, n = _D(), _D(), _I64()
+    _check(lib().h2_gemm_profile_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+    return ms.value, fl.value, n.value
+
+
+def launch_count() -> int:
+    return int(lib().h2_launch_count())
+
+
+def version() -> str:
+    return lib().h2_version().decode()

@@ -1,0 +1,752 @@
+// Construction of the H^2 approximation from Hessian-vector products.
+//
+// Peeling (Section 3.3, Figure 2, weak-admissibility sampling structure):
+//   for l = 1..L, all sibling pairs (a, b) of level l at once:
+//     range pass   Omega: Gaussian on child-0 rows;  Y = H Omega - K Omega  (K: coarser pieces)
+//                  Q_b: orthonormal range of Y[b], grown by b_inc probes until the new
+//                  probes' residuals (I - Q Q^T) y are below tau / (10 sqrt(2/pi))
+//     projection   Psi = [Q_b on child-1 rows];  Z = H Psi - K Psi;  piece H[b,a] ~ Q_b Z[a]^T
+//   leaf pass      identity probes on every leaf -> dense diagonal blocks.
+// Recompression into nested bases (Section 3.2): for every box t, the far block
+// row (far blocks of t and of its ancestors restricted to t) is, grouped by the
+// pair level lp of the sampled piece containing each block, sum_lp P_lp[t] C_lp^T.
+// Its Gram matrix sum_lp P_lp[t] M_lp(t) P_lp[t]^T (M_lp = C_lp^T C_lp, built by
+// a downsweep of per-box Gram matrices) is eigen-decomposed at the leaves and, in
+// the coordinates of the children's bases, at every upper level (upsweep), keeping
+// the directions above the truncation threshold.  Couplings S_ts are products of
+// the projected pieces, near blocks products of the pieces.
+//
+// The host only orchestrates: every arithmetic step runs in the library's kernels.
+#include <algorithm>
+#include <chrono>
+#include <tuple>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "handle.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr int STREAM_PROBE = 1;
+constexpr int STREAM_POWER = 2;
+constexpr int PANEL = 16;
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Pinned {
+    void* p = nullptr;
+    size_t cap = 0;
+    ~Pinned() {
+        if (p) cudaFreeHost(p);
+    }
+    template <class T>
+    T* get(size_t n) {
+        if (n * sizeof(T) > cap) {
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            cap = 0;
+            H2_CUDA(cudaMallocHost(&p, n * sizeof(T) + 64));
+            cap = n * sizeof(T) + 64;
+        }
+        return static_cast<T*>(p);
+    }
+};
+
+class Builder {
+  public:
+    Builder(const h2_tree_s& T, h2_op_fn op, void* ctx, double tol, const h2_build_opts& o)
+        : T_(T), op_(op), ctx_(ctx), tol_(tol), o_(o), s_((cudaStream_t)o.stream) {
+        N_ = T.N;
+        L_ = T.L;
+    }
+
+    void run(h2_handle_s* h);
+
+  private:
+    const h2_tree_s& T_;
+    h2_op_fn op_;
+    void* ctx_;
+    double tol_;
+    h2_build_opts o_;
+    cudaStream_t s_;
+    int64_t N_;
+    int L_;
+
+    DevBuf<int32_t> d_perm_, d_row_leaf_;
+    DevBuf<double> Om_, Yo_, Yt_, Ot_, Tw_, Cw_;
+    DevBuf<double> Pcap_;
+    std::vector<int64_t> pcol_;      // capacity column offset per level
+    std::vector<int> qcap_, qw_;     // capacity and final piece width per level
+    std::vector<std::vector<int>> kb_;  // per level, per pair: columns of Q_b
+    DevBuf<double> Ddiag_;
+    std::vector<int64_t> ddiag_off_;
+    GemmBatch gb_;
+    Stager stg_[4];
+    DevBuf<int64_t> d_i64a_, d_i64b_;
+    DevBuf<int> d_i32a_, d_i32b_, d_i32c_, d_flag_;
+    DevBuf<double> d_red_;
+    DevBuf<BlkDesc> d_blk_;
+    Pinned pin_;
+    int cmax_ = 0;
+    int64_t samples_ = 0, norm_products_ = 0;
+    double t_op_ = 0.0;
+    double norm_ = 0.0, tau_basis_ = 0.0, tau_test_ = 0.0;
+    bool cap_hit_ = false;
+    std::vector<int> range_probes_, proj_probes_;
+
+    void call_op(const double* X, double* Y, int ncols, bool count_sample);
+    void check_flag();
+    double norm_estimate();
+    void subtract(const double* Omt, double* Yt, int c, int lmax);
+    void project(int l, const std::vector<int>& pairs, int c, int c0, int passes);
+    std::vector<double> colnorm(int l, const std::vector<int>& pairs, int c);
+    void panel(int l, const std::vector<int>& pairs, int c0, int w);
+    void identity(int l, const std::vector<int>& pairs);
+    void blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst);
+    void peel_level(int l);
+    void leaf_pass();
+    void assemble(h2_handle_s* h);
+    template <class T>
+    T* dev_list(DevBuf<T>& buf, const std::vector<T>& v, int which) {
+        upload(buf, v, s_, stg_[which & 3]);
+        return buf.p;
+    }
+    double* Pl(int l) { return Pcap_.p + pcol_[l] * N_; }
+    int64_t bstart(int l, int b) const { return T_.start[l][b]; }
+    int bsize(int l, int b) const { return (int)T_.size[l][b]; }
+};
+
+void Builder::call_op(const double* X, double* Y, int ncols, bool count_sample) {
+    if (ncols <= 0) return;
+    const double t0 = now_s();
+    const int r = op_(ctx_, N_, ncols, X, N_, Y, N_, (h2_stream_t)s_);
+    if (r != 0) fail(H2_ERR_OP_FAILED, "Hessian operator returned " + std::to_string(r));
+    t_op_ += now_s() - t0;
+    scan_finite(N_, ncols, Y, N_, d_flag_.p, s_);
+    if (count_sample) samples_ += ncols;
+    else norm_products_ += ncols;
+}
+
+void Builder::check_flag() {
+    int* f = pin_.get<int>(1);
+    H2_CUDA(cudaMemcpyAsync(f, d_flag_.p, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    H2_CUDA(cudaStreamSynchronize(s_));
+    if (*f) fail(H2_ERR_NAN, "non-finite values in Hessian-vector products");
+}
+
+// ||H||_2 by power iteration (Section 3.2) from a Gaussian start vector.
+double Builder::norm_estimate() {
+    double* v = Om_.p;
+    double* w = Yo_.p;
+    gaussian_vector(N_, d_perm_.p, o_.seed, STREAM_POWER, v, s_);
+    auto sqnorm = [&](const double* x) {
+        col_sqnorms(N_, 1, x, N_, d_red_.p, s_);
+        double* hp = pin_.get<double>(1);
+        H2_CUDA(cudaMemcpyAsync(hp, d_red_.p, sizeof(double), cudaMemcpyDeviceToHost, s_));
+        H2_CUDA(cudaStreamSynchronize(s_));
+        return *hp;
+    };
+    auto scale = [&](double* x, double f) {
+        double* hp = pin_.get<double>(1);
+        *hp = f;
+        H2_CUDA(cudaMemcpyAsync(d_red_.p + 1, hp, sizeof(double), cudaMemcpyHostToDevice, s_));
+        scale_cols(N_, 1, x, N_, d_red_.p + 1, s_);
+        H2_CUDA(cudaStreamSynchronize(s_));
+    };
+    const double g = std::sqrt(sqnorm(v));
+    if (!(g > 0.0)) fail(H2_ERR_CUDA, "power iteration: zero start vector");
+    scale(v, 1.0 / g);
+    double lam = 0.0, prev = 0.0;
+    for (int it = 1; it <= o_.norm_maxit; ++it) {
+        call_op(v, w, 1, false);
+        check_flag();
+        lam = std::sqrt(sqnorm(w));
+        if (lam == 0.0) break;
+        scale(w, 1.0 / lam);
+        std::swap(v, w);
+        if (it > 1 && std::fabs(lam - prev) <= o_.norm_rtol * lam) break;
+        prev = lam;
+    }
+    return lam;
+}
+
+void Builder::blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst) {
+    if (d.empty()) return;
+    block_op(kind, (int)d.size(), dev_list(d_blk_, d, 0), src, dst, s_);
+}
+
+// Y -= K Omega for the pieces of levels 1..lmax (tree order, N x c, ld N).
+void Builder::subtract(const double* Omt, double* Yt, int c, int lmax) {
+    for (int lp = 1; lp <= lmax; ++lp) {
+        const int q = qw_[lp];
+        if (q == 0) continue;
+        const double* P = Pl(lp);
+        const int nb = 1 << lp;
+        const int ldt = nb * q;
+        for (int b = 0; b < nb; ++b)
+            gb_.add(P + bstart(lp, b), (int)N_, 1, Omt + bstart(lp, b), (int)N_, 0, Tw_.p + (int64_t)b * q, ldt, q,
+                    c, bsize(lp, b), 1.0, 0.0);
+        gb_.run(s_);
+        for (int i = 0; i < nb / 2; ++i) {
+            const int a = 2 * i, b = 2 * i + 1;
+            gb_.add(P + bstart(lp, b), (int)N_, 0, Tw_.p + (int64_t)a * q, ldt, 0, Yt + bstart(lp, b), (int)N_,
+                    bsize(lp, b), c, q, -1.0, 1.0);
+            gb_.add(P + bstart(lp, a), (int)N_, 0, Tw_.p + (int64_t)b * q, ldt, 0, Yt + bstart(lp, a), (int)N_,
+                    bsize(lp, a), c, q, -1.0, 1.0);
+        }
+        gb_.run(s_);
+    }
+}
+
+// Block Gram-Schmidt projection of columns [c0, c0+c) of Yt[b] against Q_b = P_l[b, 0:kb].
+void Builder::project(int l, const std::vector<int>& pairs, int c, int c0, int passes) {
+    double* P = Pl(l);
+    const int ldc = std::max(qcap_[l], 1);
+    for (int pass = 0; pass < passes; ++pass) {
+        int n = 0;
+        for (int i : pairs) {
+            const int kb = kb_[l][i];
+            if (!kb) { ++n; continue; }
+            const int64_t st = bstart(l, 2 * i + 1);
+            gb_.add(P + st, (int)N_, 1, Yt_.p + st + (int64_t)c0 * N_, (int)N_, 0, Cw_.p + (int64_t)n * ldc * c, ldc,
+                    kb, c, bsize(l, 2 * i + 1), 1.0, 0.0);
+            ++n;
+        }
+        gb_.run(s_);
+        n = 0;
+        for (int i : pairs) {
+            const int kb = kb_[l][i];
+            if (!kb) { ++n; continue; }
+            const int64_t st = bstart(l, 2 * i + 1);
+            gb_.add(P + st, (int)N_, 0, Cw_.p + (int64_t)n * ldc * c, ldc, 0, Yt_.p + st + (int64_t)c0 * N_, (int)N_,
+                    bsize(l, 2 * i + 1), c, kb, -1.0, 1.0);
+            ++n;
+        }
+        gb_.run(s_);
+    }
+}
+
+std::vector<double> Builder::colnorm(int l, const std::vector<int>& pairs, int c) {
+    std::vector<int64_t> off;
+    std::vector<int> m;
+    for (int i : pairs) {
+        off.push_back(bstart(l, 2 * i + 1));
+        m.push_back(bsize(l, 2 * i + 1));
+    }
+    std::vector<double> out(pairs.size(), 0.0);
+    if (pairs.empty()) return out;
+    panel_colnorm_max((int)pairs.size(), dev_list(d_i64a_, off, 1), dev_list(d_i32a_, m, 2), c, Yt_.p, (int)N_,
+                      d_red_.p, s_);
+    double* hp = pin_.get<double>(pairs.size());
+    H2_CUDA(cudaMemcpyAsync(hp, d_red_.p, pairs.size() * sizeof(double), cudaMemcpyDeviceToHost, s_));
+    H2_CUDA(cudaStreamSynchronize(s_));
+    std::memcpy(out.data(), hp, pairs.size() * sizeof(double));
+    return out;
+}
+
+// Appends the panel columns [c0, c0+w) of Yt[b] to Q_b = P_l[b, 0:kb] by block classical
+// Gram-Schmidt with reorthogonalisation (BCGS2; Barlow and Smoktunowicz 2013): project and
+// Householder-QR the panel, then project the orthonormal result once more and QR it again.
+// The second round keeps the new columns orthogonal to Q_b also when the panel is
+// numerically rank deficient (samples of a block whose range is already captured).
+void Builder::panel(int l, const std::vector<int>& pairs, int c0, int w) {
+    if (pairs.empty()) return;
+    std::vector<int64_t> yoff, qoff;
+    std::vector<int> m;
+    std::vector<BlkDesc> back;
+    for (int i : pairs) {
+        const int64_t st = bstart(l, 2 * i + 1);
+        yoff.push_back(st + (int64_t)c0 * N_);
+        qoff.push_back(st + (int64_t)kb_[l][i] * N_);
+        m.push_back(bsize(l, 2 * i + 1));
+        back.push_back(BlkDesc{st + (int64_t)kb_[l][i] * N_, st + (int64_t)c0 * N_, bsize(l, 2 * i + 1), w, (int)N_,
+                               (int)N_});
+    }
+    const int64_t* dy = dev_list(d_i64a_, yoff, 1);
+    const int64_t* dq = dev_list(d_i64b_, qoff, 2);
+    const int* dm = dev_list(d_i32a_, m, 3);
+    for (int round = 0; round < 2; ++round) {
+        project(l, pairs, w, c0, 1);
+        panel_qr((int)pairs.size(), dy, dq, dm, w, Yt_.p, (int)N_, Pl(l), (int)N_, s_);
+        if (round == 0) blocks(BLK_COPY, back, Pl(l), Yt_.p);
+    }
+    for (int i : pairs) kb_[l][i] += w;
+}
+
+// Q_b = I for the given pairs (their range is all of R^|b|).
+void Builder::identity(int l, const std::vector<int>& pairs) {
+    std::vector<BlkDesc> d;
+    for (int i : pairs) {
+        const int m = bsize(l, 2 * i + 1);
+        d.push_back(BlkDesc{0, bstart(l, 2 * i + 1), m, m, 0, (int)N_});
+        kb_[l][i] = m;
+    }
+    blocks(BLK_IDENTITY, d, nullptr, Pl(l));
+}
+
+void Builder::peel_level(int l) {
+    const int npairs = 1 << (l - 1);
+    int mb = 0;
+    for (int i = 0; i < npairs; ++i) mb = std::max(mb, bsize(l, 2 * i + 1));
+    kb_[l].assign(npairs, 0);
+    std::vector<int> all(npairs);
+    for (int i = 0; i < npairs; ++i) all[i] = i;
+    const double thr = tau_test_;
+    int range = 0;
+    auto range_batch = [&](int col0, int c) {
+        probe_fill(N_, c, col0, d_perm_.p, d_row_leaf_.p, L_ - l, o_.seed, STREAM_PROBE, l, Om_.p, Ot_.p, s_);
+        call_op(Om_.p, Yo_.p, c, true);
+        gather_rows(N_, c, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
+        subtract(Ot_.p, Yt_.p, c, l - 1);
+    };
+    // orthonormalise a batch of c new columns of Yt into the bases; returns max residual of the test
+    auto orth_batch = [&](int c, bool test) {
+        std::vector<int> active, full;
+        for (int i : all) {
+            const int m = bsize(l, 2 * i + 1);
+            if (kb_[l][i] >= m) continue;
+            if (kb_[l][i] + c >= m) full.push_back(i);
+            else active.push_back(i);
+        }
+        double err = 0.0;
+        if (test) {
+            std::vector<int> tp = active;
+            tp.insert(tp.end(), full.begin(), full.end());
+            project(l, tp, c, 0, 2);
+            for (double e : colnorm(l, tp, c)) err = std::max(err, e);
+        }
+        identity(l, full);
+        for (int c0 = 0; c0 < c; c0 += PANEL) {
+            const int w = std::min(PANEL, c - c0);
+            panel(l, active, c0, w);
+        }
+        return err;
+    };
+    if (o_.q0 >= mb) {
+        identity(l, all);
+    } else {
+        range_batch(0, o_.q0);
+        orth_batch(o_.q0, false);
+        int q = o_.q0;
+        while (o_.adaptive && q < o_.q_max && q < mb) {
+            const int c = std::min(o_.b_inc, o_.q_max - q);
+            range_batch(q, c);
+            const double err = orth_batch(c, true);
+            q += c;
+            if (err <= thr) break;
+        }
+        range = q;
+        if (o_.adaptive && q >= o_.q_max && q < mb) cap_hit_ = true;
+    }
+    int qp = 0;
+    for (int i : all) qp = std::max(qp, kb_[l][i]);
+    // projection pass: Psi (tree order) is P_l itself (Q_b on child-1 rows, zero elsewhere)
+    double* P = Pl(l);
+    scatter_rows(N_, qp, d_perm_.p, P, N_, Om_.p, N_, s_);
+    call_op(Om_.p, Yo_.p, qp, true);
+    gather_rows(N_, qp, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
+    subtract(P, Yt_.p, qp, l - 1);
+    std::vector<BlkDesc> d;
+    for (int i : all) {
+        const int64_t st = bstart(l, 2 * i);
+        if (kb_[l][i]) d.push_back(BlkDesc{st, st, bsize(l, 2 * i), kb_[l][i], (int)N_, (int)N_});
+    }
+    blocks(BLK_COPY, d, Yt_.p, P);
+    qw_[l] = qp;
+    range_probes_[l] = range;
+    proj_probes_[l] = qp;
+    check_flag();
+}
+
+// Identity probes on every leaf give the dense diagonal blocks once all pieces are removed.
+void Builder::leaf_pass() {
+    const int lm = T_.leaf_max;
+    const int nleaf = 1 << L_;
+    fill_zero(Ot_.p, (size_t)N_ * lm, s_);
+    std::vector<BlkDesc> d;
+    for (int t = 0; t < nleaf; ++t) d.push_back(BlkDesc{0, bstart(L_, t), bsize(L_, t), bsize(L_, t), 0, (int)N_});
+    blocks(BLK_IDENTITY, d, nullptr, Ot_.p);
+    scatter_rows(N_, lm, d_perm_.p, Ot_.p, N_, Om_.p, N_, s_);
+    call_op(Om_.p, Yo_.p, lm, true);
+    gather_rows(N_, lm, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
+    subtract(Ot_.p, Yt_.p, lm, L_);
+    ddiag_off_.assign(nleaf, 0);
+    int64_t tot = 0;
+    for (int t = 0; t < nleaf; ++t) {
+        ddiag_off_[t] = tot;
+        tot += (int64_t)bsize(L_, t) * bsize(L_, t);
+    }
+    Ddiag_.reserve((size_t)tot);
+    d.clear();
+    for (int t = 0; t < nleaf; ++t)
+        d.push_back(BlkDesc{bstart(L_, t), ddiag_off_[t], bsize(L_, t), bsize(L_, t), (int)N_, bsize(L_, t)});
+    blocks(BLK_SYMMETRIZE, d, Yt_.p, Ddiag_.p);
+    check_flag();
+}
+
+// Recompression of the sampled pieces into nested orthonormal bases, couplings and
+// near blocks.
+void Builder::assemble(h2_handle_s* h) {
+    const int L = L_;
+    h->koff.assign(L + 2, 0);
+    for (int l = 0; l <= L + 1; ++l) h->koff[l] = (1LL << l) - 1;
+    h->k.assign((size_t)h->koff[L + 1], 0);
+    std::vector<int64_t> qoff(L + 1, 0);
+    int64_t Q = 0;
+    for (int l = 1; l <= L; ++l) {
+        qoff[l] = Q;
+        Q += qw_[l];
+    }
+    DevBuf<double> Pall, Tall, gram, Gbuf, Utmp, Uhtmp;
+    std::vector<DevBuf<double>> Pi(L + 1);
+    std::vector<std::vector<int64_t>> rowoff(L + 1);
+    std::vector<int64_t> Krows(L + 1, 0);
+    std::vector<int64_t> utmp_off(1 << L, 0), uhtmp_off(h->koff[L], 0);
+    const double thr = tau_basis_ * tau_basis_;
+    DevBuf<int> d_k, d_cap(1);
+    H2_CUDA(cudaMemsetAsync(d_cap.p, 0, sizeof(int), s_));
+    auto K = [&](int l, int b) -> int& { return h->k[h->koff[l] + b]; };
+    auto read_ints = [&](const int* dsrc, int n) {
+        std::vector<int> v(n);
+        if (!n) return v;
+        int* hp = pin_.get<int>(n);
+        H2_CUDA(cudaMemcpyAsync(hp, dsrc, n * sizeof(int), cudaMemcpyDeviceToHost, s_));
+        H2_CUDA(cudaStreamSynchronize(s_));
+        std::memcpy(v.data(), hp, n * sizeof(int));
+        return v;
+    };
+    if (L >= 1 && Q > 0) {
+        // compact the pieces: Pall = [P_1 | P_2 | ... | P_L], N x Q
+        Pall.reserve((size_t)N_ * Q);
+        {
+            std::vector<BlkDesc> d;
+            const int chunk = 2048;
+            for (int l = 1; l <= L; ++l)
+                for (int64_t r = 0; r < N_; r += chunk)
+                    d.push_back(BlkDesc{pcol_[l] * N_ + r, qoff[l] * N_ + r, (int)std::min<int64_t>(chunk, N_ - r),
+                                        qw_[l], (int)N_, (int)N_});
+            blocks(BLK_COPY, d, Pcap_.p, Pall.p);
+        }
+        H2_CUDA(cudaStreamSynchronize(s_));
+        Pcap_.release();
+        Tw_.release();
+        Om_.release(); Yo_.release(); Yt_.release(); Ot_.release();
+        auto Pp = [&](int l, int b, int lp) { return Pall.p + bstart(l, b) + qoff[lp] * N_; };
+
+        // per-box Gram matrices B_lp(s) = P_lp[s]^T P_lp[s] of the column boxes of far blocks,
+        // F_lp(r) = sum of B over r's far blocks, M_lp(t) = sum of F over t and its ancestors
+        using Key = std::tuple<int, int, int>;  // (level, box, lp)
+        std::map<Key, int64_t> boff, foff, moff;
+        std::map<Key, std::vector<int64_t>> flist;
+        int64_t gtot = 0;
+        auto q2 = [&](int lp) { return (int64_t)qw_[lp] * qw_[lp]; };
+        for (int l = 1; l <= L; ++l)
+            for (auto [r, sb] : T_.far[l]) {
+                const int lp = pair_level(l, r, sb);
+                if (!qw_[lp]) continue;
+                Key kb{l, sb, lp};
+                if (!boff.count(kb)) { boff[kb] = gtot; gtot += q2(lp); }
+                flist[Key{l, r, lp}].push_back(boff[kb]);
+            }
+        for (auto& [key, lst] : flist) { foff[key] = gtot; gtot += q2(std::get<2>(key)); }
+        for (int l = 1; l <= L; ++l)
+            for (int t = 0; t < (1 << l); ++t)
+                for (int lp = 1; lp <= l; ++lp) {
+                    if (!qw_[lp]) continue;
+                    const bool has = foff.count(Key{l, t, lp}) || (l - 1 >= lp && moff.count(Key{l - 1, t >> 1, lp}));
+                    if (has) { moff[Key{l, t, lp}] = gtot; gtot += q2(lp); }
+                }
+        gram.reserve((size_t)std::max<int64_t>(gtot, 1));
+        for (auto& [key, off] : boff) {
+            auto [l, sb, lp] = key;
+            const int q = qw_[lp];
+            gb_.add(Pp(l, sb, lp), (int)N_, 1, Pp(l, sb, lp), (int)N_, 0, gram.p + off, q, q, q, bsize(l, sb), 1.0, 0.0);
+        }
+        gb_.run(s_);
+        {
+            std::vector<int64_t> oo, io;
+            std::vector<int> len, bg, en;
+            for (auto& [key, lst] : flist) {
+                oo.push_back(foff[key]);
+                len.push_back((int)q2(std::get<2>(key)));
+                bg.push_back((int)io.size());
+                io.insert(io.end(), lst.begin(), lst.end());
+                en.push_back((int)io.size());
+            }
+            sum_lists((int)oo.size(), dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
+                      dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), gram.p, gram.p, 0, s_);
+            H2_CUDA(cudaStreamSynchronize(s_));
+        }
+        for (int l = 1; l <= L; ++l) {
+            std::vector<int64_t> oo, io;
+            std::vector<int> len, bg, en;
+            for (int t = 0; t < (1 << l); ++t)
+                for (int lp = 1; lp <= l; ++lp) {
+                    auto it = moff.find(Key{l, t, lp});
+                    if (it == moff.end()) continue;
+                    oo.push_back(it->second);
+                    len.push_back((int)q2(lp));
+                    bg.push_back((int)io.size());
+                    auto f = foff.find(Key{l, t, lp});
+                    if (f != foff.end()) io.push_back(f->second);
+                    auto mp = moff.find(Key{l - 1, t >> 1, lp});
+                    if (mp != moff.end()) io.push_back(mp->second);
+                    en.push_back((int)io.size());
+                }
+            sum_lists((int)oo.size(), dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
+                      dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), gram.p, gram.p, 0, s_);
+            H2_CUDA(cudaStreamSynchronize(s_));
+        }
+
+        // leaves: G_t = sum_lp P_lp[t] M_lp(t) P_lp[t]^T, truncated eigen-decomposition
+        const int nleaf = 1 << L;
+        Tall.reserve((size_t)N_ * Q);
+        fill_zero(Tall.p, (size_t)N_ * Q, s_);
+        std::vector<int64_t> goff(nleaf);
+        int64_t gt = 0, ut = 0;
+        for (int t = 0; t < nleaf; ++t) {
+            goff[t] = gt;
+            utmp_off[t] = ut;
+            gt += (int64_t)bsize(L, t) * bsize(L, t);
+            ut += (int64_t)bsize(L, t) * bsize(L, t);
+        }
+        Gbuf.reserve((size_t)gt);
+        Utmp.reserve((size_t)ut);
+        for (int t = 0; t < nleaf; ++t)
+            for (int lp = 1; lp <= L; ++lp) {
+                auto it = moff.find(Key{L, t, lp});
+                if (it == moff.end()) continue;
+                const int q = qw_[lp];
+                gb_.add(Pp(L, t, lp), (int)N_, 0, gram.p + it->second, q, 0,
+                        Tall.p + bstart(L, t) + qoff[lp] * N_, (int)N_, bsize(L, t), q, q, 1.0, 0.0);
+            }
+        gb_.run(s_);
+        for (int t = 0; t < nleaf; ++t)
+            gb_.add(Tall.p + bstart(L, t), (int)N_, 0, Pall.p + bstart(L, t), (int)N_, 1, Gbuf.p + goff[t], bsize(L, t),
+                    bsize(L, t), bsize(L, t), (int)Q, 1.0, 0.0);
+        gb_.run(s_);
+        {
+            std::vector<int> nn(nleaf);
+            for (int t = 0; t < nleaf; ++t) nn[t] = bsize(L, t);
+            d_k.reserve(nleaf);
+            jacobi_eig_trunc(nleaf, dev_list(d_i64a_, goff, 0), dev_list(d_i32a_, nn, 1), Gbuf.p,
+                             dev_list(d_i64b_, utmp_off, 2), Utmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
+            std::vector<int> kk = read_ints(d_k.p, nleaf);
+            for (int t = 0; t < nleaf; ++t) K(L, t) = kk[t];
+        }
+        Tall.release();
+        // projected pieces at the leaves: Pi_L(t) = U_t^T P[t]  (k_t x Q)
+        auto level_rows = [&](int l) {
+            rowoff[l].assign(1 << l, 0);
+            int64_t r = 0;
+            for (int b = 0; b < (1 << l); ++b) { rowoff[l][b] = r; r += K(l, b); }
+            Krows[l] = std::max<int64_t>(r, 1);
+            Pi[l].reserve((size_t)Krows[l] * Q);
+        };
+        level_rows(L);
+        for (int t = 0; t < nleaf; ++t)
+            gb_.add(Utmp.p + utmp_off[t], bsize(L, t), 1, Pall.p + bstart(L, t), (int)N_, 0, Pi[L].p + rowoff[L][t],
+                    (int)Krows[L], K(L, t), (int)Q, bsize(L, t), 1.0, 0.0);
+        gb_.run(s_);
+        // upsweep: every box gets a (2 kmax)^2 slot for its stacked transfer matrices
+        const int nmax = 2 * o_.kmax;
+        Uhtmp.reserve((size_t)std::max<int64_t>((int64_t)h->koff[L] * nmax * nmax, 1));
+        for (int64_t i = 0; i < h->koff[L]; ++i) uhtmp_off[i] = i * nmax * nmax;
+        for (int l = L - 1; l >= 1; --l) {
+            const int nb = 1 << l;
+            const int64_t Kc = Krows[l + 1];
+            DevBuf<double> Tb((size_t)Kc * Q);
+            fill_zero(Tb.p, (size_t)Kc * Q, s_);
+            std::vector<int64_t> go(nb), uo(nb);
+            std::vector<int> nn(nb);
+            int64_t g2 = 0;
+            for (int p = 0; p < nb; ++p) {
+                nn[p] = K(l + 1, 2 * p) + K(l + 1, 2 * p + 1);
+                go[p] = g2;
+                g2 += (int64_t)nn[p] * nn[p];
+                uo[p] = uhtmp_off[h->koff[l] + p];
+            }
+            Gbuf.reserve((size_t)std::max<int64_t>(g2, 1));
+            for (int p = 0; p < nb; ++p) {
+                if (!nn[p]) continue;
+                const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
+                for (int lp = 1; lp <= l; ++lp) {
+                    auto it = moff.find(Key{l, p, lp});
+                    if (it == moff.end()) continue;
+                    const int q = qw_[lp];
+                    gb_.add(V + qoff[lp] * Kc, (int)Kc, 0, gram.p + it->second, q, 0,
+                            Tb.p + rowoff[l + 1][2 * p] + qoff[lp] * Kc, (int)Kc, nn[p], q, q, 1.0, 0.0);
+                }
+            }
+            gb_.run(s_);
+            for (int p = 0; p < nb; ++p) {
+                if (!nn[p]) continue;
+                const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
+                gb_.add(Tb.p + rowoff[l + 1][2 * p], (int)Kc, 0, V, (int)Kc, 1, Gbuf.p + go[p], nn[p], nn[p], nn[p],
+                        (int)Q, 1.0, 0.0);
+            }
+            gb_.run(s_);
+            d_k.reserve(nb);
+            jacobi_eig_trunc(nb, dev_list(d_i64a_, go, 0), dev_list(d_i32a_, nn, 1), Gbuf.p, dev_list(d_i64b_, uo, 2),
+                             Uhtmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
+            std::vector<int> kk = read_ints(d_k.p, nb);
+            for (int p = 0; p < nb; ++p) K(l, p) = kk[p];
+            level_rows(l);
+            for (int p = 0; p < nb; ++p) {
+                if (!nn[p] || !K(l, p)) continue;
+                const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
+                gb_.add(Uhtmp.p + uhtmp_off[h->koff[l] + p], nn[p], 1, V, (int)Kc, 0, Pi[l].p + rowoff[l][p],
+                        (int)Krows[l], K(l, p), (int)Q, nn[p], 1.0, 0.0);
+            }
+            gb_.run(s_);
+        }
+    }
+    // factor layout now that all ranks are known
+    layout_factors(h);
+    double* fac = h->fac64.p;
+    if (L >= 1 && Q > 0) {
+        std::vector<BlkDesc> d;
+        for (int t = 0; t < (1 << L); ++t)
+            if (K(L, t)) d.push_back(BlkDesc{utmp_off[t], h->u_off[t], bsize(L, t), K(L, t), bsize(L, t), bsize(L, t)});
+        blocks(BLK_COPY, d, Utmp.p, fac);
+        d.clear();
+        for (int l = 1; l < L; ++l)
+            for (int p = 0; p < (1 << l); ++p) {
+                const int n = K(l + 1, 2 * p) + K(l + 1, 2 * p + 1), kp = K(l, p);
+                if (n && kp) d.push_back(BlkDesc{uhtmp_off[h->koff[l] + p], h->uh_off[h->koff[l] + p], n, kp, n, n});
+            }
+        blocks(BLK_COPY, d, Uhtmp.p, fac);
+        // couplings S_ts = Pi_lp(t) Pi_lp(s)^T
+        for (int l = 1; l <= L; ++l)
+            for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+                auto [t, sb] = h->far_lower[l][i];
+                const int lp = pair_level(l, t, sb);
+                const int q = qw_[lp];
+                const int64_t Kl = Krows[l];
+                gb_.add(Pi[l].p + rowoff[l][t] + qoff[lp] * Kl, (int)Kl, 0, Pi[l].p + rowoff[l][sb] + qoff[lp] * Kl, (int)Kl,
+                        1, fac + h->s_off[l][i], std::max(K(l, t), 1), K(l, t), K(l, sb), q, 1.0, 0.0);
+            }
+        gb_.run(s_);
+        // off-diagonal near blocks D_ts = P_lp[t] P_lp[s]^T
+        for (size_t i = 0; i < h->near_lower.size(); ++i) {
+            auto [t, sb] = h->near_lower[i];
+            if (t == sb) continue;
+            const int lp = pair_level(L, t, sb);
+            gb_.add(Pall.p + bstart(L, t) + qoff[lp] * N_, (int)N_, 0, Pall.p + bstart(L, sb) + qoff[lp] * N_, (int)N_, 1,
+                    fac + h->d_off[i], bsize(L, t), bsize(L, t), bsize(L, sb), qw_[lp], 1.0, 0.0);
+        }
+        gb_.run(s_);
+    }
+    {
+        std::vector<BlkDesc> d;
+        for (size_t i = 0; i < h->near_lower.size(); ++i) {
+            auto [t, sb] = h->near_lower[i];
+            if (t != sb) continue;
+            d.push_back(BlkDesc{ddiag_off_[t], h->d_off[i], bsize(L, t), bsize(L, t), bsize(L, t), bsize(L, t)});
+        }
+        blocks(BLK_COPY, d, Ddiag_.p, fac);
+    }
+    int cap = read_ints(d_cap.p, 1)[0];
+    if (cap) cap_hit_ = true;
+    H2_CUDA(cudaStreamSynchronize(s_));
+}
+
+void Builder::run(h2_handle_s* h) {
+    const double t0 = now_s();
+    const int nleaf = 1 << L_;
+    if (T_.leaf_max > eig_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: leaf size above 96 is not supported");
+    if (2 * o_.kmax > eig_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: kmax above 48 is not supported");
+    {
+        std::vector<int32_t> perm(N_), rl(N_);
+        for (int64_t i = 0; i < N_; ++i) perm[i] = (int32_t)T_.perm[i];
+        for (int t = 0; t < nleaf; ++t)
+            for (int64_t i = 0; i < T_.size[L_][t]; ++i) rl[T_.start[L_][t] + i] = t;
+        upload(d_perm_, perm, s_, stg_[0]);
+        upload(d_row_leaf_, rl, s_, stg_[1]);
+    }
+    qcap_.assign(L_ + 1, 0);
+    qw_.assign(L_ + 1, 0);
+    pcol_.assign(L_ + 1, 0);
+    kb_.assign(L_ + 1, {});
+    range_probes_.assign(L_ + 1, 0);
+    proj_probes_.assign(L_ + 1, 0);
+    int64_t pc = 0;
+    int qcmax = 1;
+    cmax_ = std::max({o_.q0, o_.b_inc, T_.leaf_max, 1});
+    for (int l = 1; l <= L_; ++l) {
+        int mb = 0;
+        for (int i = 0; i < (1 << (l - 1)); ++i) mb = std::max(mb, bsize(l, 2 * i + 1));
+        qcap_[l] = (o_.q0 >= mb) ? mb : std::min(std::max(o_.q_max, o_.q0), mb);
+        pcol_[l] = pc;
+        pc += qcap_[l];
+        qcmax = std::max(qcmax, qcap_[l]);
+        cmax_ = std::max(cmax_, qcap_[l]);
+    }
+    Om_.reserve((size_t)N_ * cmax_);
+    Yo_.reserve((size_t)N_ * cmax_);
+    Yt_.reserve((size_t)N_ * cmax_);
+    Ot_.reserve((size_t)N_ * cmax_);
+    Tw_.reserve((size_t)(N_ + nleaf) * cmax_);
+    Cw_.reserve((size_t)std::max(1, nleaf / 2) * qcmax * PANEL);
+    Pcap_.reserve((size_t)std::max<int64_t>(N_ * pc, 1));
+    fill_zero(Pcap_.p, (size_t)N_ * pc, s_);
+    d_flag_.reserve(1);
+    H2_CUDA(cudaMemsetAsync(d_flag_.p, 0, sizeof(int), s_));
+    d_red_.reserve(std::max(nleaf, 4) + 4);
+
+    const double tn = now_s();
+    if (o_.norm_est > 0.0) norm_ = o_.norm_est;
+    else norm_ = norm_estimate();
+    const double tn1 = now_s();
+    tau_test_ = tol_ * norm_ / (10.0 * std::sqrt(2.0 / M_PI));
+    tau_basis_ = 2.0 * tol_ * norm_ / std::sqrt((double)nleaf);
+    for (int l = 1; l <= L_; ++l) peel_level(l);
+    leaf_pass();
+    const double tp = now_s();
+    assemble(h);
+    const double ta = now_s();
+
+    h2_stats& st = h->stats;
+    std::memset(&st, 0, sizeof(st));
+    st.n = N_;
+    st.levels = L_;
+    st.leaf_max = T_.leaf_max;
+    st.samples = samples_;
+    st.norm_products = norm_products_;
+    for (int l = 0; l <= L_ && l < H2_MAX_LEVELS; ++l) {
+        st.range_probes[l] = range_probes_[l];
+        st.proj_probes[l] = proj_probes_[l];
+        int mx = 0;
+        for (int b = 0; b < (1 << l); ++b) mx = std::max(mx, h->k[h->koff[l] + b]);
+        st.max_rank[l] = mx;
+    }
+    st.norm_est = norm_;
+    st.tau_basis = tau_basis_;
+    st.tau_test = tau_test_;
+    st.tol_met = cap_hit_ ? 0 : 1;
+    st.t_total = ta - t0;
+    st.t_norm = tn1 - tn;
+    st.t_op = t_op_;
+    st.t_peel = tp - tn1;
+    st.t_assemble = ta - tp;
+}
+
+}  // namespace
+
+int build_handle(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, const h2_build_opts& o,
+                 h2_handle_s* h) {
+    h->tree = std::make_shared<h2_tree_s>(*tree);
+    h->L = tree->L;
+    h->N = tree->N;
+    Builder b(*tree, op, ctx, tol, o);
+    b.run(h);
+    return h->stats.tol_met ? H2_OK : H2_WARN_TOL_NOT_MET;
+}
+
+}  // namespace h2

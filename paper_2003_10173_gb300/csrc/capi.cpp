@@ -1,0 +1,392 @@
+// C ABI of the library: argument validation, error translation, handle life cycle.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+namespace h2 {
+h2_tree_s* make_tree(const double* coords, int64_t N, int dim, int leaf, int adm, double eta);
+int build_handle(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, const h2_build_opts& o,
+                 h2_handle_s* h);
+}  // namespace h2
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guard(F&& f) {
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const h2::Error& e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return H2_ERR_INVALID_ARG;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return H2_ERR_INVALID_ARG;
+    }
+}
+
+void require(bool ok, const char* msg) {
+    if (!ok) h2::fail(H2_ERR_INVALID_ARG, msg);
+}
+
+int64_t level_boxes(int l) { return (int64_t)1 << l; }
+
+}  // namespace
+
+extern "C" {
+
+int h2_build_opts_default(h2_build_opts* o) {
+    if (!o) return H2_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->kmax = 32;
+    o->q0 = 32;
+    o->b_inc = 16;
+    o->q_max = 256;
+    o->adaptive = 1;
+    o->seed = 7;
+    o->norm_est = 0.0;
+    o->norm_maxit = 50;
+    o->norm_rtol = 1e-3;
+    o->keep_fp32 = 0;
+    o->keep_bf16 = 0;
+    o->stream = nullptr;
+    return H2_OK;
+}
+
+int h2_tree_create(const double* coords_host, int64_t n, int dim, int leaf_size, int adm, double eta,
+                   h2_tree_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_tree_create: out is NULL");
+        *out = nullptr;
+        *out = h2::make_tree(coords_host, n, dim, leaf_size, adm, eta);
+        return H2_OK;
+    });
+}
+
+void h2_tree_free(h2_tree_t tree) { delete tree; }
+
+int h2_tree_info(h2_tree_t t, int* levels, int64_t* n, int64_t* n_far, int64_t* n_near) {
+    return guard([&] {
+        require(t != nullptr, "h2_tree_info: NULL tree");
+        if (levels) *levels = t->L;
+        if (n) *n = t->N;
+        if (n_far) {
+            int64_t c = 0;
+            for (auto& f : t->far) c += (int64_t)f.size();
+            *n_far = c;
+        }
+        if (n_near) *n_near = (int64_t)t->near.size();
+        return H2_OK;
+    });
+}
+
+int h2_tree_perm(h2_tree_t t, int64_t* perm_host) {
+    return guard([&] {
+        require(t && perm_host, "h2_tree_perm: NULL argument");
+        std::memcpy(perm_host, t->perm.data(), t->perm.size() * sizeof(int64_t));
+        return H2_OK;
+    });
+}
+
+int h2_tree_boxes(h2_tree_t t, int level, int64_t* starts, int64_t* sizes) {
+    return guard([&] {
+        require(t && starts && sizes, "h2_tree_boxes: NULL argument");
+        require(level >= 0 && level <= t->L, "h2_tree_boxes: level out of range");
+        std::memcpy(starts, t->start[level].data(), t->start[level].size() * sizeof(int64_t));
+        std::memcpy(sizes, t->size[level].data(), t->size[level].size() * sizeof(int64_t));
+        return H2_OK;
+    });
+}
+
+int h2_tree_far(h2_tree_t t, int level, int64_t* count, int32_t* pairs) {
+    return guard([&] {
+        require(t && count, "h2_tree_far: NULL argument");
+        require(level >= 0 && level <= t->L, "h2_tree_far: level out of range");
+        const auto& f = t->far[level];
+        *count = (int64_t)f.size();
+        if (pairs)
+            for (size_t i = 0; i < f.size(); ++i) {
+                pairs[2 * i] = f[i].first;
+                pairs[2 * i + 1] = f[i].second;
+            }
+        return H2_OK;
+    });
+}
+
+int h2_tree_near(h2_tree_t t, int64_t* count, int32_t* pairs) {
+    return guard([&] {
+        require(t && count, "h2_tree_near: NULL argument");
+        *count = (int64_t)t->near.size();
+        if (pairs)
+            for (size_t i = 0; i < t->near.size(); ++i) {
+                pairs[2 * i] = t->near[i].first;
+                pairs[2 * i + 1] = t->near[i].second;
+            }
+        return H2_OK;
+    });
+}
+
+int h2_build(h2_op_fn op, void* ctx, h2_tree_t tree, double tol, const h2_build_opts* opts, h2_handle_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_build: out is NULL");
+        *out = nullptr;
+        require(op != nullptr && tree != nullptr, "h2_build: NULL operator or tree");
+        require(tol > 0.0 && std::isfinite(tol), "h2_build: tol must be positive");
+        h2_build_opts o;
+        h2_build_opts_default(&o);
+        if (opts) o = *opts;
+        require(o.kmax >= 1, "h2_build: kmax must be >= 1");
+        require(o.q0 >= 1 && o.q_max >= 1, "h2_build: probe counts must be >= 1");
+        require(o.b_inc >= 1 && o.b_inc <= 16, "h2_build: b_inc must be in 1..16");
+        require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
+        require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
+        auto* h = new h2_handle_s();
+        try {
+            const cudaStream_t s = (cudaStream_t)o.stream;
+            const int st = h2::build_handle(op, ctx, tree, tol, o, h);
+            std::vector<int32_t> perm(h->N);
+            for (int64_t i = 0; i < h->N; ++i) perm[i] = (int32_t)h->tree->perm[i];
+            h->d_perm.reserve(h->N);
+            H2_CUDA(cudaMemcpy(h->d_perm.p, perm.data(), h->N * sizeof(int32_t), cudaMemcpyHostToDevice));
+            h2::build_plan(h, s);
+            h2::make_copies(h, o.keep_fp32, o.keep_bf16, s);
+            H2_CUDA(cudaStreamSynchronize(s));
+            h->stats.far_lower = 0;
+            for (auto& f : h->far_lower) h->stats.far_lower += (int64_t)f.size();
+            h->stats.near_lower = (int64_t)h->near_lower.size();
+            h->stats.entries_D = h->entries_D;
+            h->stats.entries_S = h->entries_S;
+            h->stats.entries_U = h->entries_U;
+            h->stats.entries_E = h->entries_E;
+            *out = h;
+            return st;
+        } catch (...) {
+            delete h;
+            throw;
+        }
+    });
+}
+
+int h2_import(h2_tree_t tree, const int32_t* ranks, const double* U, const double* E, const double* S,
+              const double* D, int keep_fp32, int keep_bf16, h2_handle_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_import: out is NULL");
+        *out = nullptr;
+        require(tree && ranks, "h2_import: NULL tree or ranks");
+        const int L = tree->L;
+        auto* h = new h2_handle_s();
+        try {
+            h->tree = std::make_shared<h2_tree_s>(*tree);
+            h->L = L;
+            h->N = tree->N;
+            h->koff.assign(L + 2, 0);
+            for (int l = 0; l <= L + 1; ++l) h->koff[l] = ((int64_t)1 << l) - 1;
+            h->k.assign((size_t)h->koff[L + 1], 0);
+            for (size_t i = 0; i < h->k.size(); ++i) {
+                require(ranks[i] >= 0 && ranks[i] <= 96, "h2_import: rank out of range");
+                h->k[i] = ranks[i];
+            }
+            for (int t = 0; t < (1 << L); ++t)
+                require(h->k[h->koff[L] + t] <= tree->size[L][t], "h2_import: leaf rank above leaf size");
+            for (int l = 0; l < L; ++l)
+                for (int p = 0; p < (1 << l); ++p)
+                    require(h->k[h->koff[l] + p] <= h->k[h->koff[l + 1] + 2 * p] + h->k[h->koff[l + 1] + 2 * p + 1],
+                            "h2_import: rank above the children's ranks");
+            require(tree->leaf_max <= 96, "h2_import: leaf size above 96");
+            h2::layout_factors(h);
+            std::vector<double> fac((size_t)std::max<int64_t>(h->fac_entries, 1), 0.0);
+            // leaf bases
+            if (h->entries_U) {
+                require(U != nullptr, "h2_import: NULL U");
+                std::memcpy(fac.data(), U, h->entries_U * sizeof(double));
+            }
+            // transfer matrices: E_c (k_c x k_p, per child, levels 1..L) -> stacked [E_c1; E_c2]
+            {
+                int64_t eo = 0;
+                for (int l = 1; l <= L; ++l)
+                    for (int c = 0; c < (1 << l); ++c) {
+                        const int p = c >> 1;
+                        const int kc = h->k[h->koff[l] + c], kp = h->k[h->koff[l - 1] + p];
+                        const int k1 = h->k[h->koff[l] + 2 * p], k2 = h->k[h->koff[l] + 2 * p + 1];
+                        const int64_t base = h->uh_off[h->koff[l - 1] + p] + ((c & 1) ? k1 : 0);
+                        if (kc && kp) require(E != nullptr, "h2_import: NULL E");
+                        for (int j = 0; j < kp; ++j)
+                            for (int i = 0; i < kc; ++i) fac[base + i + (int64_t)j * (k1 + k2)] = E[eo + i + (int64_t)j * kc];
+                        eo += (int64_t)kc * kp;
+                    }
+            }
+            if (h->entries_S) {
+                require(S != nullptr, "h2_import: NULL S");
+                std::memcpy(fac.data() + h->entries_U + h->entries_E, S, h->entries_S * sizeof(double));
+            }
+            if (h->entries_D) {
+                require(D != nullptr, "h2_import: NULL D");
+                std::memcpy(fac.data() + h->entries_U + h->entries_E + h->entries_S, D, h->entries_D * sizeof(double));
+            }
+            H2_CUDA(cudaMemcpy(h->fac64.p, fac.data(), fac.size() * sizeof(double), cudaMemcpyHostToDevice));
+            std::vector<int32_t> perm(h->N);
+            for (int64_t i = 0; i < h->N; ++i) perm[i] = (int32_t)tree->perm[i];
+            h->d_perm.reserve(h->N);
+            H2_CUDA(cudaMemcpy(h->d_perm.p, perm.data(), h->N * sizeof(int32_t), cudaMemcpyHostToDevice));
+            h2::build_plan(h, nullptr);
+            h2::make_copies(h, keep_fp32, keep_bf16, nullptr);
+            H2_CUDA(cudaDeviceSynchronize());
+            std::memset(&h->stats, 0, sizeof(h->stats));
+            h->stats.n = h->N;
+            h->stats.levels = L;
+            h->stats.leaf_max = tree->leaf_max;
+            h->stats.tol_met = 1;
+            for (int l = 0; l <= L && l < H2_MAX_LEVELS; ++l) {
+                int mx = 0;
+                for (int b = 0; b < (1 << l); ++b) mx = std::max(mx, h->k[h->koff[l] + b]);
+                h->stats.max_rank[l] = mx;
+            }
+            h->stats.far_lower = 0;
+            for (auto& f : h->far_lower) h->stats.far_lower += (int64_t)f.size();
+            h->stats.near_lower = (int64_t)h->near_lower.size();
+            h->stats.entries_D = h->entries_D;
+            h->stats.entries_S = h->entries_S;
+            h->stats.entries_U = h->entries_U;
+            h->stats.entries_E = h->entries_E;
+            *out = h;
+            return H2_OK;
+        } catch (...) {
+            delete h;
+            throw;
+        }
+    });
+}
+
+int h2_factor_sizes(h2_handle_t h, int64_t* n_ranks, int64_t* n_U, int64_t* n_E, int64_t* n_S, int64_t* n_D) {
+    return guard([&] {
+        require(h != nullptr, "h2_factor_sizes: NULL handle");
+        if (n_ranks) *n_ranks = (int64_t)h->k.size();
+        if (n_U) *n_U = h->entries_U;
+        if (n_E) *n_E = h->entries_E;
+        if (n_S) *n_S = h->entries_S;
+        if (n_D) *n_D = h->entries_D;
+        return H2_OK;
+    });
+}
+
+int h2_export(h2_handle_t h, int32_t* ranks, double* U, double* E, double* S, double* D) {
+    return guard([&] {
+        require(h != nullptr, "h2_export: NULL handle");
+        H2_CUDA(cudaDeviceSynchronize());
+        std::vector<double> fac((size_t)std::max<int64_t>(h->fac_entries, 1));
+        if (h->fac_entries)
+            H2_CUDA(cudaMemcpy(fac.data(), h->fac64.p, h->fac_entries * sizeof(double), cudaMemcpyDeviceToHost));
+        if (ranks)
+            for (size_t i = 0; i < h->k.size(); ++i) ranks[i] = h->k[i];
+        if (U && h->entries_U) std::memcpy(U, fac.data(), h->entries_U * sizeof(double));
+        if (E) {
+            int64_t eo = 0;
+            const int L = h->L;
+            for (int l = 1; l <= L; ++l)
+                for (int c = 0; c < (1 << l); ++c) {
+                    const int p = c >> 1;
+                    const int kc = h->k[h->koff[l] + c], kp = h->k[h->koff[l - 1] + p];
+                    const int k1 = h->k[h->koff[l] + 2 * p], k2 = h->k[h->koff[l] + 2 * p + 1];
+                    const int64_t base = h->uh_off[h->koff[l - 1] + p] + ((c & 1) ? k1 : 0);
+                    for (int j = 0; j < kp; ++j)
+                        for (int i = 0; i < kc; ++i) E[eo + i + (int64_t)j * kc] = fac[base + i + (int64_t)j * (k1 + k2)];
+                    eo += (int64_t)kc * kp;
+                }
+        }
+        if (S && h->entries_S) std::memcpy(S, fac.data() + h->entries_U + h->entries_E, h->entries_S * sizeof(double));
+        if (D && h->entries_D)
+            std::memcpy(D, fac.data() + h->entries_U + h->entries_E + h->entries_S, h->entries_D * sizeof(double));
+        return H2_OK;
+    });
+}
+
+int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
+              h2_stream_t stream) {
+    return guard([&] {
+        require(h != nullptr, "h2_matvec: NULL handle");
+        require(nrhs >= 0, "h2_matvec: nrhs < 0");
+        if (nrhs == 0) return H2_OK;
+        require(X != nullptr && Y != nullptr, "h2_matvec: NULL X or Y");
+        require(ldx >= h->N && ldy >= h->N, "h2_matvec: leading dimension smaller than n");
+        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_matvec: unknown mode");
+        h2::run_matvec(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
+int h2_profile(h2_handle_t h, int enable) {
+    return guard([&] {
+        require(h != nullptr, "h2_profile: NULL handle");
+        h->prof = enable ? 1 : 0;
+        return H2_OK;
+    });
+}
+
+int h2_profile_read(h2_handle_t h, double* ms_out, int64_t* launches_out) {
+    return guard([&] {
+        require(h != nullptr, "h2_profile_read: NULL handle");
+        h2::profile_read(h, ms_out, launches_out);
+        return H2_OK;
+    });
+}
+
+int h2_gemm_profile(int enable) {
+    return guard([&] {
+        h2::gemm_profile_enable(enable ? 1 : 0);
+        return H2_OK;
+    });
+}
+
+int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out) {
+    return guard([&] {
+        h2::gemm_profile_read(ms_out, flops_out, launches_out);
+        return H2_OK;
+    });
+}
+
+int h2_get_stats(h2_handle_t h, h2_stats* out) {
+    return guard([&] {
+        require(h && out, "h2_get_stats: NULL argument");
+        *out = h->stats;
+        return H2_OK;
+    });
+}
+
+void h2_free(h2_handle_t h) {
+    if (h) {
+        cudaDeviceSynchronize();
+        delete h;
+    }
+}
+
+const char* h2_error_string(int status) {
+    switch (status) {
+        case H2_OK: return "H2_OK";
+        case H2_ERR_INVALID_ARG: return "H2_ERR_INVALID_ARG";
+        case H2_ERR_CUDA: return "H2_ERR_CUDA";
+        case H2_ERR_OP_FAILED: return "H2_ERR_OP_FAILED";
+        case H2_ERR_NAN: return "H2_ERR_NAN";
+        case H2_ERR_OOM: return "H2_ERR_OOM";
+        case H2_ERR_DEVICE_CHECK: return "H2_ERR_DEVICE_CHECK";
+        case H2_WARN_TOL_NOT_MET: return "H2_WARN_TOL_NOT_MET";
+        default: return "unknown status";
+    }
+}
+
+const char* h2_last_error(void) { return g_last_error.c_str(); }
+
+int64_t h2_launch_count(void) { return h2::g_launches.load(); }
+
+const char* h2_version(void) { return "h2hess 0.1 (sm_103a)"; }
+
+}  // extern "C"

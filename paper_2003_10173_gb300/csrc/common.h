@@ -1,0 +1,179 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/h2.h"
+
+namespace h2 {
+
+// Error carried through the host code as an exception and converted to a
+// status code at the C ABI.
+struct Error : std::runtime_error {
+    int status;
+    Error(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(int status, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define H2_CUDA(call) ::h2::check_cuda((call), #call)
+
+extern std::atomic<int64_t> g_launches;
+// Call after every kernel launch: counts it and turns a launch error into an Error.
+void after_launch(const char* name);
+
+// ---- device memory ---------------------------------------------------------
+// Owning device buffer (cudaMalloc / cudaFree).  Allocation failure -> H2_ERR_OOM.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count);
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // grow to at least count elements (contents are not preserved)
+    void reserve(size_t count) {
+        if (count > n) { release(); alloc(count); }
+    }
+};
+
+void* dev_alloc_bytes(size_t bytes);
+
+template <class T>
+void DevBuf<T>::alloc(size_t count) {
+    n = count;
+    p = count ? static_cast<T*>(dev_alloc_bytes(count * sizeof(T))) : nullptr;
+}
+
+// Pinned host staging area for asynchronous uploads of small host tables (a
+// pageable cudaMemcpyAsync would synchronise the stream).  The buffer is reused
+// only after the previous copy from it has completed.
+struct Stager {
+    void* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    Stager() = default;
+    Stager(const Stager&) = delete;
+    Stager& operator=(const Stager&) = delete;
+    ~Stager();
+    void copy(void* dst, const void* src, size_t bytes, cudaStream_t s);
+};
+
+template <class T>
+void upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s, Stager& st) {
+    d.reserve(h.size());
+    if (!h.empty()) st.copy(d.p, h.data(), h.size() * sizeof(T), s);
+}
+
+// ---- batched FP64 GEMM (gemm.cu) -------------------------------------------
+// C = alpha * op(A) * op(B) + beta * C, column-major, op = transpose if t* != 0.
+struct GemmProb {
+    const double* A;
+    const double* B;
+    double* C;
+    int m, n, k;
+    int lda, ldb, ldc;
+    int ta, tb;
+    double alpha, beta;
+};
+
+// Runs a list of independent problems (their C regions must not overlap) in
+// as few launches as possible; long reductions are split deterministically.
+class GemmBatch {
+  public:
+    void add(const GemmProb& p) {
+        if (p.m > 0 && p.n > 0) probs_.push_back(p);
+    }
+    void add(const double* A, int lda, int ta, const double* B, int ldb, int tb, double* C, int ldc,
+             int m, int n, int k, double alpha, double beta) {
+        add(GemmProb{A, B, C, m, n, k, lda, ldb, ldc, ta, tb, alpha, beta});
+    }
+    size_t size() const { return probs_.size(); }
+    void clear() { probs_.clear(); }
+    void run(cudaStream_t s);
+
+  private:
+    std::vector<GemmProb> probs_;
+    Stager st_probs_, st_tiles_;
+    DevBuf<GemmProb> d_probs_;
+    DevBuf<int4> d_tiles_;
+    DevBuf<double> d_work_;
+    DevBuf<int4> d_red_;
+};
+
+void gemm_profile_enable(int on);
+void gemm_profile_read(double* ms, double* flops, int64_t* launches);
+
+// ---- dense linear-algebra kernels (la.cu) ----------------------------------
+// Householder QR of panels in place with explicit orthonormal factor written to Q.
+// Panel i: m_i x c rows/cols at Y + y_off[i] (ld ldy), Q at Q + q_off[i] (ld ldq).
+void panel_qr(int count, const int64_t* d_y_off, const int64_t* d_q_off, const int* d_m, int c,
+              double* Y, int ldy, double* Q, int ldq, cudaStream_t s);
+// Maximum column 2-norm of each panel: out[i] = max_j ||Y_i[:, j]||.
+void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c, const double* Y,
+                       int ldy, double* out, cudaStream_t s);
+// Symmetric eigen-decomposition (cyclic Jacobi) of count n_i x n_i matrices, keeping the
+// eigenvectors with eigenvalue > thr (at most kmax), sorted descending.
+void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, const double* A,
+                      const int64_t* d_u_off, double* U, int* d_k_out, double thr, int kmax,
+                      int* d_cap_flag, cudaStream_t s);
+
+// ---- small helper kernels (misc.cu) ------------------------------------------
+void fill_zero(double* p, size_t count, cudaStream_t s);
+// Omega (original order, N x ncols, ld N): Gaussian at rows whose tree position is in a
+// child-0 box of `level`, else 0; tree-order copy in Om_tree (may be null).
+void probe_fill(int64_t N, int ncols, int col0, const int32_t* d_perm, const int32_t* d_row_box,
+                int level_shift, uint64_t seed, int stream_id, int level, double* Om_orig,
+                double* Om_tree, cudaStream_t s);
+// power-iteration start vector (tree-order Gaussian) scattered to original order
+void gaussian_vector(int64_t N, const int32_t* d_perm, uint64_t seed, int stream_id, double* x_orig,
+                     cudaStream_t s);
+// dst_tree[i, j] = src_orig[perm[i], j]
+void gather_rows(int64_t N, int ncols, const int32_t* d_perm, const double* src, int64_t lds,
+                 double* dst, int64_t ldd, cudaStream_t s);
+// dst_orig[perm[i], j] = src_tree[i, j]
+void scatter_rows(int64_t N, int ncols, const int32_t* d_perm, const double* src, int64_t lds,
+                  double* dst, int64_t ldd, cudaStream_t s);
+// sum over blocks of |x|^2 and a flag for non-finite values: out[0] += ..., out[1] = 1 if nan
+void scan_finite(int64_t N, int ncols, const double* x, int64_t ld, int* d_flag, cudaStream_t s);
+// out[i] = sum_{j in list i} in[j] for count matrices of size len_i
+void sum_lists(int count, const int64_t* d_out_off, const int* d_len, const int* d_begin,
+               const int* d_end, const int64_t* d_in_off, const double* in, double* out,
+               int accumulate, cudaStream_t s);
+// norms of vectors: out[j] = ||x[:, j]||^2
+void col_sqnorms(int64_t N, int ncols, const double* x, int64_t ld, double* out, cudaStream_t s);
+void scale_cols(int64_t N, int ncols, double* x, int64_t ld, const double* d_scale, cudaStream_t s);
+
+// Block descriptors for copies between matrices with explicit offsets and leading dimensions.
+struct BlkDesc {
+    int64_t src_off;
+    int64_t dst_off;
+    int rows, cols;
+    int lds, ldd;
+};
+enum { BLK_COPY = 0, BLK_IDENTITY = 1, BLK_SYMMETRIZE = 2 };
+// COPY: dst = src; IDENTITY: dst = I (src unused); SYMMETRIZE: dst = (src + src^T)/2 (square)
+void block_op(int kind, int count, const BlkDesc* d_desc, const double* src, double* dst, cudaStream_t s);
+uint64_t rng_key(uint64_t seed, int stream_id, int level);
+int eig_max_order();
+
+}  // namespace h2

@@ -1,0 +1,108 @@
+// Built H^2 matrix: factor storage, offsets and the matvec plan.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <memory>
+
+#include "common.h"
+#include "tree.h"
+
+namespace h2 {
+
+// One product of a matvec stage: out_block += op(M) * in_block.
+// op(M) is rows x cols; M at factor offset m_off with leading dimension ldm,
+// transposed if trans.  The input block starts at row in_off of the input buffer.
+struct MvItem {
+    int64_t m_off;
+    int64_t in_off;
+    int ldm;
+    int rows, cols;
+    int trans;
+    int in_ld;
+};
+
+// One output block of a stage with its list of items [beg, end).
+struct MvOut {
+    int64_t out_off;
+    int out_ld;
+    int rows;
+    int beg, end;
+};
+
+// A stage: its outputs write internal coefficient buffers, or the caller's Y via
+// the tree permutation; its inputs read internal buffers, or the caller's X.
+struct MvStage {
+    int kind = 0;           // H2_STAGE_* of this stage
+    std::vector<MvOut> outs;
+    std::vector<MvItem> items;
+    int out_to_y = 0;       // outputs are rows of Y (tree positions, scattered by perm)
+    int in_from_x = 0;      // bit 0: items with in_ld < 0 read X through perm
+    int accumulate = 0;     // add to the existing output instead of overwriting
+    DevBuf<MvOut> d_outs;
+    DevBuf<MvItem> d_items;
+    int max_rows = 0, max_cols = 0;
+};
+
+struct MatvecPlan {
+    std::vector<MvStage> stages;
+    int64_t ws_rows = 0;     // rows of the internal coefficient workspace (per right-hand side)
+};
+
+struct Workspace {
+    DevBuf<double> f64;
+    DevBuf<float> f32;
+    int64_t nrhs_cap = 0;
+};
+
+}  // namespace h2
+
+struct h2_handle_s {
+    std::shared_ptr<h2_tree_s> tree;
+    int L = 0;
+    int64_t N = 0;
+    // ranks of every box: k[koff[l] + box]
+    std::vector<int> k;
+    std::vector<int64_t> koff;
+    // factor offsets into fac (entries)
+    std::vector<int64_t> u_off;              // per leaf: |t| x k_t, ld |t|
+    std::vector<int64_t> uh_off;             // per box at levels 0..L-1 with children: (k_c1+k_c2) x k_p, ld k_c1+k_c2
+    std::vector<std::vector<std::pair<int, int>>> far_lower;  // [level] (t, s), t > s
+    std::vector<std::vector<int64_t>> s_off;                  // [level][i]: k_t x k_s, ld k_t
+    std::vector<std::pair<int, int>> near_lower;              // (t, s), t >= s
+    std::vector<int64_t> d_off;                                // |t| x |s|, ld |t|
+    int64_t fac_entries = 0;
+    h2::DevBuf<double> fac64;
+    h2::DevBuf<float> fac32;
+    h2::DevBuf<__nv_bfloat16> fac16;
+    h2::DevBuf<int32_t> d_perm;
+    h2::MatvecPlan plan;
+    h2::Workspace ws;
+    h2_stats stats{};
+    // per-stage timing (h2_profile)
+    int prof = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    double prof_ms[H2_STAGE_COUNT] = {0};
+    int64_t prof_n[H2_STAGE_COUNT] = {0};
+    ~h2_handle_s() {
+        for (auto e : ev_pool) cudaEventDestroy(e);
+        for (auto& u : ev_used) {
+            cudaEventDestroy(u.second.first);
+            cudaEventDestroy(u.second.second);
+        }
+    }
+    int64_t entries_U = 0, entries_E = 0, entries_S = 0, entries_D = 0;
+};
+
+namespace h2 {
+// Computes factor offsets from k (and the tree), allocates fac64.
+void layout_factors(h2_handle_s* h);
+// Builds and uploads the matvec plan from the factor layout.
+void build_plan(h2_handle_s* h, cudaStream_t s);
+// Creates the requested reduced-precision copies of the factors.
+void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s);
+void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+                int mode, cudaStream_t s);
+void profile_read(h2_handle_s* h, double* ms, int64_t* n);
+}  // namespace h2

@@ -1,0 +1,410 @@
+// Multi-right-hand-side H^2 matvec (Section 3.2, Eq. (3.2)).
+//
+//   Y = D X + U (S (U^T X))
+//
+// in five marshaled stages, each a list of small block products grouped by
+// output block (one CTA per output block and right-hand-side tile; no atomics,
+// so results are deterministic):
+//   1. leaf upsweep      xh_t = U_t^T X_t                    (X read through the tree permutation)
+//   2. upsweep           xh_p = E_c1^T xh_c1 + E_c2^T xh_c2   (one stage per level, leaves to root)
+//   3. couplings         yh_t = sum_s S_ts xh_s                (all levels in one stage)
+//   4. downsweep         yh_c += E_c yh_p                      (one stage per level, root to leaves)
+//   5. leaf expansion    Y_t = U_t yh_t + sum_s D_ts X_s       (written through the permutation)
+// Only the lower triangle of S and D is stored; upper blocks are used as
+// transposes of the stored ones.
+#include <algorithm>
+
+#include "handle.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int RMAX = 96;     // largest block dimension (leaf size / rank)
+constexpr int RT = 32;       // right-hand sides per CTA
+constexpr int OPT = (RMAX * RT + NT - 1) / NT;
+
+template <class T> __device__ __forceinline__ float to_f(T x);
+template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class TA, class T> __device__ __forceinline__ TA cvt(T x) { return (TA)to_f<T>(x); }
+template <> __device__ __forceinline__ double cvt<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
+
+// TS: factor storage type, TX: type of X, TY: type of Y, TA: arithmetic / workspace type.
+template <class TS, class TX, class TY, class TA>
+__global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ outs,
+                                                       const MvItem* __restrict__ items,
+                                                       const TS* __restrict__ fac, TA* __restrict__ ws,
+                                                       int64_t ws_ld, const int32_t* __restrict__ perm,
+                                                       const TX* __restrict__ X, int64_t ldx,
+                                                       TY* __restrict__ Y, int64_t ldy, int nrhs,
+                                                       int out_to_y, int accumulate) {
+    extern __shared__ unsigned char smem_raw[];
+    TA* Ms = reinterpret_cast<TA*>(smem_raw);             // [RMAX cols][RMAX+1 rows] column-major
+    TA* IN = Ms + RMAX * (RMAX + 1);                        // [RMAX rows][RT]
+    const MvOut o = outs[blockIdx.x];
+    const int r0 = blockIdx.y * RT;
+    const int nr = min(RT, nrhs - r0);
+    const int rows = o.rows;
+    const int nel = rows * nr;
+    TA acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) acc[q] = (TA)0;
+
+    for (int it = o.beg; it < o.end; ++it) {
+        const MvItem m = items[it];
+        const int cols = m.cols;
+        const TS* M = fac + m.m_off;
+        const bool tr = (m.trans & 1) != 0;
+        // op(M) into Ms (column j at Ms + j*(RMAX+1))
+        const int ne = rows * cols;
+        for (int e = threadIdx.x; e < ne; e += NT) {
+            int i, j;
+            if (!tr) { i = e % rows; j = e / rows; }   // contiguous along i
+            else     { j = e % cols; i = e / cols; }   // contiguous along j
+            const TS v = tr ? M[j + (int64_t)i * m.ldm] : M[i + (int64_t)j * m.ldm];
+            Ms[j * (RMAX + 1) + i] = cvt<TA>(v);
+        }
+        const int ni = cols * nr;
+        if (m.trans & 2) {
+            for (int e = threadIdx.x; e < ni; e += NT) {
+                const int j = e % cols, r = e / cols;
+                IN[j * RT + r] = cvt<TA>(X[perm[m.in_off + j] + (int64_t)(r0 + r) * ldx]);
+            }
+        } else {
+            for (int e = threadIdx.x; e < ni; e += NT) {
+                const int j = e % cols, r = e / cols;
+                IN[j * RT + r] = ws[m.in_off + j + (int64_t)(r0 + r) * ws_ld];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            const int e = threadIdx.x + q * NT;
+            if (e < nel) {
+                const int i = e % rows, r = e / rows;
+                TA s = acc[q];
+                for (int j = 0; j < cols; ++j) s = fma(Ms[j * (RMAX + 1) + i], IN[j * RT + r], s);
+                acc[q] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int e = threadIdx.x + q * NT;
+        if (e < nel) {
+            const int i = e % rows, r = e / rows;
+            if (out_to_y) {
+                TY* y = Y + perm[o.out_off + i] + (int64_t)(r0 + r) * ldy;
+                *y = accumulate ? (TY)(*y + acc[q]) : (TY)acc[q];
+            } else {
+                TA* y = ws + o.out_off + i + (int64_t)(r0 + r) * ws_ld;
+                *y = accumulate ? (TA)(*y + acc[q]) : acc[q];
+            }
+        }
+    }
+}
+
+template <class TS, class TA>
+__global__ void convert_kernel(const double* __restrict__ src, TS* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (TS)src[i];
+}
+template <>
+__global__ void convert_kernel<__nv_bfloat16, float>(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn((float)src[i]);
+}
+
+template <class TS, class TX, class TY, class TA>
+void launch_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm,
+                  const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
+    if (st.outs.empty()) return;
+    const size_t smem = (size_t)(RMAX * (RMAX + 1) + RMAX * RT) * sizeof(TA);
+    static bool attr = false;
+    if (!attr) {
+        H2_CUDA(cudaFuncSetAttribute(mv_stage_kernel<TS, TX, TY, TA>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    dim3 grid((unsigned)st.outs.size(), (unsigned)((nrhs + RT - 1) / RT));
+    mv_stage_kernel<TS, TX, TY, TA><<<grid, NT, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, perm,
+                                                           X, ldx, Y, ldy, nrhs, st.out_to_y, st.accumulate);
+    after_launch("mv_stage");
+}
+
+cudaEvent_t take_event(h2_handle_s* h) {
+    if (h->ev_pool.empty()) {
+        cudaEvent_t e;
+        H2_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+}
+
+template <class TS, class TX, class TY, class TA>
+void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy,
+             int nrhs, cudaStream_t s) {
+    for (const MvStage& st : h->plan.stages) {
+        if (h->prof && !st.outs.empty()) {
+            cudaEvent_t a = take_event(h), b = take_event(h);
+            H2_CUDA(cudaEventRecord(a, s));
+            launch_stage<TS, TX, TY, TA>(st, fac, ws, h->plan.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+            H2_CUDA(cudaEventRecord(b, s));
+            h->ev_used.push_back({st.kind, {a, b}});
+        } else {
+            launch_stage<TS, TX, TY, TA>(st, fac, ws, h->plan.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+        }
+    }
+}
+
+}  // namespace
+
+void layout_factors(h2_handle_s* h) {
+    const h2_tree_s& T = *h->tree;
+    const int L = T.L;
+    int64_t off = 0;
+    h->u_off.assign((size_t)1 << L, 0);
+    for (int t = 0; t < (1 << L); ++t) {
+        h->u_off[t] = off;
+        off += T.size[L][t] * h->k[h->koff[L] + t];
+    }
+    h->entries_U = off;
+    h->uh_off.assign(h->koff[L], 0);  // boxes of levels 0..L-1
+    for (int l = 0; l < L; ++l)
+        for (int p = 0; p < (1 << l); ++p) {
+            const int kc = h->k[h->koff[l + 1] + 2 * p] + h->k[h->koff[l + 1] + 2 * p + 1];
+            h->uh_off[h->koff[l] + p] = off;
+            off += (int64_t)kc * h->k[h->koff[l] + p];
+        }
+    h->entries_E = off - h->entries_U;
+    const int64_t s0 = off;
+    h->far_lower.assign(L + 1, {});
+    h->s_off.assign(L + 1, {});
+    for (int l = 1; l <= L; ++l)
+        for (auto [t, s] : T.far[l])
+            if (t > s) {
+                h->far_lower[l].push_back({t, s});
+                h->s_off[l].push_back(off);
+                off += (int64_t)h->k[h->koff[l] + t] * h->k[h->koff[l] + s];
+            }
+    h->entries_S = off - s0;
+    const int64_t d0 = off;
+    h->near_lower.clear();
+    h->d_off.clear();
+    for (auto [t, s] : T.near)
+        if (t >= s) {
+            h->near_lower.push_back({t, s});
+            h->d_off.push_back(off);
+            off += T.size[L][t] * T.size[L][s];
+        }
+    h->entries_D = off - d0;
+    h->fac_entries = off;
+    h->fac64.reserve((size_t)std::max<int64_t>(off, 1));
+}
+
+void build_plan(h2_handle_s* h, cudaStream_t s) {
+    const h2_tree_s& T = *h->tree;
+    const int L = T.L;
+    auto K = [&](int l, int b) { return h->k[h->koff[l] + b]; };
+    // coefficient workspace rows: xh levels then yh levels
+    std::vector<int64_t> box_row(h->k.size());
+    int64_t rows = 0;
+    for (size_t i = 0; i < h->k.size(); ++i) {
+        box_row[i] = rows;
+        rows += h->k[i];
+    }
+    const int64_t ytop = rows;
+    rows *= 2;
+    h->plan.ws_rows = std::max<int64_t>(rows, 1);
+    auto xrow = [&](int l, int b) { return box_row[h->koff[l] + b]; };
+    auto yrow = [&](int l, int b) { return ytop + box_row[h->koff[l] + b]; };
+    const int64_t wld = h->plan.ws_rows;
+    h->plan.stages.clear();
+    auto new_stage = [&]() -> MvStage& {
+        h->plan.stages.emplace_back();
+        return h->plan.stages.back();
+    };
+    auto add_out = [&](MvStage& st, int64_t off, int nrows) {
+        st.outs.push_back(MvOut{off, (int)wld, nrows, (int)st.items.size(), (int)st.items.size()});
+    };
+    auto add_item = [&](MvStage& st, int64_t moff, int ldm, int r, int c, int trans, int64_t in_off) {
+        if (r <= 0 || c <= 0) return;
+        st.items.push_back(MvItem{moff, in_off, ldm, r, c, trans, (int)wld});
+        st.outs.back().end = (int)st.items.size();
+    };
+    if (L >= 1) {
+        // 1. leaf upsweep
+        {
+            MvStage& st = new_stage();
+            st.kind = H2_STAGE_LEAF_UP;
+            for (int t = 0; t < (1 << L); ++t) {
+                const int kt = K(L, t), m = (int)T.size[L][t];
+                if (!kt) continue;
+                add_out(st, xrow(L, t), kt);
+                add_item(st, h->u_off[t], m, kt, m, 1 | 2, T.start[L][t]);
+            }
+        }
+        // 2. upsweep
+        for (int l = L - 1; l >= 1; --l) {
+            MvStage& st = new_stage();
+            st.kind = H2_STAGE_UP;
+            for (int p = 0; p < (1 << l); ++p) {
+                const int kp = K(l, p);
+                if (!kp) continue;
+                const int k1 = K(l + 1, 2 * p), k2 = K(l + 1, 2 * p + 1);
+                add_out(st, xrow(l, p), kp);
+                const int64_t uo = h->uh_off[h->koff[l] + p];
+                add_item(st, uo, k1 + k2, kp, k1, 1, xrow(l + 1, 2 * p));
+                add_item(st, uo + k1, k1 + k2, kp, k2, 1, xrow(l + 1, 2 * p + 1));
+            }
+        }
+        // 3. couplings (every box with a basis gets an output so that yh starts at zero)
+        {
+            MvStage& st = new_stage();
+            st.kind = H2_STAGE_COUPLE;
+            for (int l = 1; l <= L; ++l) {
+                std::vector<std::vector<int>> far_of(1 << l);
+                std::vector<std::vector<int64_t>> mo(1 << l);
+                std::vector<std::vector<int>> tr(1 << l);
+                for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+                    auto [t, s2] = h->far_lower[l][i];
+                    far_of[t].push_back(s2); mo[t].push_back(h->s_off[l][i]); tr[t].push_back(0);
+                    far_of[s2].push_back(t); mo[s2].push_back(h->s_off[l][i]); tr[s2].push_back(1);
+                }
+                for (int t = 0; t < (1 << l); ++t) {
+                    const int kt = K(l, t);
+                    if (!kt) continue;
+                    add_out(st, yrow(l, t), kt);
+                    for (size_t j = 0; j < far_of[t].size(); ++j) {
+                        const int sb = far_of[t][j], ks = K(l, sb);
+                        // stored block is (max, min): k_max x k_min with ld k_max
+                        const int ldm = tr[t][j] ? ks : kt;
+                        add_item(st, mo[t][j], ldm, kt, ks, tr[t][j], xrow(l, sb));
+                    }
+                }
+            }
+        }
+        // 4. downsweep
+        for (int l = 1; l <= L - 1; ++l) {
+            MvStage& st = new_stage();
+            st.kind = H2_STAGE_DOWN;
+            st.accumulate = 1;
+            for (int c = 0; c < (1 << (l + 1)); ++c) {
+                const int kc = K(l + 1, c), p = c >> 1, kp = K(l, p);
+                if (!kc || !kp) continue;
+                const int k1 = K(l + 1, 2 * p), k2 = K(l + 1, 2 * p + 1);
+                add_out(st, yrow(l + 1, c), kc);
+                const int64_t uo = h->uh_off[h->koff[l] + p] + ((c & 1) ? k1 : 0);
+                add_item(st, uo, k1 + k2, kc, kp, 0, yrow(l, p));
+            }
+        }
+    }
+    // 5. leaf expansion and near field, written to Y
+    {
+        MvStage& st = new_stage();
+        st.kind = H2_STAGE_LEAF_NEAR;
+        st.out_to_y = 1;
+        std::vector<std::vector<int>> near_of(1 << L);
+        std::vector<std::vector<int64_t>> mo(1 << L);
+        std::vector<std::vector<int>> tr(1 << L);
+        for (size_t i = 0; i < h->near_lower.size(); ++i) {
+            auto [t, s2] = h->near_lower[i];
+            near_of[t].push_back(s2); mo[t].push_back(h->d_off[i]); tr[t].push_back(0);
+            if (t != s2) { near_of[s2].push_back(t); mo[s2].push_back(h->d_off[i]); tr[s2].push_back(1); }
+        }
+        for (int t = 0; t < (1 << L); ++t) {
+            const int m = (int)T.size[L][t];
+            st.outs.push_back(MvOut{T.start[L][t], 0, m, (int)st.items.size(), (int)st.items.size()});
+            if (L >= 1) add_item(st, h->u_off[t], m, m, K(L, t), 0, yrow(L, t));
+            for (size_t j = 0; j < near_of[t].size(); ++j) {
+                const int sb = near_of[t][j], ms = (int)T.size[L][sb];
+                const int ldm = tr[t][j] ? ms : m;
+                add_item(st, mo[t][j], ldm, m, ms, tr[t][j] | 2, T.start[L][sb]);
+            }
+        }
+    }
+    Stager stg;
+    for (MvStage& st : h->plan.stages) {
+        for (auto& it : st.items) {
+            if (it.rows > RMAX || it.cols > RMAX) fail(H2_ERR_INVALID_ARG, "matvec: block larger than 96");
+        }
+        upload(st.d_outs, st.outs, s, stg);
+        upload(st.d_items, st.items, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+void profile_read(h2_handle_s* h, double* ms, int64_t* n) {
+    H2_CUDA(cudaDeviceSynchronize());
+    for (auto& u : h->ev_used) {
+        float t = 0.f;
+        H2_CUDA(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        h->prof_ms[u.first] += t;
+        h->prof_n[u.first] += 1;
+        h->ev_pool.push_back(u.second.first);
+        h->ev_pool.push_back(u.second.second);
+    }
+    h->ev_used.clear();
+    for (int k = 0; k < H2_STAGE_COUNT; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (n) n[k] = h->prof_n[k];
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+}
+
+void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s) {
+    const int64_t n = std::max<int64_t>(h->fac_entries, 1);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + NT - 1) / NT, 152 * 16);
+    if (keep_fp32) {
+        h->fac32.reserve(n);
+        convert_kernel<float, float><<<grid, NT, 0, s>>>(h->fac64.p, h->fac32.p, n);
+        after_launch("convert_fp32");
+    }
+    if (keep_bf16) {
+        h->fac16.reserve(n);
+        convert_kernel<__nv_bfloat16, float><<<grid, NT, 0, s>>>(h->fac64.p, h->fac16.p, n);
+        after_launch("convert_bf16");
+    }
+}
+
+void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+                int mode, cudaStream_t s) {
+    if (nrhs <= 0) return;
+    if (nrhs > (1 << 24)) fail(H2_ERR_INVALID_ARG, "h2_matvec: nrhs too large");
+    const int64_t need = h->plan.ws_rows * nrhs;
+    switch (mode) {
+        case H2_FP64: {
+            h->ws.f64.reserve((size_t)need);
+            run_all<double, double, double, double>(h, h->fac64.p, h->ws.f64.p, (const double*)X, ldx,
+                                                    (double*)Y, ldy, (int)nrhs, s);
+            break;
+        }
+        case H2_FP32: {
+            if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: FP32 copy of the factors was not kept");
+            h->ws.f32.reserve((size_t)need);
+            run_all<float, float, float, float>(h, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y,
+                                                ldy, (int)nrhs, s);
+            break;
+        }
+        case H2_BF16: {
+            if (!h->fac16.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: BF16 copy of the factors was not kept");
+            h->ws.f32.reserve((size_t)need);
+            run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, h->ws.f32.p,
+                                                                (const __nv_bfloat16*)X, ldx, (float*)Y, ldy,
+                                                                (int)nrhs, s);
+            break;
+        }
+        default:
+            fail(H2_ERR_INVALID_ARG, "h2_matvec: mode not supported");
+    }
+}
+
+}  // namespace h2

@@ -1,0 +1,187 @@
+// Hessian operators shipped with the library (callbacks of type h2_op_fn).
+//
+// heat2d: misfit Hessian of initial-condition inversion for the heat equation
+// on the unit square, H = F diag(mask) F / sigma^2 with F = exp(T kappa Lap_h)
+// (5-point Dirichlet Laplacian on the n x n interior grid), applied exactly by
+// the orthonormal type-I sine transform S: with the vector x read as the
+// column-major n x n array X (X[j, i] = x[i n + j]),
+//     F x  <->  S (Lambda .* (S X S)) S,   Lambda[a, b] = exp(-T kappa (mu_a + mu_b)),
+// mu_a = (4/h^2) sin^2(a pi h / 2).  Every transform is a pair of FP64 GEMMs.
+//
+// dense: Y = A X with a caller-owned dense matrix.
+#include <cmath>
+
+#include "common.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr int NT = 256;
+
+__global__ void scale_by_kernel(double* __restrict__ x, const double* __restrict__ f, int64_t per, int64_t total,
+                                double c) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] *= c * f[e % per];
+}
+
+__global__ void store_kernel(const double* __restrict__ src, int64_t N, int64_t nrhs, double c, double* __restrict__ Y,
+                             int64_t ldy) {
+    const int64_t total = N * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % N, r = e / N;
+        Y[i + r * ldy] = c * src[e];
+    }
+}
+
+unsigned grid_for(int64_t total) {
+    int64_t b = (total + NT - 1) / NT;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+struct Heat2d {
+    int n = 0;
+    double inv_s2 = 0.0;
+    DevBuf<double> S, lam, mask, W1, W2;
+    GemmBatch gb;
+};
+
+// B <- F B for B = N x c contiguous; uses W as scratch.  Result in B.
+void apply_F(Heat2d& H, double* B, double* W, int64_t c, cudaStream_t s) {
+    const int n = H.n;
+    const int64_t n2 = (int64_t)n * n;
+    for (int pass = 0; pass < 2; ++pass) {
+        // W = S * B_view  (n x n*c)
+        H.gb.add(H.S.p, n, 0, B, n, 0, W, n, n, (int)(n * c), n, 1.0, 0.0);
+        H.gb.run(s);
+        // B_r = W_r * S
+        for (int64_t r = 0; r < c; ++r) H.gb.add(W + r * n2, n, 0, H.S.p, n, 0, B + r * n2, n, n, n, n, 1.0, 0.0);
+        H.gb.run(s);
+        if (pass == 0) {
+            scale_by_kernel<<<grid_for(n2 * c), NT, 0, s>>>(B, H.lam.p, n2, n2 * c, 1.0);
+            after_launch("heat_lambda");
+        }
+    }
+}
+
+struct DenseOp {
+    const double* A = nullptr;
+    int64_t n = 0, lda = 0;
+    GemmBatch gb;
+};
+
+}  // namespace
+
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+int h2_heat2d_create(int n, double kappa, double T, double sigma, const double* mask_host, void** ctx_out) {
+    if (!ctx_out) return H2_ERR_INVALID_ARG;
+    *ctx_out = nullptr;
+    if (n < 1 || n > 4096 || !(kappa >= 0.0) || !(T >= 0.0) || !(sigma > 0.0) || !mask_host) return H2_ERR_INVALID_ARG;
+    Heat2d* H = nullptr;
+    try {
+        H = new Heat2d();
+        H->n = n;
+        H->inv_s2 = 1.0 / (sigma * sigma);
+        const double h = 1.0 / (n + 1);
+        std::vector<double> S((size_t)n * n), lam((size_t)n * n), mu(n);
+        for (int a = 0; a < n; ++a) {
+            mu[a] = (4.0 / (h * h)) * std::pow(std::sin(0.5 * M_PI * h * (a + 1)), 2);
+            for (int b = 0; b < n; ++b) S[a + (size_t)b * n] = std::sqrt(2.0 * h) * std::sin(M_PI * h * (double)(a + 1) * (b + 1));
+        }
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) lam[a + (size_t)b * n] = std::exp(-T * kappa * (mu[a] + mu[b]));
+        const int64_t N = (int64_t)n * n;
+        H->S.reserve(S.size());
+        H->lam.reserve(lam.size());
+        H->mask.reserve(N);
+        H2_CUDA(cudaMemcpy(H->S.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+        H2_CUDA(cudaMemcpy(H->lam.p, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+        H2_CUDA(cudaMemcpy(H->mask.p, mask_host, N * sizeof(double), cudaMemcpyHostToDevice));
+        *ctx_out = H;
+        return H2_OK;
+    } catch (const Error& e) {
+        delete H;
+        return e.status;
+    } catch (...) {
+        delete H;
+        return H2_ERR_OOM;
+    }
+}
+
+int h2_heat2d_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                    h2_stream_t stream) {
+    auto* H = static_cast<Heat2d*>(ctx);
+    if (!H || n != (int64_t)H->n * H->n || nrhs < 0 || ldx < n || ldy < n) return H2_ERR_INVALID_ARG;
+    if (nrhs == 0) return H2_OK;
+    if (!X || !Y) return H2_ERR_INVALID_ARG;
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        H->W1.reserve((size_t)n * nrhs);
+        H->W2.reserve((size_t)n * nrhs);
+        H2_CUDA(cudaMemcpy2DAsync(H->W1.p, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), nrhs,
+                                  cudaMemcpyDeviceToDevice, s));
+        apply_F(*H, H->W1.p, H->W2.p, nrhs, s);
+        scale_by_kernel<<<grid_for(n * nrhs), NT, 0, s>>>(H->W1.p, H->mask.p, n, n * nrhs, 1.0);
+        after_launch("heat_mask");
+        apply_F(*H, H->W1.p, H->W2.p, nrhs, s);
+        store_kernel<<<grid_for(n * nrhs), NT, 0, s>>>(H->W1.p, n, nrhs, H->inv_s2, Y, ldy);
+        after_launch("heat_store");
+        return H2_OK;
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        return H2_ERR_CUDA;
+    }
+}
+
+void h2_heat2d_destroy(void* ctx) {
+    if (ctx) {
+        cudaDeviceSynchronize();
+        delete static_cast<Heat2d*>(ctx);
+    }
+}
+
+int h2_dense_op_create(const double* A, int64_t n, int64_t lda, void** ctx_out) {
+    if (!ctx_out) return H2_ERR_INVALID_ARG;
+    *ctx_out = nullptr;
+    if (!A || n < 1 || lda < n || n >= (1 << 22)) return H2_ERR_INVALID_ARG;
+    auto* D = new (std::nothrow) DenseOp();
+    if (!D) return H2_ERR_OOM;
+    D->A = A;
+    D->n = n;
+    D->lda = lda;
+    *ctx_out = D;
+    return H2_OK;
+}
+
+int h2_dense_op_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                      h2_stream_t stream) {
+    auto* D = static_cast<DenseOp*>(ctx);
+    if (!D || n != D->n || nrhs < 0 || ldx < n || ldy < n) return H2_ERR_INVALID_ARG;
+    if (nrhs == 0) return H2_OK;
+    if (!X || !Y) return H2_ERR_INVALID_ARG;
+    try {
+        D->gb.add(D->A, (int)D->lda, 0, X, (int)ldx, 0, Y, (int)ldy, (int)n, (int)nrhs, (int)n, 1.0, 0.0);
+        D->gb.run((cudaStream_t)stream);
+        return H2_OK;
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        return H2_ERR_CUDA;
+    }
+}
+
+void h2_dense_op_destroy(void* ctx) {
+    if (ctx) {
+        cudaDeviceSynchronize();
+        delete static_cast<DenseOp*>(ctx);
+    }
+}
+
+}  // extern "C"

@@ -86,6 +86,17 @@ def test_matvec_equals_dense_expansion_and_symmetry():
         np.testing.assert_allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-13)
 
 
+def test_single_leaf_is_one_dense_block():
+    """N <= leaf: no levels, the approximation is the dense matrix from identity probes."""
+    op = O.HeatHessian(4, 0.01, 0.5, 0.01, W.sensor_mask(16, 5, 5))
+    h, res = O.build(op, W.grid_coords(4), 16, ADM_STRONG, 0.7, 1e-6, 8, 8, 8, 8, False, 3)
+    assert h.tree.L == 0 and res.samples - res.norm_its == 16
+    H = op.dense()
+    np.testing.assert_allclose(O.expand_dense(h), 0.5 * (H + H.T), rtol=0, atol=1e-12 * np.abs(H).max())
+    X = W.rhs(16, 3, 1)
+    np.testing.assert_allclose(O.matvec(h, X), O.expand_dense(h) @ X, rtol=1e-13, atol=1e-13)
+
+
 def test_norm_estimates_against_dense_svd():
     n = 20
     op = O.HeatHessian(n, 0.01, 0.5, 0.01, W.sensor_mask(n * n, 60, 9))
