@@ -212,6 +212,26 @@ int h2_export(h2_handle_t h, int32_t* ranks_host, double* U_host, double* E_host
 int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
               int mode, h2_stream_t stream);
 
+/*
+ * Same product as h2_matvec, for callers that cannot allocate device memory: for
+ * example code whose device memory is entirely managed by another allocator (a
+ * framework's caching pool that has already reserved the free memory), or
+ * latency-critical loops that must not pay the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  This entry point calls no allocation
+ * routine.  Its coefficient scratch is one fixed array of 32 MiB inside the
+ * library's device image, which every GPU that loads the library holds until the
+ * process exits; calls needing more (coefficient rows of the handle x nrhs x 8 bytes
+ * in H2_FP64, x 4 bytes otherwise) fail with H2_ERR_INVALID_ARG and a message giving
+ * the size.  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the contents of the last call (no element needs to
+ * start at zero: every element a call reads it has written before), so calls whose
+ * executions overlap on the GPU, on any handle or stream, race on it: serialise them.
+ * Arguments and errors as h2_matvec.  The paper has no counterpart of this entry point.
+ */
+int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+                      int mode, h2_stream_t stream);
+
 /* Stage kinds of the matvec, for h2_profile_read. */
 enum {
     H2_STAGE_LEAF_UP = 0,   /* xh_t = U_t^T X_t */

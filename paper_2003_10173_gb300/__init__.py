@@ -89,6 +89,7 @@ _SIGS = {
     "h2_factor_sizes": (_I, [_P, _P, _P, _P, _P, _P]),
     "h2_export": (_I, [_P, _P, _P, _P, _P, _P]),
     "h2_matvec": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
+    "h2_matvec_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
     "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "h2_profile": (_I, [_P, _I]),
     "h2_profile_read": (_I, [_P, _P, _P]),
@@ -338,6 +339,13 @@ class H2:
                ldy: int | None = None):
         n = self.stats()["n"]
         _check(lib().h2_matvec(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode, _stream_ptr(stream)))
+
+    def matvec_noalloc(self, X, Y, nrhs: int, mode: int = H2_FP64, stream=None, ldx: int | None = None,
+                       ldy: int | None = None):
+        """h2_matvec with the library's fixed 32 MiB device scratch instead of an allocated workspace."""
+        n = self.stats()["n"]
+        _check(lib().h2_matvec_noalloc(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode,
+                                       _stream_ptr(stream)))
 
     STAGES = ("leaf_up", "up", "couple", "down", "leaf_near")
 

@@ -324,6 +324,20 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
     });
 }
 
+int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
+                      h2_stream_t stream) {
+    return guard([&] {
+        require(h != nullptr, "h2_matvec_noalloc: NULL handle");
+        require(nrhs >= 0, "h2_matvec_noalloc: nrhs < 0");
+        if (nrhs == 0) return H2_OK;
+        require(X != nullptr && Y != nullptr, "h2_matvec_noalloc: NULL X or Y");
+        require(ldx >= h->N && ldy >= h->N, "h2_matvec_noalloc: leading dimension smaller than n");
+        require(mode == H2_FP64 || mode == H2_FP32 || mode == H2_BF16, "h2_matvec_noalloc: unknown mode");
+        h2::run_matvec_noalloc(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
 int h2_profile(h2_handle_t h, int enable) {
     return guard([&] {
         require(h != nullptr, "h2_profile: NULL handle");

@@ -105,4 +105,6 @@ void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s);
 void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                 int mode, cudaStream_t s);
 void profile_read(h2_handle_s* h, double* ms, int64_t* n);
+void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+                        int mode, cudaStream_t s);
 }  // namespace h2

@@ -13,6 +13,7 @@
 // Only the lower triangle of S and D is stored; upper blocks are used as
 // transposes of the stored ones.
 #include <algorithm>
+#include <mutex>
 
 #include "handle.h"
 
@@ -24,6 +25,7 @@ constexpr int NT = 256;
 constexpr int RMAX = 96;     // largest block dimension (leaf size / rank)
 constexpr int RT = 32;       // right-hand sides per CTA
 constexpr int OPT = (RMAX * RT + NT - 1) / NT;
+constexpr int64_t kMaxNrhs = 2000000;   // keeps the grid's y dimension (nrhs / RT) below 65536
 
 template <class T> __device__ __forceinline__ float to_f(T x);
 template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
@@ -34,14 +36,13 @@ template <> __device__ __forceinline__ double cvt<double, double>(double x) { re
 template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
 
 // TS: factor storage type, TX: type of X, TY: type of Y, TA: arithmetic / workspace type.
-template <class TS, class TX, class TY, class TA>
-__global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ outs,
-                                                       const MvItem* __restrict__ items,
-                                                       const TS* __restrict__ fac, TA* __restrict__ ws,
-                                                       int64_t ws_ld, const int32_t* __restrict__ perm,
-                                                       const TX* __restrict__ X, int64_t ldx,
-                                                       TY* __restrict__ Y, int64_t ldy, int nrhs,
-                                                       int out_to_y, int accumulate) {
+template <class TS, class TX, class TY, class TA, bool OUT_Y>
+__device__ __forceinline__ void mv_stage_body(const MvOut* __restrict__ outs, const MvItem* __restrict__ items,
+                                              const TS* __restrict__ fac, TA* __restrict__ ws, int64_t ws_ld,
+                                              const int32_t* __restrict__ perm, const TX* __restrict__ X,
+                                              int64_t ldx, TY* __restrict__ Y, int64_t ldy, int nrhs,
+                                              int accumulate) {
+    constexpr bool out_to_y = OUT_Y;
     extern __shared__ unsigned char smem_raw[];
     TA* Ms = reinterpret_cast<TA*>(smem_raw);             // [RMAX cols][RMAX+1 rows] column-major
     TA* IN = Ms + RMAX * (RMAX + 1);                        // [RMAX rows][RT]
@@ -109,6 +110,27 @@ __global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ 
     }
 }
 
+// Stages whose outputs are coefficient blocks (upsweep, couplings, downsweep, leaf upsweep).
+template <class TS, class TX, class TY, class TA>
+__global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ outs, const MvItem* __restrict__ items,
+                                                       const TS* __restrict__ fac, TA* __restrict__ ws, int64_t ws_ld,
+                                                       const int32_t* __restrict__ perm, const TX* __restrict__ X,
+                                                       int64_t ldx, TY* __restrict__ Y, int64_t ldy, int nrhs,
+                                                       int accumulate) {
+    mv_stage_body<TS, TX, TY, TA, false>(outs, items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs, accumulate);
+}
+
+// Final stage: leaf expansion plus the dense near field, written to Y.
+template <class TS, class TX, class TY, class TA>
+__global__ void __launch_bounds__(NT) mv_leaf_near_kernel(const MvOut* __restrict__ outs,
+                                                           const MvItem* __restrict__ items,
+                                                           const TS* __restrict__ fac, TA* __restrict__ ws,
+                                                           int64_t ws_ld, const int32_t* __restrict__ perm,
+                                                           const TX* __restrict__ X, int64_t ldx, TY* __restrict__ Y,
+                                                           int64_t ldy, int nrhs, int accumulate) {
+    mv_stage_body<TS, TX, TY, TA, true>(outs, items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs, accumulate);
+}
+
 template <class TS, class TA>
 __global__ void convert_kernel(const double* __restrict__ src, TS* __restrict__ dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -129,12 +151,20 @@ void launch_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const
     if (!attr) {
         H2_CUDA(cudaFuncSetAttribute(mv_stage_kernel<TS, TX, TY, TA>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        H2_CUDA(cudaFuncSetAttribute(mv_leaf_near_kernel<TS, TX, TY, TA>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     dim3 grid((unsigned)st.outs.size(), (unsigned)((nrhs + RT - 1) / RT));
-    mv_stage_kernel<TS, TX, TY, TA><<<grid, NT, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, perm,
-                                                           X, ldx, Y, ldy, nrhs, st.out_to_y, st.accumulate);
-    after_launch("mv_stage");
+    if (st.out_to_y) {
+        mv_leaf_near_kernel<TS, TX, TY, TA><<<grid, NT, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, perm,
+                                                                   X, ldx, Y, ldy, nrhs, st.accumulate);
+        after_launch("mv_leaf_near");
+    } else {
+        mv_stage_kernel<TS, TX, TY, TA><<<grid, NT, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, perm, X,
+                                                               ldx, Y, ldy, nrhs, st.accumulate);
+        after_launch("mv_stage");
+    }
 }
 
 cudaEvent_t take_event(h2_handle_s* h) {
@@ -150,9 +180,9 @@ cudaEvent_t take_event(h2_handle_s* h) {
 
 template <class TS, class TX, class TY, class TA>
 void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy,
-             int nrhs, cudaStream_t s) {
+             int nrhs, cudaStream_t s, bool allow_prof = true) {
     for (const MvStage& st : h->plan.stages) {
-        if (h->prof && !st.outs.empty()) {
+        if (allow_prof && h->prof && !st.outs.empty()) {
             cudaEvent_t a = take_event(h), b = take_event(h);
             H2_CUDA(cudaEventRecord(a, s));
             launch_stage<TS, TX, TY, TA>(st, fac, ws, h->plan.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
@@ -164,7 +194,68 @@ void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY
     }
 }
 
+// Scratch of h2_matvec_noalloc: a fixed array in the library's device image, so that
+// the entry point needs no allocation.  Every device that loads the library holds it.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The name of a __device__
+// variable is only a host-side stand-in, so its address is looked up once per device
+// (with that device current) and cached.
+void* noalloc_scratch() {
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(H2_ERR_CUDA, std::string("h2_matvec_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        }
+        g_scratch_addr[dev] = p;
+    }
+    return g_scratch_addr[dev];
+}
+
 }  // namespace
+
+void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
+                        cudaStream_t s) {
+    if (nrhs <= 0) return;
+    if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: nrhs above 2,000,000");
+    const size_t elt = (mode == H2_FP64) ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)h->plan.ws_rows * (size_t)nrhs * elt;
+    if (need > kNoAllocScratchBytes)
+        fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: needs " + std::to_string(need) + " bytes of scratch (" +
+                                     std::to_string(h->plan.ws_rows) + " coefficient rows x " + std::to_string(nrhs) +
+                                     " right-hand sides), above the fixed " + std::to_string(kNoAllocScratchBytes) +
+                                     " bytes; use fewer right-hand sides per call or h2_matvec");
+    void* ws = noalloc_scratch();
+    switch (mode) {
+        case H2_FP64:
+            run_all<double, double, double, double>(h, h->fac64.p, (double*)ws, (const double*)X, ldx, (double*)Y, ldy,
+                                                    (int)nrhs, s, false);
+            break;
+        case H2_FP32:
+            if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: FP32 copy of the factors was not kept");
+            run_all<float, float, float, float>(h, h->fac32.p, (float*)ws, (const float*)X, ldx, (float*)Y, ldy,
+                                                (int)nrhs, s, false);
+            break;
+        case H2_BF16:
+            if (!h->fac16.p) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: BF16 copy of the factors was not kept");
+            run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, (float*)ws, (const __nv_bfloat16*)X,
+                                                                ldx, (float*)Y, ldy, (int)nrhs, s, false);
+            break;
+        default:
+            fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: mode not supported");
+    }
+}
 
 void layout_factors(h2_handle_s* h) {
     const h2_tree_s& T = *h->tree;
@@ -378,7 +469,7 @@ void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s) {
 void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                 int mode, cudaStream_t s) {
     if (nrhs <= 0) return;
-    if (nrhs > (1 << 24)) fail(H2_ERR_INVALID_ARG, "h2_matvec: nrhs too large");
+    if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec: nrhs above 2,000,000");
     const int64_t need = h->plan.ws_rows * nrhs;
     switch (mode) {
         case H2_FP64: {
