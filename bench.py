@@ -58,12 +58,12 @@ def matvec_bytes(st: dict, N: int, nrhs: int, elt: int = 8) -> float:
     return stored * elt + N * nrhs * 2 * elt
 
 
-def leaf_near_flops(st: dict, tree_sizes, nrhs: int) -> float:
-    """FP64 flops of the leaf-expansion + near-field stage: every stored off-diagonal
-    near block is applied twice (as D and D^T), diagonal blocks once, leaf bases once."""
+def near_flops(st: dict, tree_sizes, nrhs: int) -> float:
+    """Flops of the near-field product: every stored off-diagonal near block is applied
+    twice (as D and D^T), every diagonal block once."""
     diag = float(np.sum(np.asarray(tree_sizes, dtype=np.float64) ** 2))
     off = st["entries_D"] - diag
-    return 2.0 * nrhs * (diag + 2.0 * off + st["entries_U"])
+    return 2.0 * nrhs * (diag + 2.0 * off)
 
 
 class Clocks:
@@ -300,12 +300,13 @@ def main():
     prof = Gp.profile_read()
     Gp.profile(False)
     _, sizes = tree.boxes(tree.L)
-    ln_ms, ln_n = prof["leaf_near"]
-    ln_flops = leaf_near_flops(st, sizes, 1)
-    achieved = ln_flops / (ln_ms / ln_n / 1e3) / 1e12
+    nr_ms, nr_n = prof["near"]
+    nr_s = nr_ms / nr_n / 1e3
+    achieved = near_flops(st, sizes, 1) / nr_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64, "unit": "TFLOP/s", "frac": achieved / fp64,
-                "traffic": None, "kernel": "mv_stage_kernel<double> (leaf expansion + near field), nrhs=1",
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+                "traffic": None, "kernel": "mv_scatter_kernel<double,...,1,true> (near field, nrhs=1)",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                "hbm_GBps": st["entries_D"] * 8 / nr_s / 1e9}
     gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
     roofline_build = {"bound": "alu", "achieved": gemm_tf, "peak": fp64, "unit": "TFLOP/s",
                       "frac": (gemm_tf / fp64) if gemm_tf else None, "traffic": None,

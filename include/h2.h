@@ -238,8 +238,9 @@ enum {
     H2_STAGE_UP = 1,        /* transfer upsweep, all levels */
     H2_STAGE_COUPLE = 2,    /* couplings, all levels */
     H2_STAGE_DOWN = 3,      /* transfer downsweep, all levels */
-    H2_STAGE_LEAF_NEAR = 4, /* Y_t = U_t yh_t + sum_s D_ts X_s */
-    H2_STAGE_COUNT = 5
+    H2_STAGE_LEAF_NEAR = 4, /* Y_t = U_t yh_t (+ sum_s D_ts X_s when the near field is gathered per leaf) */
+    H2_STAGE_NEAR = 5,      /* near field scattered per stored block (small nrhs): Y += D X */
+    H2_STAGE_COUNT = 6
 };
 
 /* Enable (1) or disable (0) per-stage timing of h2_matvec on handle h: CUDA events

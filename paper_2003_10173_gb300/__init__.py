@@ -347,14 +347,14 @@ class H2:
         _check(lib().h2_matvec_noalloc(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode,
                                        _stream_ptr(stream)))
 
-    STAGES = ("leaf_up", "up", "couple", "down", "leaf_near")
+    STAGES = ("leaf_up", "up", "couple", "down", "leaf_near", "near")
 
     def profile(self, enable: bool = True):
         _check(lib().h2_profile(self._h, int(enable)))
 
     def profile_read(self) -> dict:
-        ms = np.zeros(5)
-        n = np.zeros(5, dtype=np.int64)
+        ms = np.zeros(6)
+        n = np.zeros(6, dtype=np.int64)
         _check(lib().h2_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
 

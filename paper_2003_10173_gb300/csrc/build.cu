@@ -87,6 +87,7 @@ class Builder {
     DevBuf<double> Ddiag_;
     std::vector<int64_t> ddiag_off_;
     GemmBatch gb_;
+    TsqrWork tsqr_;
     Stager stg_[4];
     DevBuf<int64_t> d_i64a_, d_i64b_;
     DevBuf<int> d_i32a_, d_i32b_, d_i32c_, d_flag_;
@@ -268,12 +269,10 @@ void Builder::panel(int l, const std::vector<int>& pairs, int c0, int w) {
         back.push_back(BlkDesc{st + (int64_t)kb_[l][i] * N_, st + (int64_t)c0 * N_, bsize(l, 2 * i + 1), w, (int)N_,
                                (int)N_});
     }
-    const int64_t* dy = dev_list(d_i64a_, yoff, 1);
-    const int64_t* dq = dev_list(d_i64b_, qoff, 2);
-    const int* dm = dev_list(d_i32a_, m, 3);
     for (int round = 0; round < 2; ++round) {
         project(l, pairs, w, c0, 1);
-        panel_qr((int)pairs.size(), dy, dq, dm, w, Yt_.p, (int)N_, Pl(l), (int)N_, s_);
+        tsqr_panels((int)pairs.size(), yoff.data(), qoff.data(), m.data(), w, Yt_.p, (int)N_, Pl(l), (int)N_, tsqr_,
+                    s_);
         if (round == 0) blocks(BLK_COPY, back, Pl(l), Yt_.p);
     }
     for (int i : pairs) kb_[l][i] += w;

@@ -128,6 +128,27 @@ void gemm_profile_read(double* ms, double* flops, int64_t* launches);
 // Panel i: m_i x c rows/cols at Y + y_off[i] (ld ldy), Q at Q + q_off[i] (ld ldq).
 void panel_qr(int count, const int64_t* d_y_off, const int64_t* d_q_off, const int* d_m, int c,
               double* Y, int ldy, double* Q, int ldq, cudaStream_t s);
+// Shared-memory TSQR of panels (m_i > c rows, c <= 16 columns): explicit orthonormal factor
+// of Y_i written to Q (Y_i is used as scratch).  Host arrays y_off, q_off, m.
+struct TsqrChunk {
+    int64_t y_off;   // first row of the chunk in Y
+    int64_t q_off;   // first row of the chunk in Q
+    int rows;
+    int64_t r_off;   // offset of the chunk's R in the R buffer, -1 for single-chunk panels
+    int64_t qs_off;  // offset of the chunk's c x c block in the stacked factor buffer
+    int ldqs;
+};
+constexpr int kTsqrChunk = 512;      // target rows per chunk
+constexpr int kTsqrMaxChunks = 96;   // chunks per panel (stacked R: <= 1536 x 16)
+constexpr int kTsqrMaxRows = 1536;   // shared-memory rows of one CTA
+struct TsqrWork {
+    DevBuf<TsqrChunk> d_chunks, d_multi;
+    DevBuf<int4> d_roots;
+    DevBuf<double> Rbuf, Qs;
+    Stager st_chunks, st_multi, st_roots;
+};
+void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const int* m, int c, double* Y, int ldy,
+                 double* Q, int ldq, TsqrWork& w, cudaStream_t s);
 // Maximum column 2-norm of each panel: out[i] = max_j ||Y_i[:, j]||.
 void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c, const double* Y,
                        int ldy, double* out, cudaStream_t s);

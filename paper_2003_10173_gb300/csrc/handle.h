@@ -44,9 +44,29 @@ struct MvStage {
     int max_rows = 0, max_cols = 0;
 };
 
+// A stored (lower-triangle or diagonal) block used in both orientations by the
+// small-nrhs scatter path: out_t += M in_s and, unless diag, out_s += M^T in_t.
+struct SymItem {
+    int64_t m_off;
+    int64_t in_s, out_t, in_t, out_s;
+    int ldm, rows, cols, diag;
+};
+
+struct SymStage {
+    int kind = 0;
+    int via_perm = 0;       // inputs/outputs are X/Y rows (tree positions, through perm)
+    std::vector<SymItem> items;
+    DevBuf<SymItem> d_items;
+};
+
 struct MatvecPlan {
-    std::vector<MvStage> stages;
+    std::vector<MvStage> stages;       // gather path (any nrhs)
     int64_t ws_rows = 0;     // rows of the internal coefficient workspace (per right-hand side)
+    int64_t yh_row0 = 0;     // first row of the yh part of the workspace
+    // small-nrhs path: gather stages for the tree sweeps, scatter stages for couplings and near field
+    std::vector<MvStage> small_up, small_down;   // leaf upsweep + upsweep; downsweep
+    MvStage small_expand;                        // Y += U_t yh_t (accumulate)
+    SymStage couple, near;
 };
 
 struct Workspace {

@@ -305,7 +305,233 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const int64_t* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tall-skinny QR (TSQR) of panels in shared memory.
+//
+// Each panel (m rows x c <= 16 columns) is split into row chunks; every chunk is
+// factorised by Householder QR in shared memory (stage 1), the stacked c x c R
+// factors of a panel are factorised once more (stage 2), and each chunk's
+// orthonormal factor is multiplied by its c x c block of the second factor
+// (stage 3): Q = diag(Q_1..Q_k) Q_s.  Householder vectors follow dlarfg; the
+// explicit factor is formed in place backwards as in dorg2r.
+// ---------------------------------------------------------------------------
+
+// Householder QR in place of the h x c matrix A (shared memory, leading dimension h),
+// h >= c.  R in the upper triangle, reflectors below the diagonal, tau[0..c).
+__device__ void house_qr_smem(double* A, int h, int c, double* tau, double* sh, double* res) {
+    for (int j = 0; j < c; ++j) {
+        double p[1] = {0.0};
+        for (int i = j + 1 + threadIdx.x; i < h; i += NT) p[0] = fma(A[i + j * h], A[i + j * h], p[0]);
+        block_sum<1>(p, sh, res);
+        const double xn2 = res[0];
+        const double alpha = A[j + j * h];
+        double tj = 0.0, scale = 0.0, beta = alpha;
+        if (xn2 > 0.0) {
+            beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+            tj = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+        }
+        __syncthreads();
+        if (tj != 0.0)
+            for (int i = j + 1 + threadIdx.x; i < h; i += NT) A[i + j * h] *= scale;
+        if (threadIdx.x == 0) {
+            tau[j] = tj;
+            A[j + j * h] = beta;
+        }
+        __syncthreads();
+        if (tj == 0.0) continue;
+        double w[MAXC];
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) w[k] = 0.0;
+        for (int i = j + 1 + threadIdx.x; i < h; i += NT) {
+            const double v = A[i + j * h];
+#pragma unroll
+            for (int k = 0; k < MAXC; ++k)
+                if (k > j && k < c) w[k] = fma(v, A[i + k * h], w[k]);
+        }
+        block_sum<MAXC>(w, sh, res);
+        if (threadIdx.x > j && threadIdx.x < c) res[threadIdx.x] += A[j + threadIdx.x * h];
+        __syncthreads();
+        for (int e = threadIdx.x; e < (h - j) * (c - j - 1); e += NT) {
+            const int i = j + e % (h - j), k = j + 1 + e / (h - j);
+            const double f = tj * res[k];
+            const double v = (i == j) ? 1.0 : A[i + j * h];
+            A[i + k * h] = fma(-f, v, A[i + k * h]);
+        }
+        __syncthreads();
+    }
+}
+
+// Overwrites the reflectors of house_qr_smem with the explicit h x c orthonormal factor.
+__device__ void house_orgqr_smem(double* A, int h, int c, const double* tau, double* sh, double* res) {
+    for (int j = c - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (j < c - 1) {
+            // apply H_j to A[j:h, j+1:c] with v = [1; A[j+1:h, j]]
+            double w[MAXC];
+#pragma unroll
+            for (int k = 0; k < MAXC; ++k) w[k] = 0.0;
+            for (int i = j + 1 + threadIdx.x; i < h; i += NT) {
+                const double v = A[i + j * h];
+#pragma unroll
+                for (int k = 0; k < MAXC; ++k)
+                    if (k > j && k < c) w[k] = fma(v, A[i + k * h], w[k]);
+            }
+            block_sum<MAXC>(w, sh, res);
+            if (threadIdx.x > j && threadIdx.x < c) res[threadIdx.x] += A[j + threadIdx.x * h];
+            __syncthreads();
+            for (int e = threadIdx.x; e < (h - j) * (c - j - 1); e += NT) {
+                const int i = j + e % (h - j), k = j + 1 + e / (h - j);
+                const double v = (i == j) ? 1.0 : A[i + j * h];
+                A[i + k * h] = fma(-tj * res[k], v, A[i + k * h]);
+            }
+            __syncthreads();
+        }
+        for (int i = j + 1 + threadIdx.x; i < h; i += NT) A[i + j * h] *= -tj;
+        for (int i = threadIdx.x; i < j; i += NT) A[i + j * h] = 0.0;
+        if (threadIdx.x == 0) A[j + j * h] = 1.0 - tj;
+        __syncthreads();
+    }
+}
+
+// stage 1: one chunk per CTA.  d = {src offset in Y, dst offset in Q, rows, R offset (-1: single chunk)}
+__global__ void __launch_bounds__(NT) tsqr_chunk_kernel(const TsqrChunk* __restrict__ chunks, int c,
+                                                         const double* __restrict__ Y, int ldy,
+                                                         double* __restrict__ Q, int ldq, double* __restrict__ Rbuf) {
+    extern __shared__ double A[];
+    __shared__ double sh[NW * MAXC];
+    __shared__ double res[MAXC];
+    __shared__ double tau[MAXC];
+    const TsqrChunk d = chunks[blockIdx.x];
+    const int h = d.rows;
+    for (int e = threadIdx.x; e < h * c; e += NT) {
+        const int i = e % h, k = e / h;
+        A[i + k * h] = Y[d.y_off + i + (int64_t)k * ldy];
+    }
+    __syncthreads();
+    house_qr_smem(A, h, c, tau, sh, res);
+    if (d.r_off >= 0)
+        for (int e = threadIdx.x; e < c * c; e += NT) {
+            const int i = e % c, k = e / c;
+            Rbuf[d.r_off + i + k * c] = (i <= k) ? A[i + k * h] : 0.0;
+        }
+    __syncthreads();
+    house_orgqr_smem(A, h, c, tau, sh, res);
+    for (int e = threadIdx.x; e < h * c; e += NT) {
+        const int i = e % h, k = e / h;
+        Q[d.q_off + i + (int64_t)k * ldq] = A[i + k * h];
+    }
+}
+
+// stage 2: the stacked R factors of one panel per CTA -> Qs (nchunk*c x c, leading dimension nchunk*c)
+__global__ void __launch_bounds__(NT) tsqr_root_kernel(const int4* __restrict__ roots, int c,
+                                                        const double* __restrict__ Rbuf, double* __restrict__ Qs) {
+    extern __shared__ double A[];
+    __shared__ double sh[NW * MAXC];
+    __shared__ double res[MAXC];
+    __shared__ double tau[MAXC];
+    const int4 r = roots[blockIdx.x];   // x: first R offset / (c*c) chunk index, y: nchunk, z: Qs offset (in c*c units)
+    const int nch = r.y;
+    const int h = nch * c;
+    const double* R = Rbuf + (int64_t)r.x * c * c;
+    for (int e = threadIdx.x; e < h * c; e += NT) {
+        const int i = e % h, k = e / h;
+        const int ch = i / c, ii = i % c;
+        A[i + k * h] = R[(int64_t)ch * c * c + ii + k * c];
+    }
+    __syncthreads();
+    house_qr_smem(A, h, c, tau, sh, res);
+    __syncthreads();
+    house_orgqr_smem(A, h, c, tau, sh, res);
+    double* out = Qs + (int64_t)r.z * c * c;
+    for (int e = threadIdx.x; e < h * c; e += NT) out[e] = A[e];
+}
+
+// stage 3: Q_chunk <- Q_chunk * Qs[chunk block]  (in place, row by row)
+__global__ void __launch_bounds__(NT) tsqr_apply_kernel(const TsqrChunk* __restrict__ chunks, int c,
+                                                         double* __restrict__ Q, int ldq, const double* __restrict__ Qs) {
+    __shared__ double B[MAXC * MAXC];
+    const TsqrChunk d = chunks[blockIdx.x];
+    // qs position: Qs block rows [kc*c, kc*c+c) of the panel's Qs with leading dimension ldqs
+    const int64_t base = d.qs_off;
+    const int ldqs = d.ldqs;
+    for (int e = threadIdx.x; e < c * c; e += NT) {
+        const int i = e % c, k = e / c;
+        B[i + k * MAXC] = Qs[base + i + (int64_t)k * ldqs];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d.rows; i += NT) {
+        double q[MAXC], o[MAXC];
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) q[k] = (k < c) ? Q[d.q_off + i + (int64_t)k * ldq] : 0.0;
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < MAXC; ++j) acc = fma(q[j], B[j + k * MAXC], acc);
+            o[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < MAXC; ++k)
+            if (k < c) Q[d.q_off + i + (int64_t)k * ldq] = o[k];
+    }
+}
+
 }  // namespace
+
+void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const int* m, int c, double* Y, int ldy,
+                 double* Q, int ldq, TsqrWork& w, cudaStream_t s) {
+    if (count <= 0) return;
+    if (c < 1 || c > MAXC) fail(H2_ERR_INVALID_ARG, "tsqr: panel width out of range");
+    std::vector<TsqrChunk> chunks, multi;
+    std::vector<int4> roots;
+    int64_t rcount = 0, qscount = 0;
+    int max_h = 0, max_root = 0;
+    for (int p = 0; p < count; ++p) {
+        if (m[p] <= c) fail(H2_ERR_INVALID_ARG, "tsqr: panel must have more rows than columns");
+        int nch = std::max(1, std::min(kTsqrMaxChunks, m[p] / kTsqrChunk));
+        if ((m[p] + nch - 1) / nch > kTsqrMaxRows) fail(H2_ERR_INVALID_ARG, "tsqr: panel too tall");
+        const int64_t r0 = rcount, qs0 = qscount;
+        int row = 0;
+        for (int k = 0; k < nch; ++k) {
+            const int h = m[p] / nch + (k < m[p] % nch ? 1 : 0);
+            TsqrChunk d{y_off[p] + row, q_off[p] + row, h, nch > 1 ? (r0 + k) * c * c : -1,
+                        (qs0 * c * c) + (int64_t)k * c, nch * c};
+            chunks.push_back(d);
+            if (nch > 1) multi.push_back(d);
+            max_h = std::max(max_h, h);
+            row += h;
+        }
+        if (nch > 1) {
+            roots.push_back(make_int4((int)r0, nch, (int)qs0, 0));
+            rcount += nch;
+            qscount += nch;
+            max_root = std::max(max_root, nch * c);
+        }
+    }
+    upload(w.d_chunks, chunks, s, w.st_chunks);
+    w.Rbuf.reserve((size_t)std::max<int64_t>(rcount * c * c, 1));
+    w.Qs.reserve((size_t)std::max<int64_t>(qscount * c * c, 1));
+    const size_t smem1 = (size_t)max_h * c * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        const int mx = kTsqrMaxRows * MAXC * (int)sizeof(double);
+        H2_CUDA(cudaFuncSetAttribute(tsqr_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        H2_CUDA(cudaFuncSetAttribute(tsqr_root_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        attr = true;
+    }
+    tsqr_chunk_kernel<<<(unsigned)chunks.size(), NT, smem1, s>>>(w.d_chunks.p, c, Y, ldy, Q, ldq, w.Rbuf.p);
+    after_launch("tsqr_chunk");
+    if (!roots.empty()) {
+        upload(w.d_roots, roots, s, w.st_roots);
+        upload(w.d_multi, multi, s, w.st_multi);
+        tsqr_root_kernel<<<(unsigned)roots.size(), NT, (size_t)max_root * c * sizeof(double), s>>>(w.d_roots.p, c,
+                                                                                                 w.Rbuf.p, w.Qs.p);
+        after_launch("tsqr_root");
+        tsqr_apply_kernel<<<(unsigned)multi.size(), NT, 0, s>>>(w.d_multi.p, c, Q, ldq, w.Qs.p);
+        after_launch("tsqr_apply");
+    }
+}
 
 void panel_qr(int count, const int64_t* d_y_off, const int64_t* d_q_off, const int* d_m, int c,
               double* Y, int ldy, double* Q, int ldq, cudaStream_t s) {

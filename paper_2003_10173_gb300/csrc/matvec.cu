@@ -142,6 +142,111 @@ __global__ void convert_kernel<__nv_bfloat16, float>(const double* __restrict__ 
         dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
+// Small-nrhs scatter product: one warp per stored block, read once in 32 x 32 tiles
+// (coalesced along rows); out_t += M in_s from registers and out_s += M^T in_t from a
+// per-warp shared-memory copy of the tile; both added with atomics.
+constexpr int SW = 8;   // warps per CTA
+
+template <class TA, class TX, bool VIA_PERM>
+__device__ __forceinline__ TA sc_in(const TX* __restrict__ X, int64_t ldx, const TA* __restrict__ ws, int64_t ws_ld,
+                                    const int32_t* __restrict__ perm, int64_t off, int j, int r) {
+    if constexpr (VIA_PERM) return cvt<TA>(X[perm[off + j] + (int64_t)r * ldx]);
+    else return ws[off + j + (int64_t)r * ws_ld];
+}
+
+template <class TA, class TY, bool VIA_PERM>
+__device__ __forceinline__ void sc_add(TY* __restrict__ Y, int64_t ldy, TA* __restrict__ ws, int64_t ws_ld,
+                                       const int32_t* __restrict__ perm, int64_t off, int i, int r, TA v) {
+    if constexpr (VIA_PERM) atomicAdd(Y + perm[off + i] + (int64_t)r * ldy, (TY)v);
+    else atomicAdd(ws + off + i + (int64_t)r * ws_ld, v);
+}
+
+template <class TS, class TX, class TY, class TA, int NR, bool VIA_PERM>
+__global__ void __launch_bounds__(SW * 32) mv_scatter_kernel(const SymItem* __restrict__ items, int nitems,
+                                                              const TS* __restrict__ fac, TA* __restrict__ ws,
+                                                              int64_t ws_ld, const int32_t* __restrict__ perm,
+                                                              const TX* __restrict__ X, int64_t ldx,
+                                                              TY* __restrict__ Y, int64_t ldy) {
+    __shared__ TA tile[SW][32][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * SW + warp;
+    if (idx >= nitems) return;
+    const SymItem it = items[idx];
+    const TS* M = fac + it.m_off;
+    TA (*T)[33] = tile[warp];
+    for (int i0 = 0; i0 < it.rows; i0 += 32) {
+        const int i = i0 + lane;
+        const bool rin = i < it.rows;
+        TA xt[NR], yt[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            yt[r] = (TA)0;
+            xt[r] = (!it.diag && rin) ? sc_in<TA, TX, VIA_PERM>(X, ldx, ws, ws_ld, perm, it.in_t, i, r) : (TA)0;
+        }
+        for (int j0 = 0; j0 < it.cols; j0 += 32) {
+            const int jl = j0 + lane;
+            const bool cin = jl < it.cols;
+            TA xs[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                xs[r] = cin ? sc_in<TA, TX, VIA_PERM>(X, ldx, ws, ws_ld, perm, it.in_s, jl, r) : (TA)0;
+            const int nc = min(32, it.cols - j0);
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) {
+                TA d = (TA)0;
+                if (rin && c < nc) d = cvt<TA>(M[i + (int64_t)(j0 + c) * it.ldm]);
+                T[c][lane] = d;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
+            }
+            if (!it.diag) {
+                __syncwarp();
+                TA ys[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) ys[r] = (TA)0;
+#pragma unroll 8
+                for (int row = 0; row < 32; ++row) {
+                    const TA d = T[lane][row];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) ys[r] = fma(d, __shfl_sync(0xffffffffu, xt[r], row), ys[r]);
+                }
+                if (cin)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) sc_add<TA, TY, VIA_PERM>(Y, ldy, ws, ws_ld, perm, it.out_s, jl, r, ys[r]);
+            }
+            __syncwarp();
+        }
+        if (rin)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sc_add<TA, TY, VIA_PERM>(Y, ldy, ws, ws_ld, perm, it.out_t, i, r, yt[r]);
+    }
+}
+
+template <class TS, class TX, class TY, class TA, int NR>
+void launch_scatter_nr(const SymStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm, const TX* X,
+                       int64_t ldx, TY* Y, int64_t ldy, cudaStream_t s) {
+    const unsigned grid = (unsigned)((st.items.size() + SW - 1) / SW);
+    if (st.via_perm)
+        mv_scatter_kernel<TS, TX, TY, TA, NR, true><<<grid, SW * 32, 0, s>>>(st.d_items.p, (int)st.items.size(), fac,
+                                                                             ws, ws_ld, perm, X, ldx, Y, ldy);
+    else
+        mv_scatter_kernel<TS, TX, TY, TA, NR, false><<<grid, SW * 32, 0, s>>>(st.d_items.p, (int)st.items.size(), fac,
+                                                                              ws, ws_ld, perm, X, ldx, Y, ldy);
+    after_launch(st.via_perm ? "mv_near_scatter" : "mv_couple_scatter");
+}
+
+template <class TS, class TX, class TY, class TA>
+void launch_scatter(const SymStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm, const TX* X,
+                    int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
+    if (st.items.empty()) return;
+    switch (nrhs) {
+        case 1: launch_scatter_nr<TS, TX, TY, TA, 1>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        case 2: launch_scatter_nr<TS, TX, TY, TA, 2>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        case 3: launch_scatter_nr<TS, TX, TY, TA, 3>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        default: launch_scatter_nr<TS, TX, TY, TA, 4>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+    }
+}
+
 template <class TS, class TX, class TY, class TA>
 void launch_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm,
                   const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
@@ -178,9 +283,43 @@ cudaEvent_t take_event(h2_handle_s* h) {
     return e;
 }
 
+constexpr int kSmallNrhs = 4;
+
+template <class TS, class TX, class TY, class TA>
+void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs,
+               cudaStream_t s, bool prof) {
+    const MatvecPlan& P = h->plan;
+    const int64_t wld = P.ws_rows;
+    auto timed = [&](int kind, auto&& fn) {
+        if (!prof) { fn(); return; }
+        cudaEvent_t a = take_event(h), b = take_event(h);
+        H2_CUDA(cudaEventRecord(a, s));
+        fn();
+        H2_CUDA(cudaEventRecord(b, s));
+        h->ev_used.push_back({kind, {a, b}});
+    };
+    // Y and yh start at zero: the scatter stages add into them
+    H2_CUDA(cudaMemset2DAsync(Y, ldy * sizeof(TY), 0, h->N * sizeof(TY), nrhs, s));
+    if (wld > P.yh_row0)
+        H2_CUDA(cudaMemset2DAsync(ws + P.yh_row0, wld * sizeof(TA), 0, (wld - P.yh_row0) * sizeof(TA), nrhs, s));
+    timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    for (const MvStage& st : P.small_up)
+        timed(st.kind, [&] { launch_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    timed(H2_STAGE_COUPLE, [&] { launch_scatter<TS, TX, TY, TA>(P.couple, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    for (const MvStage& st : P.small_down)
+        timed(st.kind, [&] { launch_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    timed(H2_STAGE_LEAF_NEAR, [&] {
+        launch_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+    });
+}
+
 template <class TS, class TX, class TY, class TA>
 void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy,
              int nrhs, cudaStream_t s, bool allow_prof = true) {
+    if (nrhs <= kSmallNrhs) {
+        run_small<TS, TX, TY, TA>(h, fac, ws, X, ldx, Y, ldy, nrhs, s, allow_prof && h->prof);
+        return;
+    }
     for (const MvStage& st : h->plan.stages) {
         if (allow_prof && h->prof && !st.outs.empty()) {
             cudaEvent_t a = take_event(h), b = take_event(h);
@@ -304,7 +443,7 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
     const h2_tree_s& T = *h->tree;
     const int L = T.L;
     auto K = [&](int l, int b) { return h->k[h->koff[l] + b]; };
-    // coefficient workspace rows: xh levels then yh levels
+    // coefficient workspace rows: xh of every box, then yh of every box
     std::vector<int64_t> box_row(h->k.size());
     int64_t rows = 0;
     for (size_t i = 0; i < h->k.size(); ++i) {
@@ -313,15 +452,15 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
     }
     const int64_t ytop = rows;
     rows *= 2;
-    h->plan.ws_rows = std::max<int64_t>(rows, 1);
+    MatvecPlan& P = h->plan;
+    P.ws_rows = std::max<int64_t>(rows, 1);
+    P.yh_row0 = ytop;
     auto xrow = [&](int l, int b) { return box_row[h->koff[l] + b]; };
     auto yrow = [&](int l, int b) { return ytop + box_row[h->koff[l] + b]; };
-    const int64_t wld = h->plan.ws_rows;
-    h->plan.stages.clear();
-    auto new_stage = [&]() -> MvStage& {
-        h->plan.stages.emplace_back();
-        return h->plan.stages.back();
-    };
+    const int64_t wld = P.ws_rows;
+    P.stages.clear();
+    P.small_up.clear();
+    P.small_down.clear();
     auto add_out = [&](MvStage& st, int64_t off, int nrows) {
         st.outs.push_back(MvOut{off, (int)wld, nrows, (int)st.items.size(), (int)st.items.size()});
     };
@@ -330,86 +469,51 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
         st.items.push_back(MvItem{moff, in_off, ldm, r, c, trans, (int)wld});
         st.outs.back().end = (int)st.items.size();
     };
-    if (L >= 1) {
-        // 1. leaf upsweep
-        {
-            MvStage& st = new_stage();
-            st.kind = H2_STAGE_LEAF_UP;
-            for (int t = 0; t < (1 << L); ++t) {
-                const int kt = K(L, t), m = (int)T.size[L][t];
-                if (!kt) continue;
-                add_out(st, xrow(L, t), kt);
-                add_item(st, h->u_off[t], m, kt, m, 1 | 2, T.start[L][t]);
-            }
+    auto make_leaf_up = [&](MvStage& st) {
+        st.kind = H2_STAGE_LEAF_UP;
+        for (int t = 0; t < (1 << L); ++t) {
+            const int kt = K(L, t), m = (int)T.size[L][t];
+            if (!kt) continue;
+            add_out(st, xrow(L, t), kt);
+            add_item(st, h->u_off[t], m, kt, m, 1 | 2, T.start[L][t]);
         }
-        // 2. upsweep
-        for (int l = L - 1; l >= 1; --l) {
-            MvStage& st = new_stage();
-            st.kind = H2_STAGE_UP;
-            for (int p = 0; p < (1 << l); ++p) {
-                const int kp = K(l, p);
-                if (!kp) continue;
-                const int k1 = K(l + 1, 2 * p), k2 = K(l + 1, 2 * p + 1);
-                add_out(st, xrow(l, p), kp);
-                const int64_t uo = h->uh_off[h->koff[l] + p];
-                add_item(st, uo, k1 + k2, kp, k1, 1, xrow(l + 1, 2 * p));
-                add_item(st, uo + k1, k1 + k2, kp, k2, 1, xrow(l + 1, 2 * p + 1));
-            }
+    };
+    auto make_up = [&](MvStage& st, int l) {
+        st.kind = H2_STAGE_UP;
+        for (int p = 0; p < (1 << l); ++p) {
+            const int kp = K(l, p);
+            if (!kp) continue;
+            const int k1 = K(l + 1, 2 * p), k2 = K(l + 1, 2 * p + 1);
+            add_out(st, xrow(l, p), kp);
+            const int64_t uo = h->uh_off[h->koff[l] + p];
+            add_item(st, uo, k1 + k2, kp, k1, 1, xrow(l + 1, 2 * p));
+            add_item(st, uo + k1, k1 + k2, kp, k2, 1, xrow(l + 1, 2 * p + 1));
         }
-        // 3. couplings (every box with a basis gets an output so that yh starts at zero)
-        {
-            MvStage& st = new_stage();
-            st.kind = H2_STAGE_COUPLE;
-            for (int l = 1; l <= L; ++l) {
-                std::vector<std::vector<int>> far_of(1 << l);
-                std::vector<std::vector<int64_t>> mo(1 << l);
-                std::vector<std::vector<int>> tr(1 << l);
-                for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
-                    auto [t, s2] = h->far_lower[l][i];
-                    far_of[t].push_back(s2); mo[t].push_back(h->s_off[l][i]); tr[t].push_back(0);
-                    far_of[s2].push_back(t); mo[s2].push_back(h->s_off[l][i]); tr[s2].push_back(1);
-                }
-                for (int t = 0; t < (1 << l); ++t) {
-                    const int kt = K(l, t);
-                    if (!kt) continue;
-                    add_out(st, yrow(l, t), kt);
-                    for (size_t j = 0; j < far_of[t].size(); ++j) {
-                        const int sb = far_of[t][j], ks = K(l, sb);
-                        // stored block is (max, min): k_max x k_min with ld k_max
-                        const int ldm = tr[t][j] ? ks : kt;
-                        add_item(st, mo[t][j], ldm, kt, ks, tr[t][j], xrow(l, sb));
-                    }
-                }
-            }
+    };
+    auto make_down = [&](MvStage& st, int l) {
+        st.kind = H2_STAGE_DOWN;
+        st.accumulate = 1;
+        for (int c = 0; c < (1 << (l + 1)); ++c) {
+            const int kc = K(l + 1, c), p = c >> 1, kp = K(l, p);
+            if (!kc || !kp) continue;
+            const int k1 = K(l + 1, 2 * p);
+            add_out(st, yrow(l + 1, c), kc);
+            const int64_t uo = h->uh_off[h->koff[l] + p] + ((c & 1) ? k1 : 0);
+            add_item(st, uo, k1 + K(l + 1, 2 * p + 1), kc, kp, 0, yrow(l, p));
         }
-        // 4. downsweep
-        for (int l = 1; l <= L - 1; ++l) {
-            MvStage& st = new_stage();
-            st.kind = H2_STAGE_DOWN;
-            st.accumulate = 1;
-            for (int c = 0; c < (1 << (l + 1)); ++c) {
-                const int kc = K(l + 1, c), p = c >> 1, kp = K(l, p);
-                if (!kc || !kp) continue;
-                const int k1 = K(l + 1, 2 * p), k2 = K(l + 1, 2 * p + 1);
-                add_out(st, yrow(l + 1, c), kc);
-                const int64_t uo = h->uh_off[h->koff[l] + p] + ((c & 1) ? k1 : 0);
-                add_item(st, uo, k1 + k2, kc, kp, 0, yrow(l, p));
-            }
-        }
-    }
-    // 5. leaf expansion and near field, written to Y
-    {
-        MvStage& st = new_stage();
+    };
+    auto make_expand = [&](MvStage& st, bool with_near) {
         st.kind = H2_STAGE_LEAF_NEAR;
         st.out_to_y = 1;
         std::vector<std::vector<int>> near_of(1 << L);
         std::vector<std::vector<int64_t>> mo(1 << L);
         std::vector<std::vector<int>> tr(1 << L);
-        for (size_t i = 0; i < h->near_lower.size(); ++i) {
-            auto [t, s2] = h->near_lower[i];
-            near_of[t].push_back(s2); mo[t].push_back(h->d_off[i]); tr[t].push_back(0);
-            if (t != s2) { near_of[s2].push_back(t); mo[s2].push_back(h->d_off[i]); tr[s2].push_back(1); }
-        }
+        if (with_near)
+            for (size_t i = 0; i < h->near_lower.size(); ++i) {
+                auto [t, s2] = h->near_lower[i];
+                near_of[t].push_back(s2); mo[t].push_back(h->d_off[i]); tr[t].push_back(0);
+                if (t != s2) { near_of[s2].push_back(t); mo[s2].push_back(h->d_off[i]); tr[s2].push_back(1); }
+            }
         for (int t = 0; t < (1 << L); ++t) {
             const int m = (int)T.size[L][t];
             st.outs.push_back(MvOut{T.start[L][t], 0, m, (int)st.items.size(), (int)st.items.size()});
@@ -420,14 +524,95 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
                 add_item(st, mo[t][j], ldm, m, ms, tr[t][j] | 2, T.start[L][sb]);
             }
         }
+    };
+    // ---- gather plan (any nrhs) ----
+    if (L >= 1) {
+        P.stages.emplace_back();
+        make_leaf_up(P.stages.back());
+        for (int l = L - 1; l >= 1; --l) {
+            P.stages.emplace_back();
+            make_up(P.stages.back(), l);
+        }
+        P.stages.emplace_back();
+        MvStage& st = P.stages.back();
+        st.kind = H2_STAGE_COUPLE;
+        for (int l = 1; l <= L; ++l) {
+            std::vector<std::vector<int>> far_of(1 << l);
+            std::vector<std::vector<int64_t>> mo(1 << l);
+            std::vector<std::vector<int>> tr(1 << l);
+            for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+                auto [t, s2] = h->far_lower[l][i];
+                far_of[t].push_back(s2); mo[t].push_back(h->s_off[l][i]); tr[t].push_back(0);
+                far_of[s2].push_back(t); mo[s2].push_back(h->s_off[l][i]); tr[s2].push_back(1);
+            }
+            for (int t = 0; t < (1 << l); ++t) {
+                const int kt = K(l, t);
+                if (!kt) continue;
+                add_out(st, yrow(l, t), kt);   // every box with a basis gets an output: yh starts at zero
+                for (size_t j = 0; j < far_of[t].size(); ++j) {
+                    const int sb = far_of[t][j], ks = K(l, sb);
+                    const int ldm = tr[t][j] ? ks : kt;   // stored block is k_max x k_min, ld k_max
+                    add_item(st, mo[t][j], ldm, kt, ks, tr[t][j], xrow(l, sb));
+                }
+            }
+        }
+        for (int l = 1; l <= L - 1; ++l) {
+            P.stages.emplace_back();
+            make_down(P.stages.back(), l);
+        }
+    }
+    P.stages.emplace_back();
+    make_expand(P.stages.back(), true);
+    // ---- small-nrhs plan ----
+    if (L >= 1) {
+        P.small_up.emplace_back();
+        make_leaf_up(P.small_up.back());
+        for (int l = L - 1; l >= 1; --l) {
+            P.small_up.emplace_back();
+            make_up(P.small_up.back(), l);
+        }
+        for (int l = 1; l <= L - 1; ++l) {
+            P.small_down.emplace_back();
+            make_down(P.small_down.back(), l);
+        }
+    }
+    P.small_expand = MvStage();
+    make_expand(P.small_expand, false);
+    P.small_expand.accumulate = 1;
+    P.couple = SymStage();
+    P.couple.kind = H2_STAGE_COUPLE;
+    for (int l = 1; l <= L; ++l)
+        for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+            auto [t, s2] = h->far_lower[l][i];
+            const int kt = K(l, t), ks = K(l, s2);
+            if (!kt || !ks) continue;
+            P.couple.items.push_back(SymItem{h->s_off[l][i], xrow(l, s2), yrow(l, t), xrow(l, t), yrow(l, s2), kt, kt, ks, 0});
+        }
+    P.near = SymStage();
+    P.near.kind = H2_STAGE_NEAR;
+    P.near.via_perm = 1;
+    for (size_t i = 0; i < h->near_lower.size(); ++i) {
+        auto [t, s2] = h->near_lower[i];
+        const int mt = (int)T.size[L][t], ms = (int)T.size[L][s2];
+        P.near.items.push_back(SymItem{h->d_off[i], T.start[L][s2], T.start[L][t], T.start[L][t], T.start[L][s2], mt, mt,
+                                       ms, t == s2 ? 1 : 0});
     }
     Stager stg;
-    for (MvStage& st : h->plan.stages) {
-        for (auto& it : st.items) {
+    auto up_stage = [&](MvStage& st) {
+        for (auto& it : st.items)
             if (it.rows > RMAX || it.cols > RMAX) fail(H2_ERR_INVALID_ARG, "matvec: block larger than 96");
-        }
         upload(st.d_outs, st.outs, s, stg);
         upload(st.d_items, st.items, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+    };
+    for (MvStage& st : P.stages) up_stage(st);
+    for (MvStage& st : P.small_up) up_stage(st);
+    for (MvStage& st : P.small_down) up_stage(st);
+    up_stage(P.small_expand);
+    for (SymStage* ss : {&P.couple, &P.near}) {
+        for (auto& it : ss->items)
+            if (it.rows > RMAX || it.cols > RMAX) fail(H2_ERR_INVALID_ARG, "matvec: block larger than 96");
+        upload(ss->d_items, ss->items, s, stg);
         H2_CUDA(cudaStreamSynchronize(s));
     }
 }

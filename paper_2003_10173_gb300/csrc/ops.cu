@@ -2,11 +2,13 @@
 //
 // heat2d: misfit Hessian of initial-condition inversion for the heat equation
 // on the unit square, H = F diag(mask) F / sigma^2 with F = exp(T kappa Lap_h)
-// (5-point Dirichlet Laplacian on the n x n interior grid), applied exactly by
-// the orthonormal type-I sine transform S: with the vector x read as the
-// column-major n x n array X (X[j, i] = x[i n + j]),
-//     F x  <->  S (Lambda .* (S X S)) S,   Lambda[a, b] = exp(-T kappa (mu_a + mu_b)),
-// mu_a = (4/h^2) sin^2(a pi h / 2).  Every transform is a pair of FP64 GEMMs.
+// (5-point Dirichlet Laplacian on the n x n interior grid).  The 2-D Laplacian is
+// the Kronecker sum of 1-D ones, so its exponential is a Kronecker product:
+// F = F1 (x) F1 with F1 = exp(T kappa Lap_1) = S diag(exp(-T kappa mu)) S, S the
+// orthonormal type-I sine transform and mu_a = (4/h^2) sin^2(a pi h / 2).  With the
+// vector x read as the column-major n x n array X (X[j, i] = x[i n + j]),
+//     F x  <->  F1 X F1,
+// two FP64 GEMMs per application; F1 is formed once on the device from S.
 //
 // dense: Y = A X with a caller-owned dense matrix.
 #include <cmath>
@@ -43,26 +45,20 @@ unsigned grid_for(int64_t total) {
 struct Heat2d {
     int n = 0;
     double inv_s2 = 0.0;
-    DevBuf<double> S, lam, mask, W1, W2;
+    DevBuf<double> F1, mask, W1, W2;
     GemmBatch gb;
 };
 
-// B <- F B for B = N x c contiguous; uses W as scratch.  Result in B.
+// B <- F B = F1 B_r F1 for every column r of B (N x c contiguous); W is scratch.
 void apply_F(Heat2d& H, double* B, double* W, int64_t c, cudaStream_t s) {
     const int n = H.n;
     const int64_t n2 = (int64_t)n * n;
-    for (int pass = 0; pass < 2; ++pass) {
-        // W = S * B_view  (n x n*c)
-        H.gb.add(H.S.p, n, 0, B, n, 0, W, n, n, (int)(n * c), n, 1.0, 0.0);
-        H.gb.run(s);
-        // B_r = W_r * S
-        for (int64_t r = 0; r < c; ++r) H.gb.add(W + r * n2, n, 0, H.S.p, n, 0, B + r * n2, n, n, n, n, 1.0, 0.0);
-        H.gb.run(s);
-        if (pass == 0) {
-            scale_by_kernel<<<grid_for(n2 * c), NT, 0, s>>>(B, H.lam.p, n2, n2 * c, 1.0);
-            after_launch("heat_lambda");
-        }
-    }
+    // W = F1 * B_view  (n x n*c)
+    H.gb.add(H.F1.p, n, 0, B, n, 0, W, n, n, (int)(n * c), n, 1.0, 0.0);
+    H.gb.run(s);
+    // B_r = W_r * F1
+    for (int64_t r = 0; r < c; ++r) H.gb.add(W + r * n2, n, 0, H.F1.p, n, 0, B + r * n2, n, n, n, n, 1.0, 0.0);
+    H.gb.run(s);
 }
 
 struct DenseOp {
@@ -89,19 +85,25 @@ int h2_heat2d_create(int n, double kappa, double T, double sigma, const double* 
         H->n = n;
         H->inv_s2 = 1.0 / (sigma * sigma);
         const double h = 1.0 / (n + 1);
-        std::vector<double> S((size_t)n * n), lam((size_t)n * n), mu(n);
-        for (int a = 0; a < n; ++a) {
-            mu[a] = (4.0 / (h * h)) * std::pow(std::sin(0.5 * M_PI * h * (a + 1)), 2);
-            for (int b = 0; b < n; ++b) S[a + (size_t)b * n] = std::sqrt(2.0 * h) * std::sin(M_PI * h * (double)(a + 1) * (b + 1));
+        // S and S diag(exp(-T kappa mu)) on the host, F1 = (S diag(.)) S by the library's GEMM
+        std::vector<double> S((size_t)n * n), Sa((size_t)n * n);
+        for (int b = 0; b < n; ++b) {
+            const double mu = (4.0 / (h * h)) * std::pow(std::sin(0.5 * M_PI * h * (b + 1)), 2);
+            const double ab = std::exp(-T * kappa * mu);
+            for (int a = 0; a < n; ++a) {
+                S[a + (size_t)b * n] = std::sqrt(2.0 * h) * std::sin(M_PI * h * (double)(a + 1) * (b + 1));
+                Sa[a + (size_t)b * n] = S[a + (size_t)b * n] * ab;
+            }
         }
-        for (int a = 0; a < n; ++a)
-            for (int b = 0; b < n; ++b) lam[a + (size_t)b * n] = std::exp(-T * kappa * (mu[a] + mu[b]));
         const int64_t N = (int64_t)n * n;
-        H->S.reserve(S.size());
-        H->lam.reserve(lam.size());
+        DevBuf<double> dS(S.size()), dSa(Sa.size());
+        H->F1.reserve(S.size());
         H->mask.reserve(N);
-        H2_CUDA(cudaMemcpy(H->S.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
-        H2_CUDA(cudaMemcpy(H->lam.p, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+        H2_CUDA(cudaMemcpy(dS.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+        H2_CUDA(cudaMemcpy(dSa.p, Sa.data(), Sa.size() * sizeof(double), cudaMemcpyHostToDevice));
+        H->gb.add(dSa.p, n, 0, dS.p, n, 0, H->F1.p, n, n, n, n, 1.0, 0.0);
+        H->gb.run(nullptr);
+        H2_CUDA(cudaDeviceSynchronize());
         H2_CUDA(cudaMemcpy(H->mask.p, mask_host, N * sizeof(double), cudaMemcpyHostToDevice));
         *ctx_out = H;
         return H2_OK;
