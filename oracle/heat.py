@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU
 baseline use this module.
 
 The paper's Hessians are only available through Hessian-vector products
-(Section 3.3; Eq. (2.7) gives the Gauss-Newton structure G^T K^-T F_uu K^-1 G).
+(Section 3.3; Eq. (2.5) gives the Gauss-Newton structure G^T K^-T F_uu K^-1 G).
 The synthetic stand-in is the misfit Hessian of initial-condition inversion
 for the heat equation u_t = kappa Lap u on the unit square with homogeneous
 Dirichlet data, observed at m sensor nodes at time T with noise sigma:

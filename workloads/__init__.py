@@ -9,7 +9,7 @@ any computational code.
 The workload stands in for the PDE-constrained Hessians of the paper
 (Section 4): a 2-D initial-condition inversion for the heat equation on the
 unit square, with sensor-limited data (cf. the sensor-count study of
-Section 4.2), KD-tree leaves of 64 points (Section 4.2, Section 5.2) and a
+Section 4.2), KD-tree leaves of 64 points (Section 4.2, Appendix A.1) and a
 construction tolerance of 1e-6 (Section 4.1).
 """
 from __future__ import annotations
