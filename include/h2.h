@@ -259,6 +259,10 @@ int h2_profile_read(h2_handle_t h, double* ms_out, int64_t* launches_out);
 int h2_gemm_profile(int enable);
 int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out);
 
+/* Synchronise the device and report whether a kernel of handle h recorded a failed bounded
+ * wait (H2_ERR_DEVICE_CHECK) since h was created; H2_OK otherwise. */
+int h2_device_status(h2_handle_t h);
+
 /* Statistics of the construction of h (host struct). */
 int h2_get_stats(h2_handle_t h, h2_stats* out);
 

@@ -92,6 +92,7 @@ _SIGS = {
     "h2_matvec_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
     "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "h2_profile": (_I, [_P, _I]),
+    "h2_device_status": (_I, [_P]),
     "h2_profile_read": (_I, [_P, _P, _P]),
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P]),
@@ -357,6 +358,9 @@ class H2:
         n = np.zeros(6, dtype=np.int64)
         _check(lib().h2_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    def device_status(self) -> int:
+        return int(lib().h2_device_status(self._h))
 
     def stats(self) -> dict:
         s = Stats()

@@ -332,7 +332,7 @@ int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_
         if (nrhs == 0) return H2_OK;
         require(X != nullptr && Y != nullptr, "h2_matvec_noalloc: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec_noalloc: leading dimension smaller than n");
-        require(mode == H2_FP64 || mode == H2_FP32 || mode == H2_BF16, "h2_matvec_noalloc: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_matvec_noalloc: unknown mode");
         h2::run_matvec_noalloc(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });
@@ -364,6 +364,15 @@ int h2_gemm_profile(int enable) {
 int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out) {
     return guard([&] {
         h2::gemm_profile_read(ms_out, flops_out, launches_out);
+        return H2_OK;
+    });
+}
+
+int h2_device_status(h2_handle_t h) {
+    return guard([&] {
+        require(h != nullptr, "h2_device_status: NULL handle");
+        H2_CUDA(cudaDeviceSynchronize());
+        if (h2::tc_device_error(h)) h2::fail(H2_ERR_DEVICE_CHECK, "a tensor-core kernel timed out on a bounded wait");
         return H2_OK;
     });
 }

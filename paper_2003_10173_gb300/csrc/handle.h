@@ -69,6 +69,17 @@ struct MatvecPlan {
     SymStage couple, near;
 };
 
+// Tensor-core near field: every use (t, s) of a near block, grouped by output leaf t, with
+// its op(D_ts) tile pre-rounded (BF16 or TF32) and laid out as the MMA B operand.
+struct TcPlan {
+    int LP = 0;              // padded leaf rows (16, 32 or 64)
+    int nleaf = 0;           // 0: tensor-core path unavailable
+    int64_t nitems = 0;
+    DevBuf<int> d_beg, d_src, d_leaf_size, d_err;
+    DevBuf<int64_t> d_leaf_start;
+    DevBuf<unsigned char> W16, W32, Xp;
+};
+
 struct Workspace {
     DevBuf<double> f64;
     DevBuf<float> f32;
@@ -97,6 +108,7 @@ struct h2_handle_s {
     h2::DevBuf<__nv_bfloat16> fac16;
     h2::DevBuf<int32_t> d_perm;
     h2::MatvecPlan plan;
+    h2::TcPlan tc;
     h2::Workspace ws;
     h2_stats stats{};
     // per-stage timing (h2_profile)
@@ -127,4 +139,8 @@ void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy
 void profile_read(h2_handle_s* h, double* ms, int64_t* n);
 void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                         int mode, cudaStream_t s);
+bool tc_supported(const h2_handle_s* h);
+void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s);
+void tc_near(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, cudaStream_t s);
+int tc_device_error(h2_handle_s* h);
 }  // namespace h2

@@ -362,6 +362,33 @@ void* noalloc_scratch() {
     return g_scratch_addr[dev];
 }
 
+constexpr int kTcMinNrhs = 64;
+
+// Tensor-core path: near field on tcgen05 (overwrites Y), tree part on the gather kernels,
+// then the leaf expansion adds U_t yh_t.
+template <class TS, class TX>
+void run_tc(h2_handle_s* h, int mode, const TS* fac, float* ws, const TX* X, int64_t ldx, float* Y, int64_t ldy,
+            int nrhs, cudaStream_t s) {
+    const MatvecPlan& P = h->plan;
+    const bool prof = h->prof;
+    auto timed = [&](int kind, auto&& fn) {
+        if (!prof) { fn(); return; }
+        cudaEvent_t a = take_event(h), b = take_event(h);
+        H2_CUDA(cudaEventRecord(a, s));
+        fn();
+        H2_CUDA(cudaEventRecord(b, s));
+        h->ev_used.push_back({kind, {a, b}});
+    };
+    timed(H2_STAGE_NEAR, [&] { tc_near(h, mode, X, ldx, Y, ldy, nrhs, s); });
+    for (const MvStage& st : P.stages) {
+        if (st.out_to_y) continue;   // the per-leaf gather of the near field is replaced
+        timed(st.kind, [&] { launch_stage<TS, TX, float, float>(st, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    }
+    timed(H2_STAGE_LEAF_NEAR, [&] {
+        launch_stage<TS, TX, float, float>(P.small_expand, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+    });
+}
+
 }  // namespace
 
 void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
@@ -370,6 +397,7 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
     if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: nrhs above 2,000,000");
     const size_t elt = (mode == H2_FP64) ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)h->plan.ws_rows * (size_t)nrhs * elt;
+    if (mode == H2_TF32) mode = H2_FP32;   // the tensor-core path needs a staged operand copy: not here
     if (need > kNoAllocScratchBytes)
         fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: needs " + std::to_string(need) + " bytes of scratch (" +
                                      std::to_string(h->plan.ws_rows) + " coefficient rows x " + std::to_string(nrhs) +
@@ -649,6 +677,7 @@ void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s) {
         convert_kernel<__nv_bfloat16, float><<<grid, NT, 0, s>>>(h->fac64.p, h->fac16.p, n);
         after_launch("convert_bf16");
     }
+    tc_prepare(h, keep_bf16, keep_fp32, s);
 }
 
 void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
@@ -663,19 +692,28 @@ void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy
                                                     (double*)Y, ldy, (int)nrhs, s);
             break;
         }
-        case H2_FP32: {
+        case H2_FP32:
+        case H2_TF32: {
             if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: FP32 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
-            run_all<float, float, float, float>(h, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y,
-                                                ldy, (int)nrhs, s);
+            if (mode == H2_TF32 && nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W32.p)
+                run_tc<float, float>(h, mode, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y, ldy,
+                                     (int)nrhs, s);
+            else
+                run_all<float, float, float, float>(h, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y,
+                                                    ldy, (int)nrhs, s);
             break;
         }
         case H2_BF16: {
             if (!h->fac16.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: BF16 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
-            run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, h->ws.f32.p,
-                                                                (const __nv_bfloat16*)X, ldx, (float*)Y, ldy,
-                                                                (int)nrhs, s);
+            if (nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W16.p)
+                run_tc<__nv_bfloat16, __nv_bfloat16>(h, mode, h->fac16.p, h->ws.f32.p, (const __nv_bfloat16*)X, ldx,
+                                                     (float*)Y, ldy, (int)nrhs, s);
+            else
+                run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, h->ws.f32.p,
+                                                                    (const __nv_bfloat16*)X, ldx, (float*)Y, ldy,
+                                                                    (int)nrhs, s);
             break;
         }
         default:

@@ -132,6 +132,37 @@ def test_matvec_fp64_matches_oracle(h2, kind, nrhs):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind", ["heat32_strong", "ragged", "heat64"])
+@pytest.mark.parametrize("nrhs", [64, 130])
+def test_matvec_tensor_cores_match_oracle(h2, kind, nrhs):
+    """nrhs >= 64 in BF16 / TF32 runs the near field on tcgen05 (FP32 accumulation in tensor memory).
+    Bounds against the FP64 oracle: BF16 2e-2 (8-bit mantissa), TF32 2e-3 (10-bit mantissa)."""
+    if kind == "heat64":
+        mask, op = _heat_problem(64, 256, 1002)
+        h = O.build(op, W.grid_coords(64), 64, ADM_STRONG, 0.7, 1e-6, 32, 32, 16, 256, True, 7)[0]
+        n, leaf, adm = 64, 64, ADM_STRONG
+    else:
+        h, n, leaf, adm = _oracle_h2(kind)
+    tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
+    G = h2.H2.from_factors(tree, *factors.oracle_to_import(h), keep_fp32=True, keep_bf16=True)
+    X = W.rhs(n * n, nrhs, 21)
+    want = O.matvec(h, X)
+    Xd = dev(X)
+    Yb = torch.full((nrhs, n * n), float("nan"), dtype=torch.float32, device="cuda")
+    G.matvec(Xd.to(torch.bfloat16), Yb, nrhs, h2.H2_BF16)
+    Yt = torch.full((nrhs, n * n), float("nan"), dtype=torch.float32, device="cuda")
+    G.matvec(Xd.float(), Yt, nrhs, h2.H2_TF32)
+    torch.cuda.synchronize()
+    assert G.device_status() == h2.H2_OK
+    assert rel(host(Yb), want) < 2e-2
+    assert rel(host(Yt), want) < 2e-3
+    # same inputs through the SIMT path (nrhs <= 4 columns at a time) agree column by column
+    Y4 = torch.empty((4, n * n), dtype=torch.float32, device="cuda")
+    G.matvec(Xd[:4].float(), Y4, 4, h2.H2_FP32)
+    torch.cuda.synchronize()
+    assert rel(host(Yt[:4]), host(Y4)) < 2e-3
+
+
 def test_matvec_leading_dimensions_and_empty(h2):
     h, n, leaf, adm = _oracle_h2("heat32_strong")
     tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
