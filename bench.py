@@ -111,6 +111,68 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def precision_section(h2, torch, stream, bf16_peak: float) -> dict:
+    """512 x 512 heat Hessian (N = 262,144, 16,384 sensors, kappa 0.005, rank cap 48): FP64
+    construction, then the matvec with nrhs = 1024 in FP64, TF32 and BF16 (FP32 accumulation,
+    near field on tcgen05).  Errors of the reduced-precision results are stated against the
+    FP64 matvec of the same H^2."""
+    c = W.LARGE_N512
+    p, b = c["problem"], c["build"]
+    N = p.N
+    nrhs = c["nrhs"][0]
+    mask = W.sensor_mask(N, p.m, p.sensor_seed)
+    gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, mask)
+    tree = h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta)
+    opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
+                           seed=b.seed, stream=stream, keep_fp32=1, keep_bf16=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = h2.H2.build(gop, tree, b.tol, opts)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    st = G.stats()
+    gen = torch.Generator(device="cuda").manual_seed(c["rhs_seed"])
+    X64 = torch.randn((nrhs, N), dtype=torch.float64, device="cuda", generator=gen)
+    Y64 = torch.empty_like(X64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    G.matvec(X64, Y64, nrhs, h2.H2_FP64, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": c["name"], "N": N, "nrhs": nrhs, "build_s": build_s, "samples": st["samples"],
+           "max_rank": st["max_rank"], "modes": {"FP64": {"ms": e0.elapsed_time(e1)}}}
+    _, sizes = tree.boxes(tree.L)
+    nflops = near_flops(st, sizes, nrhs)
+    for name, mode, xdt, peak in (("TF32", h2.H2_TF32, torch.float32, bf16_peak / 2.0),
+                                  ("BF16", h2.H2_BF16, torch.bfloat16, bf16_peak)):
+        X = X64.to(xdt)
+        Y = torch.empty((nrhs, N), dtype=torch.float32, device="cuda")
+        G.matvec(X, Y, nrhs, mode, stream=stream)          # warm-up
+        torch.cuda.synchronize()
+        G.profile(True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            G.matvec(X, Y, nrhs, mode, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = G.profile_read()
+        G.profile(False)
+        ms = e0.elapsed_time(e1) / reps
+        near_ms = prof["near"][0] / max(prof["near"][1], 1)
+        err = float((Y.double() - Y64).norm() / Y64.norm())
+        tf = nflops / (near_ms / 1e3) / 1e12
+        out["modes"][name] = {"ms": ms, "near_ms": near_ms, "near_TFLOPs": tf, "near_frac_of_peak": tf / peak,
+                              "peak_TFLOPs": peak, "rel_err_vs_fp64_matvec": err,
+                              "stage_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
+        del X, Y
+    assert G.device_status() == h2.H2_OK
+    del X64, Y64
+    G.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
     """The oracle as it stands on a bounded sample of the workload: the same operator family
     (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
@@ -199,6 +261,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -317,6 +380,16 @@ def main():
                 "frac_of_hbm": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9 / hbm, "hbm_peak_GBps": hbm,
                 "hbm_peak_source": hbm_src}
 
+    precision = None
+    if rank == 0 and not args.no_precision:
+        bf16_peak = 1937.9
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = float(json.load(f)["bf16_tflops"])
+        except Exception:
+            pass
+        precision = precision_section(h2, torch, stream, bf16_peak)
+
     # end to end through the public call with host buffers (pinned) and copies in the timed region
     Gp2 = results[-1][0]
     Xh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
@@ -385,6 +458,8 @@ def main():
             "build_phase_s": {k: st[k] for k in ("t_norm", "t_op", "t_peel", "t_assemble")},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         }
+        if precision is not None:
+            line["precision"] = precision
         if cpu is not None:
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(line), flush=True)

@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 
+#include <functional>
 #include <memory>
 
 #include "common.h"
@@ -69,15 +70,43 @@ struct MatvecPlan {
     SymStage couple, near;
 };
 
-// Tensor-core near field: every use (t, s) of a near block, grouped by output leaf t, with
-// its op(D_ts) tile pre-rounded (BF16 or TF32) and laid out as the MMA B operand.
+// Tensor-core products (tcgen05): output blocks with lists of items; an item multiplies rows
+// [a_row, a_row + k) of the padded operand buffer by a pre-laid-out n x k B tile.
+struct TcOut {
+    int64_t out_off;   // tree row (to_y) or workspace row of the output block
+    int rows;          // rows written
+    int n;             // MMA N (rows padded to 16)
+    int beg, end;      // item range
+    int to_y;          // 1: write Y through the permutation, 0: write the coefficient workspace
+};
+struct TcItem {
+    int64_t a_row;     // first operand row
+    int k;             // MMA K extent (padded to 16)
+    int64_t b_off;     // byte offset of the B tile in the tile pool of the precision
+};
+struct TcTileSrc {     // how a B tile is made from the FP64 factors
+    int64_t m_off, dst;
+    int ldm, trans, rows, cols, n, k;
+};
+struct TcStage {
+    std::vector<TcOut> outs;
+    std::vector<TcItem> items;     // b_off holds the tile index until packing
+    DevBuf<TcOut> d_outs;
+    DevBuf<TcItem> d_items16, d_items32;
+};
 struct TcPlan {
-    int LP = 0;              // padded leaf rows (16, 32 or 64)
+    int LP = 0;              // padded leaf rows
     int nleaf = 0;           // 0: tensor-core path unavailable
-    int64_t nitems = 0;
-    DevBuf<int> d_beg, d_src, d_leaf_size, d_err;
-    DevBuf<int64_t> d_leaf_start;
-    DevBuf<unsigned char> W16, W32, Xp;
+    int64_t op_rows = 0;     // rows of the operand buffer (X of leaves, xh and yh of boxes)
+    int64_t w_elems = 0;     // elements of a tile pool
+    int cur_eb = 0;
+    TcStage leaf_up, couple, near;
+    std::vector<int4> xh_boxes, yh_boxes;    // (operand row, k, padded k)
+    std::vector<int64_t> xh_src, yh_src;     // workspace rows
+    DevBuf<int4> d_xh_boxes, d_yh_boxes;
+    DevBuf<int64_t> d_xh_src, d_yh_src, d_leaf_start;
+    DevBuf<int> d_leaf_size, d_err;
+    DevBuf<unsigned char> W16, W32, opnd;
 };
 
 struct Workspace {
@@ -141,6 +170,8 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
                         int mode, cudaStream_t s);
 bool tc_supported(const h2_handle_s* h);
 void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s);
-void tc_near(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, cudaStream_t s);
+void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
+               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
+               const std::function<void(int, std::function<void()>)>& timed);
 int tc_device_error(h2_handle_s* h);
 }  // namespace h2

@@ -364,14 +364,14 @@ void* noalloc_scratch() {
 
 constexpr int kTcMinNrhs = 64;
 
-// Tensor-core path: near field on tcgen05 (overwrites Y), tree part on the gather kernels,
-// then the leaf expansion adds U_t yh_t.
+// Tensor-core path: leaf upsweep, couplings and near field + leaf expansion on tcgen05; the
+// transfer upsweep and downsweep on the SIMT stage kernels.
 template <class TS, class TX>
 void run_tc(h2_handle_s* h, int mode, const TS* fac, float* ws, const TX* X, int64_t ldx, float* Y, int64_t ldy,
             int nrhs, cudaStream_t s) {
     const MatvecPlan& P = h->plan;
     const bool prof = h->prof;
-    auto timed = [&](int kind, auto&& fn) {
+    std::function<void(int, std::function<void()>)> timed = [&](int kind, std::function<void()> fn) {
         if (!prof) { fn(); return; }
         cudaEvent_t a = take_event(h), b = take_event(h);
         H2_CUDA(cudaEventRecord(a, s));
@@ -379,14 +379,15 @@ void run_tc(h2_handle_s* h, int mode, const TS* fac, float* ws, const TX* X, int
         H2_CUDA(cudaEventRecord(b, s));
         h->ev_used.push_back({kind, {a, b}});
     };
-    timed(H2_STAGE_NEAR, [&] { tc_near(h, mode, X, ldx, Y, ldy, nrhs, s); });
-    for (const MvStage& st : P.stages) {
-        if (st.out_to_y) continue;   // the per-leaf gather of the near field is replaced
-        timed(st.kind, [&] { launch_stage<TS, TX, float, float>(st, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
-    }
-    timed(H2_STAGE_LEAF_NEAR, [&] {
-        launch_stage<TS, TX, float, float>(P.small_expand, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
-    });
+    std::function<void(int)> sweeps = [&](int down) {
+        for (const MvStage& st : P.stages) {
+            if (st.kind != (down ? H2_STAGE_DOWN : H2_STAGE_UP)) continue;
+            timed(st.kind, [&] {
+                launch_stage<TS, TX, float, float>(st, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+            });
+        }
+    };
+    tc_matvec(h, mode, X, ldx, Y, ldy, nrhs, ws, P.ws_rows, s, sweeps, timed);
 }
 
 }  // namespace

@@ -1,18 +1,22 @@
-// Near field of the multi-RHS matvec on the 5th-generation tensor cores (tcgen05).
+// Multi-RHS matvec products on the 5th-generation tensor cores (tcgen05), BF16 or TF32 operands
+// with FP32 accumulation in tensor memory (the precision pattern: the multi-RHS basis,
+// coupling and near-field products at reduced precision, everything else in FP32/FP64).
 //
-// For every leaf t and a tile of 128 right-hand sides, Y_t^T = sum_s X_s^T op(D_ts)^T is
-// computed as a chain of 128 x LP x 16 (BF16) or 128 x LP x 8 (TF32) MMAs with the FP32
-// accumulator in tensor memory:
-//   A operand  X_s^T  (M = rhs, K = rows of s): read from a tree-ordered, leaf-padded copy of X;
-//   B operand  op(D_ts) (N = rows of t, K = rows of s): every use of a near block (both
-//              triangles) stored once, pre-rounded and pre-laid out in the canonical
-//              K-major core-matrix layout, so a tile load is a contiguous copy.
+// Three block-sparse product lists, each output a tile of 128 right-hand sides:
+//   leaf upsweep     xh_t^T = X_t^T U_t                    (N = k_t, K = leaf rows)
+//   couplings        yh_t^T = sum_s xh_s^T S_ts^T           (N = k_t, K = k_s)
+//   near + leaves    Y_t^T  = sum_s X_s^T op(D_ts)^T + yh_t^T U_t^T   (N = leaf rows)
+// computed as chains of 128 x N x K MMAs (M = right-hand sides).  A operands are rows of one
+// padded operand buffer (X in tree order, xh and yh of every box, K-major per right-hand
+// side); B operands are the factors' blocks, one tile per use, pre-rounded and pre-laid out
+// in the canonical K-major core-matrix layout so that a tile load is a contiguous copy.
 // Operands are staged in shared memory by cp.async (3-stage ring); one thread issues the MMAs
 // and commits them to a per-stage mbarrier that releases the stage.  The accumulator is read
-// with tcgen05.ld, transposed through shared memory and written to Y through the tree
-// permutation.  Every mbarrier wait is bounded: on timeout the kernel records a device error,
-// drains its copies, frees its tensor memory and returns.
+// with tcgen05.ld, transposed through shared memory and written to Y (through the tree
+// permutation) or to the coefficient workspace.  Every mbarrier wait is bounded: on timeout
+// the kernel records a device error, drains its copies, frees its tensor memory and returns.
 #include <algorithm>
+#include <functional>
 
 #include "handle.h"
 
@@ -87,30 +91,62 @@ struct TcTraits<4> {   // TF32 operands, kind::tf32, K = 8 per MMA
     }
 };
 
-// EB: operand element bytes (2: BF16, 4: TF32 in FP32 containers); LP: padded leaf rows.
-template <int EB, int LP>
-__global__ void __launch_bounds__(TC_THREADS) mv_near_tc_kernel(
-    const int* __restrict__ item_beg, const int* __restrict__ item_src, const unsigned char* __restrict__ W,
-    const unsigned char* __restrict__ Xp, int64_t ldxp, const int32_t* __restrict__ perm,
-    const int64_t* __restrict__ leaf_start, const int* __restrict__ leaf_size, float* __restrict__ Y, int64_t ldy,
-    int nrhs, int* __restrict__ err) {
+// Block-sparse product list on tensor cores.  Output o (N_o rows, padded to 16) for a tile of
+// 128 right-hand sides: acc[r][i] = sum over items of A_item[r][k] * B_item[i][k], with
+//   A_item = rows [a_row, a_row + K) of the padded operand buffer (K-major: rows are contiguous
+//            per right-hand side), and
+//   B_item = a pre-laid-out N_o x K tile of the tile pool.
+// The accumulator is written transposed: to Y through the tree permutation (leaf outputs) or
+// to the coefficient workspace (upsweep / coupling outputs).
+constexpr int TC_NMAX = 64, TC_KMAX = 64;
+
+template <int EB>
+struct TcCfg {
+    static constexpr int STAGES = EB == 2 ? 4 : 3;
+    static constexpr int A_BYTES = TC_M * TC_KMAX * EB;
+    static constexpr int B_BYTES = TC_NMAX * TC_KMAX * EB;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES;
+};
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+template <int EB>
+__global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
+    const TcOut* __restrict__ outs, const TcItem* __restrict__ items, const unsigned char* __restrict__ W,
+    const unsigned char* __restrict__ opnd, const int32_t* __restrict__ perm, float* __restrict__ Y, int64_t ldy,
+    float* __restrict__ ws, int64_t ws_ld, int nrhs, int* __restrict__ err) {
     using Tr = TcTraits<EB>;
-    constexpr int A_BYTES = TC_M * LP * EB;
-    constexpr int B_BYTES = LP * LP * EB;
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    constexpr int TMEM_COLS = LP <= 32 ? 32 : (LP <= 64 ? 64 : 128);
+    using C = TcCfg<EB>;
+    constexpr int S = C::STAGES;
+    constexpr int TMEM_COLS = 64;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ uint32_t tmem_slot;
+    __shared__ int okflag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int t = blockIdx.x;
-    const int r0 = blockIdx.y * TC_M;
-    const int ibeg = item_beg[t], iend = item_beg[t + 1];
-    const int nitem = iend - ibeg;
+    const int rt = blockIdx.x;
+    const int r0 = rt * TC_M;
+    const TcOut o = outs[blockIdx.y];
+    const int nitem = o.end - o.beg;
+    const int N = o.n;
 
-    if (tid == 0)
-        for (int s = 0; s < TC_STAGES; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+        }
+        okflag = 1;
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(TMEM_COLS));
@@ -122,80 +158,69 @@ __global__ void __launch_bounds__(TC_THREADS) mv_near_tc_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
 
-    // issue the copies of item `it` into stage `st`
-    auto load = [&](int it, int st) {
-        unsigned char* sA = smem + st * STAGE_BYTES;
-        unsigned char* sB = sA + A_BYTES;
-        const int s = item_src[ibeg + it];
-        const unsigned char* xs = Xp + (int64_t)s * LP * EB;
-        constexpr int ACH = TC_M * LP * EB / 16;   // 16-byte chunks of A
-        for (int c = tid; c < ACH; c += TC_THREADS) {
-            const int r = c / (LP * EB / 16);
-            const int k = (c % (LP * EB / 16)) * (16 / EB);
-            const bool valid = (r0 + r) < nrhs;
-            const unsigned char* src = xs + ((int64_t)(valid ? r0 + r : 0) * ldxp + k) * EB;
-            cp_async16(smem_u32(sA + kmaj_off<EB>(r, k, LP)), src, valid);
-        }
-        const unsigned char* wb = W + (int64_t)(ibeg + it) * B_BYTES;
-        for (int c = tid; c < B_BYTES / 16; c += TC_THREADS) cp_async16(smem_u32(sB + c * 16), wb + c * 16, true);
-        asm volatile("cp.async.commit_group;");
-    };
-
-    bool ok = true;
-    const uint32_t idesc = (1u << 4) | (Tr::ab_fmt << 7) | (Tr::ab_fmt << 10) | ((uint32_t)(LP >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
-    // prologue: first TC_STAGES-1 items
-    for (int p = 0; p < TC_STAGES - 1; ++p) {
-        if (p < nitem) load(p, p);
-        else asm volatile("cp.async.commit_group;");
-    }
-    for (int it = 0; it < nitem && ok; ++it) {
-        const int nxt = it + TC_STAGES - 1;
-        if (nxt < nitem) {
-            const int st = nxt % TC_STAGES;
-            if (nxt >= TC_STAGES) {   // stage previously used by item nxt - TC_STAGES
-                const int prev = nxt - TC_STAGES;
-                ok = mbar_wait(smem_u32(&mbar[st]), (uint32_t)((prev / TC_STAGES) & 1), err);
-            }
-            if (ok) load(nxt, st);
-            else asm volatile("cp.async.commit_group;");
-        } else {
-            asm volatile("cp.async.commit_group;");
-        }
-        asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 1));
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        if (tid == 0) {
+    // one thread produces (bulk copies) and consumes (MMAs); the others wait for the epilogue
+    if (tid == 0) {
+        const uint32_t idesc = (1u << 4) | (Tr::ab_fmt << 7) | (Tr::ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        auto issue = [&](int it, int st) {
+            const TcItem m = items[o.beg + it];
+            const uint32_t abytes = (uint32_t)(TC_M * m.k * EB);
+            const uint32_t bbytes = (uint32_t)(N * m.k * EB);
+            const uint32_t sa = smem_u32(smem + st * C::STAGE_BYTES);
+            const uint32_t fb = smem_u32(&full[st]);
+            mbar_expect(fb, abytes + bbytes);
+            // block base (rows) x tiles x 128 columns, then this tile
+            const int64_t aoff = ((int64_t)m.a_row * gridDim.x * TC_M + (int64_t)rt * TC_M * m.k) * EB;
+            bulk_g2s(sa, opnd + aoff, abytes, fb);
+            bulk_g2s(sa + C::A_BYTES, W + m.b_off, bbytes, fb);
+        };
+        bool ok = true;
+        int issued = 0;
+        for (; issued < S && issued < nitem; ++issued) issue(issued, issued);
+        int done = 0;
+        for (int it = 0; it < nitem; ++it) {
+            const int st = it % S;
+            const uint32_t ph = (uint32_t)((it / S) & 1);
+            if (!mbar_wait(smem_u32(&full[st]), ph, err)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int st = it % TC_STAGES;
-            const uint32_t a0 = smem_u32(smem + st * STAGE_BYTES);
-            const uint32_t b0 = a0 + A_BYTES;
-            constexpr uint32_t SBO = (uint32_t)(LP * EB / 16) * 128;
-            for (int kk = 0; kk < LP / Tr::KSTEP; ++kk) {
+            const int K = items[o.beg + it].k;
+            const uint32_t a0 = smem_u32(smem + st * C::STAGE_BYTES);
+            const uint32_t b0 = a0 + C::A_BYTES;
+            const uint32_t SBO = (uint32_t)(K * EB / 16) * 128;
+            for (int kk = 0; kk < K / Tr::KSTEP; ++kk) {
                 const uint64_t ad = smem_desc(a0 + kk * 256, 128, SBO);
                 const uint64_t bd = smem_desc(b0 + kk * 256, 128, SBO);
                 Tr::mma(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar[st])));
+                smem_u32(&empty[st])));
+            done = it + 1;
+            if (issued < nitem) {
+                // the stage is free again once the MMAs just issued have read it
+                if (!mbar_wait(smem_u32(&empty[st]), ph, err)) { ok = false; break; }
+                issue(issued, st);
+                ++issued;
+            }
+        }
+        if (ok && nitem > 0) {
+            const int last = nitem - 1;
+            ok = mbar_wait(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1), err);
+        }
+        if (!ok) {
+            // let copies already issued land before the shared memory is reused or released
+            for (int it = done; it < issued; ++it)
+                mbar_wait(smem_u32(&full[it % S]), (uint32_t)((it / S) & 1), err);
+            okflag = 0;
         }
     }
-    asm volatile("cp.async.wait_group 0;");
-    if (ok && nitem > 0) {
-        const int last = nitem - 1;
-        ok = mbar_wait(smem_u32(&mbar[last % TC_STAGES]), (uint32_t)((last / TC_STAGES) & 1), err);
-    }
-    ok = __syncthreads_and(ok);
+    __syncthreads();
+    const bool ok = okflag != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: accumulator (lane = rhs r, column = row i of t) -> shared [r][i] -> Y
-    const int m = leaf_size[t];
     float* stage = reinterpret_cast<float*>(smem);
-    constexpr int SLD = LP + 1;
+    constexpr int SLD = TC_NMAX + 1;
     if (ok) {
         const int r = warp * 32 + (tid & 31);
-        for (int c0 = 0; c0 < LP; c0 += 16) {
+        for (int c0 = 0; c0 < N; c0 += 16) {
             uint32_t v[16];
             if (nitem > 0) {
                 asm volatile(
@@ -216,28 +241,29 @@ __global__ void __launch_bounds__(TC_THREADS) mv_near_tc_kernel(
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     if (!ok) return;
-    const int64_t st0 = leaf_start[t];
+    const int m = o.rows;
     for (int e = tid; e < m * TC_M; e += TC_THREADS) {
         const int i = e % m, r = e / m;
-        if (r0 + r < nrhs) Y[perm[st0 + i] + (int64_t)(r0 + r) * ldy] = stage[r * SLD + i];
+        if (r0 + r >= nrhs) continue;
+        const float v = stage[r * SLD + i];
+        if (o.to_y) Y[perm[o.out_off + i] + (int64_t)(r0 + r) * ldy] = v;
+        else ws[o.out_off + i + (int64_t)(r0 + r) * ws_ld] = v;
     }
 }
 
-// near-block tile of one use: op(D) (rows of t x rows of s) rounded and laid out as the B operand
+// B tiles: tile b is op(M) (valid rows x cols, zero padded to n x k) laid out as an n x k
+// K-major operand at byte offset dst[b] of the pool.
 template <int EB>
-__global__ void tc_pack_blocks_kernel(const double* __restrict__ fac, const int64_t* __restrict__ m_off,
-                                      const int* __restrict__ ldm, const int* __restrict__ trans,
-                                      const int* __restrict__ rows, const int* __restrict__ cols, int LP,
-                                      unsigned char* __restrict__ W) {
-    const int b = blockIdx.x;
-    const int nr = rows[b], nc = cols[b];
-    const double* M = fac + m_off[b];
-    unsigned char* out = W + (int64_t)b * LP * LP * EB;
-    for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
-        const int i = e % LP, j = e / LP;
+__global__ void tc_pack_tiles_kernel(const double* __restrict__ fac, const TcTileSrc* __restrict__ src,
+                                     unsigned char* __restrict__ W) {
+    const TcTileSrc d = src[blockIdx.x];
+    const double* M = fac + d.m_off;
+    unsigned char* out = W + d.dst;
+    for (int e = threadIdx.x; e < d.n * d.k; e += blockDim.x) {
+        const int i = e % d.n, j = e / d.n;
         double v = 0.0;
-        if (i < nr && j < nc) v = trans[b] ? M[j + (int64_t)i * ldm[b]] : M[i + (int64_t)j * ldm[b]];
-        const uint32_t o = kmaj_off<EB>(i, j, LP);
+        if (i < d.rows && j < d.cols) v = d.trans ? M[j + (int64_t)i * d.ldm] : M[i + (int64_t)j * d.ldm];
+        const uint32_t o = kmaj_off<EB>(i, j, d.k);
         if constexpr (EB == 2) {
             *reinterpret_cast<__nv_bfloat16*>(out + o) = __double2bfloat16(v);
         } else {
@@ -249,152 +275,313 @@ __global__ void tc_pack_blocks_kernel(const double* __restrict__ fac, const int6
     }
 }
 
-// X (caller order) -> tree-ordered, leaf-padded operand copy (BF16 or TF32-rounded FP32)
+__device__ __forceinline__ void store_opnd_bf16(unsigned char* dst, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ void store_opnd_tf32(unsigned char* dst, float v) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+    *reinterpret_cast<uint32_t*>(dst) = u;
+}
+
+// The operand buffer is tiled: operand block b (K rows: the points of a leaf, or the padded
+// coefficients of a box) and right-hand-side tile rt (128 columns) form one contiguous
+// 128 x K chunk in the canonical K-major layout, at byte base_b * nrt + rt * 128 * K * EB, where
+// base_b is the block's offset in units of 128-column tiles.  A tile load is one bulk copy.
+//
+// X (caller order) -> leaf blocks (zero padded rows and right-hand sides)
 template <class TX, int EB>
 __global__ void tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm,
                                  const int64_t* __restrict__ leaf_start, const int* __restrict__ leaf_size, int LP,
-                                 int nleaf, int nrhs, unsigned char* __restrict__ Xp, int64_t ldxp) {
-    const int64_t total = (int64_t)nleaf * LP * nrhs;
+                                 int nleaf, int nrhs, int nrt, unsigned char* __restrict__ opnd) {
+    const int64_t per_leaf = (int64_t)nrt * TC_M * LP;
+    const int64_t total = per_leaf * nleaf;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e % ((int64_t)nleaf * LP);
-        const int r = (int)(e / ((int64_t)nleaf * LP));
-        const int t = (int)(row / LP), i = (int)(row % LP);
+        const int t = (int)(e / per_leaf);
+        const int64_t w = e % per_leaf;
+        const int i = (int)(w % LP);
+        const int r = (int)(w / LP);          // global right-hand side
         float v = 0.f;
-        if (i < leaf_size[t]) {
+        if (i < leaf_size[t] && r < nrhs) {
             const TX x = X[perm[leaf_start[t] + i] + (int64_t)r * ldx];
             if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(x);
             else v = (float)x;
         }
-        unsigned char* dst = Xp + (row + (int64_t)r * ldxp) * EB;
-        if constexpr (EB == 2) {
-            *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
-        } else {
-            uint32_t u;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-            *reinterpret_cast<uint32_t*>(dst) = u;
-        }
+        const int rt = r / TC_M, rr = r % TC_M;
+        unsigned char* dst = opnd + ((int64_t)t * LP * TC_M * nrt + (int64_t)rt * TC_M * LP) * EB + kmaj_off<EB>(rr, i, LP);
+        if constexpr (EB == 2) store_opnd_bf16(dst, v);
+        else store_opnd_tf32(dst, v);
     }
 }
 
-template <int EB, int LP>
-void launch_near_tc(h2_handle_s* h, TcPlan& P, const unsigned char* W, const unsigned char* Xp, int64_t ldxp, float* Y,
-                    int64_t ldy, int nrhs, cudaStream_t s) {
-    constexpr int STAGE_BYTES = TC_M * LP * EB + LP * LP * EB;
-    const size_t smem = std::max((size_t)TC_STAGES * STAGE_BYTES, (size_t)TC_M * (LP + 1) * sizeof(float));
+// coefficient rows of the workspace -> box blocks: box list (block base row, k, kpad)
+template <int EB>
+__global__ void tc_pack_coef_kernel(const int4* __restrict__ boxes, const float* __restrict__ ws, int64_t ws_ld,
+                                    const int64_t* __restrict__ src_row, int nrhs, int nrt,
+                                    unsigned char* __restrict__ opnd) {
+    const int b = blockIdx.x;
+    const int4 d = boxes[b];   // x: block base row, y: k, z: kpad
+    const int64_t s0 = src_row[b];
+    const int kp = d.z;
+    const int64_t n = (int64_t)nrt * TC_M * kp;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = (int)(e % kp), r = (int)(e / kp);
+        const float v = (i < d.y && r < nrhs) ? ws[s0 + i + (int64_t)r * ws_ld] : 0.f;
+        const int rt = r / TC_M, rr = r % TC_M;
+        unsigned char* dst = opnd + ((int64_t)d.x * nrt * TC_M + (int64_t)rt * TC_M * kp) * EB + kmaj_off<EB>(rr, i, kp);
+        if constexpr (EB == 2) store_opnd_bf16(dst, v);
+        else store_opnd_tf32(dst, v);
+    }
+}
+
+template <int EB>
+void launch_products(const TcStage& st, const TcItem* d_items, const unsigned char* W, const unsigned char* opnd,
+                     const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld, int nrhs, int* err,
+                     cudaStream_t s) {
+    if (st.outs.empty()) return;
+    const size_t smem = std::max((size_t)TcCfg<EB>::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
     static bool attr = false;
     if (!attr) {
-        H2_CUDA(cudaFuncSetAttribute(mv_near_tc_kernel<EB, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        H2_CUDA(cudaFuncSetAttribute(tc_products_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    dim3 grid((unsigned)P.nleaf, (unsigned)((nrhs + TC_M - 1) / TC_M));
-    mv_near_tc_kernel<EB, LP><<<grid, TC_THREADS, smem, s>>>(P.d_beg.p, P.d_src.p, W, Xp, ldxp, h->d_perm.p,
-                                                             P.d_leaf_start.p, P.d_leaf_size.p, Y, ldy, nrhs, P.d_err.p);
-    after_launch("mv_near_tc");
+    dim3 grid((unsigned)((nrhs + TC_M - 1) / TC_M), (unsigned)st.outs.size());
+    tc_products_kernel<EB><<<grid, TC_THREADS, smem, s>>>(st.d_outs.p, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs,
+                                                          err);
+    after_launch("tc_products");
 }
+
+inline int pad16(int k) { return (k + 15) / 16 * 16; }
 
 }  // namespace
 
 bool tc_supported(const h2_handle_s* h) { return h->tc.nleaf > 0; }
 
-// Lists the near-block uses per leaf and packs their tensor-core tiles (both precisions kept
-// if requested).  Leaves must be at most 64 rows (padded to 16 or 32 or 64).
+// Builds the tensor-core plan: operand rows (X of every leaf, xh and yh of every box with a
+// basis), the product lists of the leaf upsweep, the couplings and the near field + leaf
+// expansion, and the B-tile pools (BF16 and/or TF32).  Requires leaves of at most 64 points.
 void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
     TcPlan& P = h->tc;
     const h2_tree_s& T = *h->tree;
     const int L = T.L;
-    if (T.leaf_max > 64 || (!want_bf16 && !want_tf32)) return;
+    if (T.leaf_max > TC_NMAX || (!want_bf16 && !want_tf32)) return;
     const int nleaf = 1 << L;
-    P.LP = T.leaf_max <= 16 ? 16 : (T.leaf_max <= 32 ? 32 : 64);
+    P.LP = pad16(T.leaf_max);
     P.nleaf = nleaf;
-    std::vector<std::vector<int>> src(nleaf), tr(nleaf);
-    std::vector<std::vector<int64_t>> mo(nleaf);
-    for (size_t i = 0; i < h->near_lower.size(); ++i) {
-        auto [t, s2] = h->near_lower[i];
-        src[t].push_back(s2); mo[t].push_back(h->d_off[i]); tr[t].push_back(0);
-        if (t != s2) { src[s2].push_back(t); mo[s2].push_back(h->d_off[i]); tr[s2].push_back(1); }
-    }
-    std::vector<int> beg(nleaf + 1, 0), isrc, ild, itr, irows, icols, lsz(nleaf);
-    std::vector<int64_t> imo, lst(nleaf);
-    for (int t = 0; t < nleaf; ++t) {
-        lst[t] = T.start[L][t];
-        lsz[t] = (int)T.size[L][t];
-        for (size_t j = 0; j < src[t].size(); ++j) {
-            const int sb = src[t][j];
-            isrc.push_back(sb);
-            imo.push_back(mo[t][j]);
-            itr.push_back(tr[t][j]);
-            irows.push_back((int)T.size[L][t]);
-            icols.push_back((int)T.size[L][sb]);
-            ild.push_back(tr[t][j] ? (int)T.size[L][sb] : (int)T.size[L][t]);
+    auto K = [&](int l, int b) { return h->k[h->koff[l] + b]; };
+    // coefficient rows of the workspace (same layout as build_plan)
+    std::vector<int64_t> box_row(h->k.size());
+    int64_t rows = 0;
+    for (size_t i = 0; i < h->k.size(); ++i) { box_row[i] = rows; rows += h->k[i]; }
+    const int64_t ytop = rows;
+    // operand rows: X of leaves, then xh (padded) of every box, then yh (padded) of leaves
+    int64_t orow = (int64_t)nleaf * P.LP;
+    std::vector<int64_t> xop(h->k.size(), -1), yop(nleaf, -1);
+    P.xh_boxes.clear();
+    P.xh_src.clear();
+    for (int l = 1; l <= L; ++l)
+        for (int b = 0; b < (1 << l); ++b) {
+            const int k = K(l, b);
+            if (!k) continue;
+            xop[h->koff[l] + b] = orow;
+            P.xh_boxes.push_back(make_int4((int)orow, k, pad16(k), 0));
+            P.xh_src.push_back(box_row[h->koff[l] + b]);
+            orow += pad16(k);
         }
-        beg[t + 1] = (int)isrc.size();
+    P.yh_boxes.clear();
+    P.yh_src.clear();
+    for (int t = 0; t < nleaf; ++t) {
+        const int k = K(L, t);
+        if (!k || L == 0) continue;
+        yop[t] = orow;
+        P.yh_boxes.push_back(make_int4((int)orow, k, pad16(k), 0));
+        P.yh_src.push_back(ytop + box_row[h->koff[L] + t]);
+        orow += pad16(k);
     }
-    P.nitems = (int64_t)isrc.size();
-    Stager st;
-    upload(P.d_beg, beg, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(P.d_src, isrc, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(P.d_leaf_start, lst, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(P.d_leaf_size, lsz, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    DevBuf<int64_t> d_mo;
-    DevBuf<int> d_ld, d_tr, d_rows, d_cols;
-    upload(d_mo, imo, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(d_ld, ild, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(d_tr, itr, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(d_rows, irows, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
-    upload(d_cols, icols, s, st);
-    H2_CUDA(cudaStreamSynchronize(s));
+    P.op_rows = (orow + 7) / 8 * 8;
+    // product lists and tile sources (byte offsets are per element size; both pools share them)
+    std::vector<TcTileSrc> tiles;
+    int64_t wpos = 0;   // in elements
+    auto add_tile = [&](int64_t m_off, int ldm, int trans, int rows_, int cols_, int n, int k) {
+        tiles.push_back(TcTileSrc{m_off, wpos, ldm, trans, rows_, cols_, n, k});
+        wpos += (int64_t)n * k;
+        return tiles.size() - 1;
+    };
+    auto build = [&](TcStage& st, std::vector<TcOut>& outs, std::vector<TcItem>& items) {
+        st.outs = outs;
+        st.items = items;
+    };
+    // 1. leaf upsweep: xh_t = U_t^T X_t   (N = pad(k_t), K = LP)
+    {
+        std::vector<TcOut> outs;
+        std::vector<TcItem> items;
+        for (int t = 0; t < nleaf && L >= 1; ++t) {
+            const int kt = K(L, t);
+            if (!kt) continue;
+            const int m = (int)T.size[L][t];
+            outs.push_back(TcOut{box_row[h->koff[L] + t], kt, pad16(kt), (int)items.size(), 0, 0});
+            const size_t ti = add_tile(h->u_off[t], m, 1, kt, m, pad16(kt), P.LP);
+            items.push_back(TcItem{(int64_t)t * P.LP, P.LP, (int64_t)ti});
+            outs.back().end = (int)items.size();
+        }
+        build(P.leaf_up, outs, items);
+    }
+    // 2. couplings: yh_t = sum_s S_ts xh_s   (N = pad(k_t), K = pad(k_s))
+    {
+        std::vector<TcOut> outs;
+        std::vector<TcItem> items;
+        for (int l = 1; l <= L; ++l) {
+            std::vector<std::vector<int>> far_of(1 << l), trn(1 << l);
+            std::vector<std::vector<int64_t>> mo(1 << l);
+            for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+                auto [t, s2] = h->far_lower[l][i];
+                far_of[t].push_back(s2); mo[t].push_back(h->s_off[l][i]); trn[t].push_back(0);
+                far_of[s2].push_back(t); mo[s2].push_back(h->s_off[l][i]); trn[s2].push_back(1);
+            }
+            for (int t = 0; t < (1 << l); ++t) {
+                const int kt = K(l, t);
+                if (!kt) continue;
+                outs.push_back(TcOut{ytop + box_row[h->koff[l] + t], kt, pad16(kt), (int)items.size(), 0, 0});
+                for (size_t j = 0; j < far_of[t].size(); ++j) {
+                    const int sb = far_of[t][j], ks = K(l, sb);
+                    if (!ks) continue;
+                    const int ldm = trn[t][j] ? ks : kt;
+                    const size_t ti = add_tile(mo[t][j], ldm, trn[t][j], kt, ks, pad16(kt), pad16(ks));
+                    items.push_back(TcItem{xop[h->koff[l] + sb], pad16(ks), (int64_t)ti});
+                }
+                outs.back().end = (int)items.size();
+            }
+        }
+        build(P.couple, outs, items);
+    }
+    // 3. near field + leaf expansion: Y_t = sum_s op(D_ts) X_s + U_t yh_t   (N = LP)
+    {
+        std::vector<std::vector<int>> src(nleaf), trn(nleaf);
+        std::vector<std::vector<int64_t>> mo(nleaf);
+        for (size_t i = 0; i < h->near_lower.size(); ++i) {
+            auto [t, s2] = h->near_lower[i];
+            src[t].push_back(s2); mo[t].push_back(h->d_off[i]); trn[t].push_back(0);
+            if (t != s2) { src[s2].push_back(t); mo[s2].push_back(h->d_off[i]); trn[s2].push_back(1); }
+        }
+        std::vector<TcOut> outs;
+        std::vector<TcItem> items;
+        for (int t = 0; t < nleaf; ++t) {
+            const int m = (int)T.size[L][t];
+            outs.push_back(TcOut{T.start[L][t], m, P.LP, (int)items.size(), 0, 1});
+            for (size_t j = 0; j < src[t].size(); ++j) {
+                const int sb = src[t][j], ms = (int)T.size[L][sb];
+                const int ldm = trn[t][j] ? ms : m;
+                const size_t ti = add_tile(mo[t][j], ldm, trn[t][j], m, ms, P.LP, P.LP);
+                items.push_back(TcItem{(int64_t)sb * P.LP, P.LP, (int64_t)ti});
+            }
+            const int kt = L >= 1 ? K(L, t) : 0;
+            if (kt) {
+                const size_t ti = add_tile(h->u_off[t], m, 0, m, kt, P.LP, pad16(kt));
+                items.push_back(TcItem{yop[t], pad16(kt), (int64_t)ti});
+            }
+            outs.back().end = (int)items.size();
+        }
+        build(P.near, outs, items);
+    }
+    for (TcStage* st : {&P.leaf_up, &P.couple, &P.near})
+        for (auto& o : st->outs)
+            if (o.n > TC_NMAX || o.n % 16) fail(H2_ERR_INVALID_ARG, "tensor-core plan: output rows out of range");
+    P.w_elems = wpos;
+    Stager stg;
+    for (TcStage* st : {&P.leaf_up, &P.couple, &P.near}) {
+        upload(st->d_outs, st->outs, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+    }
     P.d_err.reserve(1);
     H2_CUDA(cudaMemsetAsync(P.d_err.p, 0, sizeof(int), s));
-    const unsigned nb = (unsigned)std::max<int64_t>(P.nitems, 1);
-    if (want_bf16 && P.nitems) {
-        P.W16.reserve((size_t)P.nitems * P.LP * P.LP * 2);
-        tc_pack_blocks_kernel<2><<<nb, 256, 0, s>>>(h->fac64.p, d_mo.p, d_ld.p, d_tr.p, d_rows.p, d_cols.p, P.LP, P.W16.p);
-        after_launch("tc_pack_bf16");
-    }
-    if (want_tf32 && P.nitems) {
-        P.W32.reserve((size_t)P.nitems * P.LP * P.LP * 4);
-        tc_pack_blocks_kernel<4><<<nb, 256, 0, s>>>(h->fac64.p, d_mo.p, d_ld.p, d_tr.p, d_rows.p, d_cols.p, P.LP, P.W32.p);
-        after_launch("tc_pack_tf32");
-    }
+    std::vector<int64_t> lst(nleaf);
+    std::vector<int> lsz(nleaf);
+    for (int t = 0; t < nleaf; ++t) { lst[t] = T.start[L][t]; lsz[t] = (int)T.size[L][t]; }
+    upload(P.d_leaf_start, lst, s, stg);
     H2_CUDA(cudaStreamSynchronize(s));
+    upload(P.d_leaf_size, lsz, s, stg);
+    H2_CUDA(cudaStreamSynchronize(s));
+    for (int which = 0; which < 2; ++which) {
+        std::vector<int4>& bx = which ? P.yh_boxes : P.xh_boxes;
+        std::vector<int64_t>& sr = which ? P.yh_src : P.xh_src;
+        upload(which ? P.d_yh_boxes : P.d_xh_boxes, bx, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+        upload(which ? P.d_yh_src : P.d_xh_src, sr, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+    }
+    // tiles: byte offsets per precision; items refer to tile indices until here
+    DevBuf<TcTileSrc> d_tiles;
+    for (int eb : {2, 4}) {
+        if ((eb == 2 && !want_bf16) || (eb == 4 && !want_tf32) || tiles.empty()) continue;
+        std::vector<TcTileSrc> tb = tiles;
+        for (auto& t : tb) t.dst *= eb;
+        upload(d_tiles, tb, s, stg);
+        DevBuf<unsigned char>& Wp = (eb == 2) ? P.W16 : P.W32;
+        Wp.reserve((size_t)P.w_elems * eb);
+        if (eb == 2) tc_pack_tiles_kernel<2><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p);
+        else tc_pack_tiles_kernel<4><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p);
+        after_launch("tc_pack_tiles");
+        H2_CUDA(cudaStreamSynchronize(s));
+        // per-precision item lists (byte offsets of B tiles)
+        for (TcStage* st : {&P.leaf_up, &P.couple, &P.near}) {
+            std::vector<TcItem> it = st->items;
+            for (auto& x : it) x.b_off = tiles[(size_t)x.b_off].dst * eb;
+            upload(eb == 2 ? st->d_items16 : st->d_items32, it, s, stg);
+            H2_CUDA(cudaStreamSynchronize(s));
+        }
+    }
 }
 
-// Y = near field of X for a BF16 (X bf16) or TF32 (X fp32) matvec with nrhs right-hand sides.
-void tc_near(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, cudaStream_t s) {
+// Tensor-core matvec for BF16 (X bf16) or TF32 (X fp32): leaf upsweep, couplings and near field
+// + leaf expansion on tcgen05; the transfer sweeps on the SIMT stage kernels (run_tree_sweeps).
+void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
+               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
+               const std::function<void(int, std::function<void()>)>& timed) {
     TcPlan& P = h->tc;
     const int EB = (mode == H2_BF16) ? 2 : 4;
-    const int64_t rows = (int64_t)P.nleaf * P.LP;
-    const int64_t ldxp = rows;
-    P.Xp.reserve((size_t)(rows * nrhs * EB));
-    const int64_t total = rows * nrhs;
-    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-    if (mode == H2_BF16) {
-        tc_pack_x_kernel<__nv_bfloat16, 2><<<g, 256, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
-                                                              P.d_leaf_size.p, P.LP, P.nleaf, nrhs, P.Xp.p, ldxp);
-    } else {
-        tc_pack_x_kernel<float, 4><<<g, 256, 0, s>>>((const float*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
-                                                     P.d_leaf_size.p, P.LP, P.nleaf, nrhs, P.Xp.p, ldxp);
-    }
-    after_launch("tc_pack_x");
+    const int nrt = (nrhs + TC_M - 1) / TC_M;
+    P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
     const unsigned char* W = (mode == H2_BF16) ? P.W16.p : P.W32.p;
     if (!W) fail(H2_ERR_INVALID_ARG, "h2_matvec: tensor-core tiles of this precision were not kept");
-    switch (P.LP * 10 + EB) {
-        case 162: launch_near_tc<2, 16>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        case 322: launch_near_tc<2, 32>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        case 642: launch_near_tc<2, 64>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        case 164: launch_near_tc<4, 16>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        case 324: launch_near_tc<4, 32>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        case 644: launch_near_tc<4, 64>(h, P, W, P.Xp.p, ldxp, Y, ldy, nrhs, s); break;
-        default: fail(H2_ERR_INVALID_ARG, "h2_matvec: unsupported padded leaf size for tensor cores");
-    }
+    const int64_t xel = (int64_t)P.nleaf * P.LP * nrt * TC_M;
+    const unsigned g = (unsigned)std::min<int64_t>((xel + 255) / 256, 152 * 32);
+    auto run = [&](TcStage& st) {
+        if (st.outs.empty()) return;
+        if (EB == 2)
+            launch_products<2>(st, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs, P.d_err.p, s);
+        else
+            launch_products<4>(st, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs, P.d_err.p, s);
+    };
+    auto pack_coef = [&](const std::vector<int4>& bx, const DevBuf<int4>& dbx, const DevBuf<int64_t>& dsrc) {
+        if (bx.empty()) return;
+        if (EB == 2)
+            tc_pack_coef_kernel<2><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p);
+        else
+            tc_pack_coef_kernel<4><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p);
+        after_launch("tc_pack_coef");
+    };
+    P.cur_eb = EB;
+    timed(H2_STAGE_LEAF_UP, [&] {
+        if (EB == 2)
+            tc_pack_x_kernel<__nv_bfloat16, 2><<<g, 256, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p,
+                                                                  P.d_leaf_start.p, P.d_leaf_size.p, P.LP, P.nleaf,
+                                                                  nrhs, nrt, P.opnd.p);
+        else
+            tc_pack_x_kernel<float, 4><<<g, 256, 0, s>>>((const float*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
+                                                         P.d_leaf_size.p, P.LP, P.nleaf, nrhs, nrt, P.opnd.p);
+        after_launch("tc_pack_x");
+        run(P.leaf_up);
+    });
+    sweeps(0);   // transfer upsweep (SIMT)
+    timed(H2_STAGE_COUPLE, [&] {
+        pack_coef(P.xh_boxes, P.d_xh_boxes, P.d_xh_src);
+        run(P.couple);
+    });
+    sweeps(1);   // transfer downsweep (SIMT)
+    timed(H2_STAGE_NEAR, [&] {
+        pack_coef(P.yh_boxes, P.d_yh_boxes, P.d_yh_src);
+        run(P.near);
+    });
 }
 
 int tc_device_error(h2_handle_s* h) {
