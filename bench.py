@@ -173,6 +173,68 @@ def precision_section(h2, torch, stream, bf16_peak: float) -> dict:
     return out
 
 
+def batching_section(h2, torch, stream) -> dict:
+    """64 heat Hessians of uneven sizes (n ~ U{64..256}, kappa ~ U[0.002, 0.05], 5-20 % sensors):
+    batched FP64 construction and the merged, autotuned, graph-captured FP32 matvec with
+    nrhs = 64, against the plain FP64 form (one h2_build and one FP64 h2_matvec per Hessian)."""
+    probs = W.batch_problems(64)
+    b = CFG["build"]
+    nrhs = 64
+    ops = [h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed)) for p in probs]
+    trees = [h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta) for p in probs]
+    opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
+                           seed=b.seed, keep_fp32=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gs = h2.build_batched(ops, trees, b.tol, opts)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    plain_opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
+                                 seed=b.seed, stream=stream)
+    t0 = time.perf_counter()
+    plain = [h2.H2.build(op, t, b.tol, plain_opts) for op, t in zip(ops, trees)]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    gen = torch.Generator(device="cuda").manual_seed(77)
+    X64 = [torch.randn((nrhs, p.N), dtype=torch.float64, device="cuda", generator=gen) for p in probs]
+    X32 = [x.float() for x in X64]
+    Y64 = [torch.empty_like(x) for x in X64]
+    Y32 = [torch.empty_like(x) for x in X32]
+    B = h2.Batch(Gs)
+    B.matvec(X32, Y32, nrhs, h2.H2_FP32, stream=stream)     # autotune + capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        B.matvec(X32, Y32, nrhs, h2.H2_FP32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_bmv = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for _ in range(reps):
+        for G, X, Y in zip(plain, X64, Y64):
+            G.matvec(X, Y, nrhs, h2.H2_FP64, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pmv = e0.elapsed_time(e1) / reps
+    err = max(float((y32.double() - y64).norm() / y64.norm()) for y32, y64 in zip(Y32, Y64))
+    by32 = sum(matvec_bytes(G.stats(), p.N, nrhs, 4) for G, p in zip(Gs, probs))
+    by64 = sum(matvec_bytes(G.stats(), p.N, nrhs, 8) for G, p in zip(plain, probs))
+    out = {"workload": "heat2d_batch64_n64-256", "hessians": len(probs), "N_total": sum(p.N for p in probs),
+           "nrhs": nrhs, "build_batched_s": t_batched, "build_plain_fp64_s": t_plain,
+           "build_speedup": t_plain / t_batched,
+           "matvec_batched_fp32_ms": t_bmv, "matvec_plain_fp64_ms": t_pmv, "matvec_speedup": t_pmv / t_bmv,
+           "matvec_batched_GBps": by32 / (t_bmv / 1e3) / 1e9, "matvec_plain_GBps": by64 / (t_pmv / 1e3) / 1e9,
+           "rhs_tile_autotuned": B.tuned(nrhs, h2.H2_FP32), "rel_err_fp32_vs_fp64_max": err,
+           "samples_total": sum(G.stats()["samples"] for G in Gs)}
+    B.close()
+    for G in Gs + plain:
+        G.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
     """The oracle as it stands on a bounded sample of the workload: the same operator family
     (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
@@ -262,6 +324,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -390,6 +453,10 @@ def main():
             pass
         precision = precision_section(h2, torch, stream, bf16_peak)
 
+    batching = None
+    if rank == 0 and not args.no_batching:
+        batching = batching_section(h2, torch, stream)
+
     # end to end through the public call with host buffers (pinned) and copies in the timed region
     Gp2 = results[-1][0]
     Xh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
@@ -460,6 +527,8 @@ def main():
         }
         if precision is not None:
             line["precision"] = precision
+        if batching is not None:
+            line["batching"] = batching
         if cpu is not None:
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(line), flush=True)

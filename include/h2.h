@@ -39,6 +39,7 @@ extern "C" {
 typedef void* h2_stream_t;
 typedef struct h2_tree_s* h2_tree_t;
 typedef struct h2_handle_s* h2_handle_t;
+typedef struct h2_batch_s* h2_batch_t;
 
 /* ---- status codes ------------------------------------------------------- */
 enum {
@@ -197,6 +198,19 @@ int h2_factor_sizes(h2_handle_t h, int64_t* n_ranks, int64_t* n_U, int64_t* n_E,
 int h2_export(h2_handle_t h, int32_t* ranks_host, double* U_host, double* E_host, double* S_host,
               double* D_host);
 
+/*
+ * Construct count H^2 approximations (uneven sizes allowed) in one call: Hessian i uses
+ * ops[i], ctxs[i] (ctxs may be NULL), trees[i], the common tol and opts.  The builds run on
+ * a pool of up to 8 host workers with their own CUDA streams, so that the many small
+ * launches of different Hessians overlap on the GPU; each Hessian's arithmetic is exactly
+ * that of h2_build (its operator is called on the worker's stream, so callbacks must be
+ * callable from several threads for different contexts).  opts->stream is ignored; all work
+ * is complete when the call returns.  outs[i] receive the handles.  On error every handle
+ * is freed, outs are NULL, and the first error is returned; otherwise the largest warning.
+ */
+int h2_build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tree_t* trees, double tol,
+                     const h2_build_opts* opts, h2_handle_t* outs);
+
 /* ---- application ----------------------------------------------------------- */
 
 /*
@@ -262,6 +276,22 @@ int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_ou
 /* Synchronise the device and report whether a kernel of handle h recorded a failed bounded
  * wait (H2_ERR_DEVICE_CHECK) since h was created; H2_OK otherwise. */
 int h2_device_status(h2_handle_t h);
+
+/*
+ * Batched application (the batching pattern): the matvec stages of count handles are merged
+ * into one launch per stage and tree level, the per-handle pointers are read from a device
+ * table, and for every (nrhs, mode) the launch sequence is autotuned (right-hand-side tile 8,
+ * 16 or 32, timed once on the first call) and captured in a CUDA graph that later calls replay.
+ * The handles must stay alive while the batch exists.  h2_batch_matvec computes
+ * Y[i] = A_i X[i] for every handle (device buffers, leading dimensions ldx[i], ldy[i], element
+ * types as h2_matvec for `mode`; H2_TF32 runs in FP32 here).  Errors: INVALID_ARG, CUDA, OOM.
+ */
+int h2_batch_create(int count, const h2_handle_t* hs, h2_batch_t* out);
+int h2_batch_matvec(h2_batch_t b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
+                    int64_t nrhs, int mode, h2_stream_t stream);
+/* Right-hand-side tile the autotuner chose for (nrhs, mode), 0 if that key was not run yet. */
+int h2_batch_tuned(h2_batch_t b, int64_t nrhs, int mode, int* rhs_tile);
+void h2_batch_free(h2_batch_t b);
 
 /* Statistics of the construction of h (host struct). */
 int h2_get_stats(h2_handle_t h, h2_stats* out);

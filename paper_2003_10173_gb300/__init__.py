@@ -89,6 +89,11 @@ _SIGS = {
     "h2_factor_sizes": (_I, [_P, _P, _P, _P, _P, _P]),
     "h2_export": (_I, [_P, _P, _P, _P, _P, _P]),
     "h2_matvec": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
+    "h2_build_batched": (_I, [_I, _P, _P, _P, _D, ctypes.POINTER(BuildOpts), _P]),
+    "h2_batch_create": (_I, [_I, _P, ctypes.POINTER(_P)]),
+    "h2_batch_matvec": (_I, [_P, _P, _P, _P, _P, _I64, _I, _P]),
+    "h2_batch_tuned": (_I, [_P, _I64, _I, _P]),
+    "h2_batch_free": (None, [_P]),
     "h2_matvec_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
     "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "h2_profile": (_I, [_P, _I]),
@@ -387,6 +392,53 @@ def gemm_profile_read():
     ms, fl, n = _D(), _D(), _I64()
     _check(lib().h2_gemm_profile_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
     return ms.value, fl.value, n.value
+
+
+def build_batched(ops, trees, tol: float, opts: BuildOpts | None = None):
+    """Construct several H^2 matrices in one call (concurrent workers); returns a list of H2."""
+    n = len(ops)
+    fns = (ctypes.c_void_p * n)(*[o.fn.value if hasattr(o.fn, "value") else o.fn for o in ops])
+    ctxs = (ctypes.c_void_p * n)(*[o.ctx.value if isinstance(o.ctx, ctypes.c_void_p) else o.ctx for o in ops])
+    trs = (ctypes.c_void_p * n)(*[t.handle.value for t in trees])
+    outs = (ctypes.c_void_p * n)()
+    st = lib().h2_build_batched(n, fns, ctxs, trs, tol, ctypes.byref(opts) if opts is not None else None, outs)
+    _check(st, allow_warn=True)
+    return [H2(ctypes.c_void_p(outs[i]), st) for i in range(n)]
+
+
+class Batch:
+    """Merged, autotuned and graph-captured matvec over several handles (which must stay alive)."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        n = len(self.handles)
+        arr = (ctypes.c_void_p * n)(*[h._h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(lib().h2_batch_create(n, arr, ctypes.byref(b)))
+        self._b = b
+
+    def matvec(self, Xs, Ys, nrhs: int, mode: int = H2_FP64, stream=None):
+        n = len(self.handles)
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in Xs])
+        yp = (ctypes.c_void_p * n)(*[_ptr(y) for y in Ys])
+        lx = (ctypes.c_int64 * n)(*[h.stats()["n"] for h in self.handles])
+        _check(lib().h2_batch_matvec(self._b, xp, lx, yp, lx, nrhs, mode, _stream_ptr(stream)))
+
+    def tuned(self, nrhs: int, mode: int) -> int:
+        v = _I()
+        _check(lib().h2_batch_tuned(self._b, nrhs, mode, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self._b:
+            lib().h2_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

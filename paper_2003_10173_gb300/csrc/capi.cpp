@@ -9,6 +9,31 @@ namespace h2 {
 h2_tree_s* make_tree(const double* coords, int64_t N, int dim, int leaf, int adm, double eta);
 int build_handle(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, const h2_build_opts& o,
                  h2_handle_s* h);
+int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tree_t* trees, double tol,
+                  const h2_build_opts& o, h2_handle_t* outs);
+h2_batch_s* batch_create(int count, const h2_handle_t* hs);
+void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
+                  int64_t nrhs, int mode, cudaStream_t s);
+int batch_tuned(h2_batch_s* b, int64_t nrhs, int mode);
+
+// Device permutation, matvec plan, reduced-precision copies and statistics of a built handle.
+void finish_handle(h2_handle_s* h, const h2_build_opts& o, cudaStream_t s) {
+    std::vector<int32_t> perm(h->N);
+    for (int64_t i = 0; i < h->N; ++i) perm[i] = (int32_t)h->tree->perm[i];
+    h->d_perm.reserve(h->N);
+    H2_CUDA(cudaMemcpyAsync(h->d_perm.p, perm.data(), h->N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+    build_plan(h, s);
+    make_copies(h, o.keep_fp32, o.keep_bf16, s);
+    H2_CUDA(cudaStreamSynchronize(s));
+    h->stats.far_lower = 0;
+    for (auto& f : h->far_lower) h->stats.far_lower += (int64_t)f.size();
+    h->stats.near_lower = (int64_t)h->near_lower.size();
+    h->stats.entries_D = h->entries_D;
+    h->stats.entries_S = h->entries_S;
+    h->stats.entries_U = h->entries_U;
+    h->stats.entries_E = h->entries_E;
+}
 }  // namespace h2
 
 namespace {
@@ -39,7 +64,18 @@ void require(bool ok, const char* msg) {
     if (!ok) h2::fail(H2_ERR_INVALID_ARG, msg);
 }
 
-int64_t level_boxes(int l) { return (int64_t)1 << l; }
+h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
+    require(tol > 0.0 && std::isfinite(tol), "h2_build: tol must be positive");
+    h2_build_opts o;
+    h2_build_opts_default(&o);
+    if (opts) o = *opts;
+    require(o.kmax >= 1, "h2_build: kmax must be >= 1");
+    require(o.q0 >= 1 && o.q_max >= 1, "h2_build: probe counts must be >= 1");
+    require(o.b_inc >= 1 && o.b_inc <= 16, "h2_build: b_inc must be in 1..16");
+    require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
+    require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
+    return o;
+}
 
 }  // namespace
 
@@ -141,33 +177,12 @@ int h2_build(h2_op_fn op, void* ctx, h2_tree_t tree, double tol, const h2_build_
         require(out != nullptr, "h2_build: out is NULL");
         *out = nullptr;
         require(op != nullptr && tree != nullptr, "h2_build: NULL operator or tree");
-        require(tol > 0.0 && std::isfinite(tol), "h2_build: tol must be positive");
-        h2_build_opts o;
-        h2_build_opts_default(&o);
-        if (opts) o = *opts;
-        require(o.kmax >= 1, "h2_build: kmax must be >= 1");
-        require(o.q0 >= 1 && o.q_max >= 1, "h2_build: probe counts must be >= 1");
-        require(o.b_inc >= 1 && o.b_inc <= 16, "h2_build: b_inc must be in 1..16");
-        require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
-        require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
+        h2_build_opts o = checked_opts(tol, opts);
         auto* h = new h2_handle_s();
         try {
             const cudaStream_t s = (cudaStream_t)o.stream;
             const int st = h2::build_handle(op, ctx, tree, tol, o, h);
-            std::vector<int32_t> perm(h->N);
-            for (int64_t i = 0; i < h->N; ++i) perm[i] = (int32_t)h->tree->perm[i];
-            h->d_perm.reserve(h->N);
-            H2_CUDA(cudaMemcpy(h->d_perm.p, perm.data(), h->N * sizeof(int32_t), cudaMemcpyHostToDevice));
-            h2::build_plan(h, s);
-            h2::make_copies(h, o.keep_fp32, o.keep_bf16, s);
-            H2_CUDA(cudaStreamSynchronize(s));
-            h->stats.far_lower = 0;
-            for (auto& f : h->far_lower) h->stats.far_lower += (int64_t)f.size();
-            h->stats.near_lower = (int64_t)h->near_lower.size();
-            h->stats.entries_D = h->entries_D;
-            h->stats.entries_S = h->entries_S;
-            h->stats.entries_U = h->entries_U;
-            h->stats.entries_E = h->entries_E;
+            h2::finish_handle(h, o, s);
             *out = h;
             return st;
         } catch (...) {
@@ -175,6 +190,56 @@ int h2_build(h2_op_fn op, void* ctx, h2_tree_t tree, double tol, const h2_build_
             throw;
         }
     });
+}
+
+int h2_build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tree_t* trees, double tol,
+                     const h2_build_opts* opts, h2_handle_t* outs) {
+    return guard([&] {
+        require(count >= 0 && (count == 0 || (ops && trees && outs)), "h2_build_batched: NULL arrays");
+        for (int i = 0; i < count; ++i) require(ops[i] && trees[i], "h2_build_batched: NULL operator or tree");
+        h2_build_opts o = checked_opts(tol, opts);
+        if (count == 0) return (int)H2_OK;
+        return h2::build_batched(count, ops, ctxs, trees, tol, o, outs);
+    });
+}
+
+int h2_batch_create(int count, const h2_handle_t* hs, h2_batch_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_batch_create: out is NULL");
+        *out = nullptr;
+        require(count >= 1 && hs, "h2_batch_create: need at least one handle");
+        for (int i = 0; i < count; ++i) require(hs[i] != nullptr, "h2_batch_create: NULL handle");
+        *out = h2::batch_create(count, hs);
+        return H2_OK;
+    });
+}
+
+int h2_batch_matvec(h2_batch_t b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
+                    int64_t nrhs, int mode, h2_stream_t stream) {
+    return guard([&] {
+        require(b != nullptr, "h2_batch_matvec: NULL batch");
+        require(nrhs >= 0 && nrhs <= 2000000, "h2_batch_matvec: nrhs out of range");
+        if (nrhs == 0) return H2_OK;
+        require(X && Y && ldx && ldy, "h2_batch_matvec: NULL arrays");
+        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_batch_matvec: unknown mode");
+        h2::batch_matvec(b, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
+int h2_batch_tuned(h2_batch_t b, int64_t nrhs, int mode, int* rhs_tile) {
+    return guard([&] {
+        require(b && rhs_tile, "h2_batch_tuned: NULL argument");
+        *rhs_tile = h2::batch_tuned(b, nrhs, mode);
+        return H2_OK;
+    });
+}
+
+void h2_batch_free(h2_batch_t b) {
+    if (b) {
+        cudaDeviceSynchronize();
+        delete b;
+    }
 }
 
 int h2_import(h2_tree_t tree, const int32_t* ranks, const double* U, const double* E, const double* S,

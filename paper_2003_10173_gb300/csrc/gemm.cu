@@ -11,6 +11,7 @@
 // workspace and summed in a fixed order afterwards, so results do not depend
 // on scheduling.
 #include <algorithm>
+#include <mutex>
 
 #include "common.h"
 
@@ -150,6 +151,7 @@ __global__ void gemm_scale_kernel(const GemmProb* __restrict__ probs, const int4
 }
 
 struct GemmProfile {
+    std::mutex mu;   // construction workers of a batched build may run concurrently
     int on = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used;
     std::vector<cudaEvent_t> pool;
@@ -174,6 +176,7 @@ void gemm_profile_enable(int on) { g_prof.on = on; }
 
 void gemm_profile_read(double* ms, double* flops, int64_t* launches) {
     H2_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lock(g_prof.mu);
     for (auto& u : g_prof.used) {
         float t = 0.f;
         H2_CUDA(cudaEventElapsedTime(&t, u.first, u.second));
@@ -231,6 +234,8 @@ void GemmBatch::run(cudaStream_t s) {
     if (slots) d_work_.reserve((size_t)slots * TM * TN);
     if (!tiles.empty()) {
         cudaEvent_t ea = nullptr, eb = nullptr;
+        std::unique_lock<std::mutex> lock(g_prof.mu, std::defer_lock);
+        if (g_prof.on) lock.lock();
         if (g_prof.on) {
             ea = g_prof.take();
             eb = g_prof.take();

@@ -29,6 +29,19 @@ struct MvOut {
     int out_ld;
     int rows;
     int beg, end;
+    int h = 0;          // handle index in a batch (0 for single-handle plans)
+};
+
+// Per-handle bases of a batched matvec launch.
+struct BatchBase {
+    const void* fac;
+    void* ws;
+    int64_t ws_ld;
+    const int32_t* perm;
+    const void* X;
+    int64_t ldx;
+    void* Y;
+    int64_t ldy;
 };
 
 // A stage: its outputs write internal coefficient buffers, or the caller's Y via

@@ -14,6 +14,8 @@
 //   (Section 3.2: "truncated to the target accuracy via an SVD").
 #include <cfloat>
 
+#include <mutex>
+
 #include "common.h"
 
 namespace h2 {
@@ -513,13 +515,12 @@ void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const in
     w.Rbuf.reserve((size_t)std::max<int64_t>(rcount * c * c, 1));
     w.Qs.reserve((size_t)std::max<int64_t>(qscount * c * c, 1));
     const size_t smem1 = (size_t)max_h * c * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
         const int mx = kTsqrMaxRows * MAXC * (int)sizeof(double);
         H2_CUDA(cudaFuncSetAttribute(tsqr_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         H2_CUDA(cudaFuncSetAttribute(tsqr_root_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        attr = true;
-    }
+    });
     tsqr_chunk_kernel<<<(unsigned)chunks.size(), NT, smem1, s>>>(w.d_chunks.p, c, Y, ldy, Q, ldq, w.Rbuf.p);
     after_launch("tsqr_chunk");
     if (!roots.empty()) {
@@ -555,11 +556,10 @@ void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, const d
     if (count <= 0) return;
     const int np = EIG_MAXN;
     const size_t smem = 2 * (size_t)np * (np + 1) * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_set;
+    std::call_once(attr_set, [&] {
         H2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    });
     jacobi_kernel<<<count, NT, smem, s>>>(d_a_off, d_n, A, d_u_off, U, d_k_out, thr, kmax, d_cap_flag);
     after_launch("jacobi_eig");
 }

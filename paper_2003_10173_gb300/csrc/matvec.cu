@@ -36,31 +36,29 @@ template <> __device__ __forceinline__ double cvt<double, double>(double x) { re
 template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
 
 // TS: factor storage type, TX: type of X, TY: type of Y, TA: arithmetic / workspace type.
-template <class TS, class TX, class TY, class TA, bool OUT_Y>
-__device__ __forceinline__ void mv_stage_body(const MvOut* __restrict__ outs, const MvItem* __restrict__ items,
+template <class TS, class TX, class TY, class TA, bool OUT_Y, int RTT>
+__device__ __forceinline__ void mv_stage_body(const MvOut& o, const MvItem* __restrict__ items,
                                               const TS* __restrict__ fac, TA* __restrict__ ws, int64_t ws_ld,
                                               const int32_t* __restrict__ perm, const TX* __restrict__ X,
                                               int64_t ldx, TY* __restrict__ Y, int64_t ldy, int nrhs,
                                               int accumulate) {
-    constexpr bool out_to_y = OUT_Y;
+    constexpr int OPTT = (RMAX * RTT + NT - 1) / NT;
     extern __shared__ unsigned char smem_raw[];
     TA* Ms = reinterpret_cast<TA*>(smem_raw);             // [RMAX cols][RMAX+1 rows] column-major
-    TA* IN = Ms + RMAX * (RMAX + 1);                        // [RMAX rows][RT]
-    const MvOut o = outs[blockIdx.x];
-    const int r0 = blockIdx.y * RT;
-    const int nr = min(RT, nrhs - r0);
+    TA* IN = Ms + RMAX * (RMAX + 1);                        // [RMAX rows][RTT]
+    const int r0 = blockIdx.y * RTT;
+    const int nr = min(RTT, nrhs - r0);
     const int rows = o.rows;
     const int nel = rows * nr;
-    TA acc[OPT];
+    TA acc[OPTT];
 #pragma unroll
-    for (int q = 0; q < OPT; ++q) acc[q] = (TA)0;
+    for (int q = 0; q < OPTT; ++q) acc[q] = (TA)0;
 
     for (int it = o.beg; it < o.end; ++it) {
         const MvItem m = items[it];
         const int cols = m.cols;
         const TS* M = fac + m.m_off;
         const bool tr = (m.trans & 1) != 0;
-        // op(M) into Ms (column j at Ms + j*(RMAX+1))
         const int ne = rows * cols;
         for (int e = threadIdx.x; e < ne; e += NT) {
             int i, j;
@@ -73,33 +71,33 @@ __device__ __forceinline__ void mv_stage_body(const MvOut* __restrict__ outs, co
         if (m.trans & 2) {
             for (int e = threadIdx.x; e < ni; e += NT) {
                 const int j = e % cols, r = e / cols;
-                IN[j * RT + r] = cvt<TA>(X[perm[m.in_off + j] + (int64_t)(r0 + r) * ldx]);
+                IN[j * RTT + r] = cvt<TA>(X[perm[m.in_off + j] + (int64_t)(r0 + r) * ldx]);
             }
         } else {
             for (int e = threadIdx.x; e < ni; e += NT) {
                 const int j = e % cols, r = e / cols;
-                IN[j * RT + r] = ws[m.in_off + j + (int64_t)(r0 + r) * ws_ld];
+                IN[j * RTT + r] = ws[m.in_off + j + (int64_t)(r0 + r) * ws_ld];
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < OPT; ++q) {
+        for (int q = 0; q < OPTT; ++q) {
             const int e = threadIdx.x + q * NT;
             if (e < nel) {
                 const int i = e % rows, r = e / rows;
                 TA s = acc[q];
-                for (int j = 0; j < cols; ++j) s = fma(Ms[j * (RMAX + 1) + i], IN[j * RT + r], s);
+                for (int j = 0; j < cols; ++j) s = fma(Ms[j * (RMAX + 1) + i], IN[j * RTT + r], s);
                 acc[q] = s;
             }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < OPT; ++q) {
+    for (int q = 0; q < OPTT; ++q) {
         const int e = threadIdx.x + q * NT;
         if (e < nel) {
             const int i = e % rows, r = e / rows;
-            if (out_to_y) {
+            if (OUT_Y) {
                 TY* y = Y + perm[o.out_off + i] + (int64_t)(r0 + r) * ldy;
                 *y = accumulate ? (TY)(*y + acc[q]) : (TY)acc[q];
             } else {
@@ -117,7 +115,8 @@ __global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ 
                                                        const int32_t* __restrict__ perm, const TX* __restrict__ X,
                                                        int64_t ldx, TY* __restrict__ Y, int64_t ldy, int nrhs,
                                                        int accumulate) {
-    mv_stage_body<TS, TX, TY, TA, false>(outs, items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs, accumulate);
+    mv_stage_body<TS, TX, TY, TA, false, RT>(outs[blockIdx.x], items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs,
+                                             accumulate);
 }
 
 // Final stage: leaf expansion plus the dense near field, written to Y.
@@ -128,7 +127,21 @@ __global__ void __launch_bounds__(NT) mv_leaf_near_kernel(const MvOut* __restric
                                                            int64_t ws_ld, const int32_t* __restrict__ perm,
                                                            const TX* __restrict__ X, int64_t ldx, TY* __restrict__ Y,
                                                            int64_t ldy, int nrhs, int accumulate) {
-    mv_stage_body<TS, TX, TY, TA, true>(outs, items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs, accumulate);
+    mv_stage_body<TS, TX, TY, TA, true, RT>(outs[blockIdx.x], items, fac, ws, ws_ld, perm, X, ldx, Y, ldy, nrhs,
+                                            accumulate);
+}
+
+// Batched stages: outputs of several handles in one launch; each output names its handle and the
+// handle's bases (factors, workspace, permutation, X, Y) come from a device table.
+template <class TS, class TX, class TY, class TA, bool OUT_Y, int RTT>
+__global__ void __launch_bounds__(NT) mv_batch_stage_kernel(const MvOut* __restrict__ outs,
+                                                             const MvItem* __restrict__ items,
+                                                             const BatchBase* __restrict__ bases, int nrhs,
+                                                             int accumulate) {
+    const MvOut o = outs[blockIdx.x];
+    const BatchBase b = bases[o.h];
+    mv_stage_body<TS, TX, TY, TA, OUT_Y, RTT>(o, items, (const TS*)b.fac, (TA*)b.ws, b.ws_ld, b.perm, (const TX*)b.X,
+                                              b.ldx, (TY*)b.Y, b.ldy, nrhs, accumulate);
 }
 
 template <class TS, class TA>
@@ -252,14 +265,13 @@ void launch_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const
                   const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
     if (st.outs.empty()) return;
     const size_t smem = (size_t)(RMAX * (RMAX + 1) + RMAX * RT) * sizeof(TA);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(mv_stage_kernel<TS, TX, TY, TA>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         H2_CUDA(cudaFuncSetAttribute(mv_leaf_near_kernel<TS, TX, TY, TA>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    });
     dim3 grid((unsigned)st.outs.size(), (unsigned)((nrhs + RT - 1) / RT));
     if (st.out_to_y) {
         mv_leaf_near_kernel<TS, TX, TY, TA><<<grid, NT, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, perm,
@@ -424,6 +436,51 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
             fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: mode not supported");
     }
 }
+
+namespace {
+
+template <class TS, class TX, class TY, class TA, int RTT>
+void launch_batch_t(int out_y, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
+                    const BatchBase* bases, int nrhs, cudaStream_t s) {
+    const size_t smem = (size_t)(RMAX * (RMAX + 1) + RMAX * RTT) * sizeof(TA);
+    static std::once_flag once;
+    std::call_once(once, [&] {
+        H2_CUDA(cudaFuncSetAttribute(mv_batch_stage_kernel<TS, TX, TY, TA, false, RTT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        H2_CUDA(cudaFuncSetAttribute(mv_batch_stage_kernel<TS, TX, TY, TA, true, RTT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    });
+    dim3 grid((unsigned)nouts, (unsigned)((nrhs + RTT - 1) / RTT));
+    if (out_y)
+        mv_batch_stage_kernel<TS, TX, TY, TA, true, RTT><<<grid, NT, smem, s>>>(outs, items, bases, nrhs, accumulate);
+    else
+        mv_batch_stage_kernel<TS, TX, TY, TA, false, RTT><<<grid, NT, smem, s>>>(outs, items, bases, nrhs, accumulate);
+    after_launch("mv_batch_stage");
+}
+
+template <class TS, class TX, class TY, class TA>
+void launch_batch_rt(int rt, int out_y, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
+                     const BatchBase* bases, int nrhs, cudaStream_t s) {
+    switch (rt) {
+        case 8: launch_batch_t<TS, TX, TY, TA, 8>(out_y, accumulate, outs, nouts, items, bases, nrhs, s); break;
+        case 16: launch_batch_t<TS, TX, TY, TA, 16>(out_y, accumulate, outs, nouts, items, bases, nrhs, s); break;
+        default: launch_batch_t<TS, TX, TY, TA, 32>(out_y, accumulate, outs, nouts, items, bases, nrhs, s); break;
+    }
+}
+
+}  // namespace
+
+void launch_batch_stage(int mode, int rt, int out_y, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
+                        const BatchBase* bases, int nrhs, cudaStream_t s) {
+    if (mode == H2_FP64)
+        launch_batch_rt<double, double, double, double>(rt, out_y, accumulate, outs, nouts, items, bases, nrhs, s);
+    else if (mode == H2_BF16)
+        launch_batch_rt<__nv_bfloat16, __nv_bfloat16, float, float>(rt, out_y, accumulate, outs, nouts, items, bases,
+                                                                    nrhs, s);
+    else
+        launch_batch_rt<float, float, float, float>(rt, out_y, accumulate, outs, nouts, items, bases, nrhs, s);
+}
+
 
 void layout_factors(h2_handle_s* h) {
     const h2_tree_s& T = *h->tree;

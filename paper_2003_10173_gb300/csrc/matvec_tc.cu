@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <functional>
 
+#include <mutex>
+
 #include "handle.h"
 
 namespace h2 {
@@ -340,11 +342,10 @@ void launch_products(const TcStage& st, const TcItem* d_items, const unsigned ch
                      cudaStream_t s) {
     if (st.outs.empty()) return;
     const size_t smem = std::max((size_t)TcCfg<EB>::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(tc_products_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    });
     dim3 grid((unsigned)((nrhs + TC_M - 1) / TC_M), (unsigned)st.outs.size());
     tc_products_kernel<EB><<<grid, TC_THREADS, smem, s>>>(st.d_outs.p, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs,
                                                           err);
