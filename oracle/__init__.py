@@ -25,11 +25,13 @@ def basis_threshold(tol: float, norm_est: float, n_leaves: int) -> float:
     return 2.0 * tol * norm_est / (n_leaves ** 0.5)
 
 
-def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None):
+def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None,
+          q_level=None, q_test=8):
     """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result)."""
     tree = ClusterTree(coords, leaf)
     part = Partition(tree, adm, eta)
-    res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est)
+    res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est, q_level=q_level,
+               q_test=q_test)
     res.tau_basis = basis_threshold(tol, res.norm_est, 1 << tree.L)
     h = assemble(tree, part, res, res.tau_basis, kmax)
     return h, res

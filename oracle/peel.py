@@ -25,6 +25,12 @@ the paper's implementation uses:
   is the whole of R^|b| and Q_b = I (no range pass is spent).
 * Finally identity probes on every leaf give the dense diagonal leaf blocks,
   after removing all sampled pieces; they are symmetrised.
+* Predicted start counts (the learned-rank path): with q_level[l] given, level l
+  starts from q_level[l] probes instead of q0 (identity when q_level[l] >= the
+  largest child-1 box) and the first a-posteriori test uses q_test columns;
+  when that test fails, growth by b_inc resumes as above, so the prediction
+  only changes where the adaptive finder starts (Section 3.3: the per-level
+  sample count C_l k is the quantity being tuned).
 
 Pieces of level l are stored in one N x q_l array P_l (tree order): rows of
 child-1 boxes hold Q_b, rows of child-0 boxes hold Z[a], so that for every
@@ -95,6 +101,9 @@ class PeelResult:
         self.range_probes = {}    # level -> range-pass probes spent
         self.proj_probes = {}     # level -> projection-pass probes spent
         self.test_err = {}        # level -> list of max residual per pair of each adaptive test
+        self.range_calls = {}     # level -> operator calls of the range pass
+        self.passed = {}          # level -> 1 test passed, 0 no test passed, -1 identity range
+        self.need = {}            # level -> probes of the range basis that passed the test
         self.D_diag = []          # dense leaf diagonal blocks, per leaf
         self.samples = 0
         self.norm_est = 0.0
@@ -103,8 +112,10 @@ class PeelResult:
 
 
 def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, adaptive: bool,
-         seed: int, norm_est: float | None = None) -> PeelResult:
-    """Construct the sibling pieces and the leaf diagonal blocks from products with op."""
+         seed: int, norm_est: float | None = None, q_level=None, q_test: int = 8) -> PeelResult:
+    """Construct the sibling pieces and the leaf diagonal blocks from products with op.
+
+    q_level: optional sequence indexed by level (entries <= 0 mean q0) of start counts."""
     N = tree.N
     opt = TreeOperator(op, tree)
     res = PeelResult()
@@ -124,11 +135,19 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
         below = range(1, l)
         Qs = []
         res.test_err[l] = []
-        if q0 >= mb:
+        ql = q0
+        predicted = q_level is not None and l < len(q_level) and q_level[l] > 0
+        if predicted:
+            ql = int(q_level[l])
+        res.range_calls[l] = 0
+        res.passed[l] = 0
+        if ql >= mb:
             # the range of H[b, a] is all of R^|b|
             for b in B:
                 Qs.append(np.eye(b.stop - b.start))
             res.range_probes[l] = 0
+            res.passed[l] = -1
+            res.need[l] = mb
         else:
             def probe(col0, ncols):
                 Om = np.zeros((N, ncols))
@@ -138,13 +157,18 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
                     Om[a] = rng.gaussian(seed, rng.STREAM_PROBE, l, r, c)
                 return opt(Om) - apply_pieces(res.pieces, below, tree, Om)
 
-            q = q0
+            q = ql
             Y = probe(0, q)
+            res.range_calls[l] += 1
             Ys = [Y[b] for b in B]
             Qs = [np.linalg.qr(y)[0] for y in Ys]
+            res.need[l] = q
+            inc = q_test if predicted else b_inc
             while adaptive and q < q_max and q < mb:
-                c = min(b_inc, q_max - q)
+                c = min(inc, q_max - q)
+                inc = b_inc
                 Yn = probe(q, c)
+                res.range_calls[l] += 1
                 errs = []
                 for i, b in enumerate(B):
                     yb = Yn[b]
@@ -156,9 +180,13 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
                     Ys[i] = np.hstack([Ys[i], yb])
                     Qs[i] = np.linalg.qr(Ys[i])[0]
                 res.test_err[l].append(errs)
+                res.need[l] = q
                 q += c
                 if max(errs) <= thr:
+                    res.passed[l] = 1
                     break
+            if res.passed[l] != 1:
+                res.need[l] = q
             res.range_probes[l] = q
         ranks = [Q.shape[1] for Q in Qs]
         qp = max(ranks)
