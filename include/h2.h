@@ -95,6 +95,14 @@ typedef struct {
     int keep_fp32;       /* also keep an FP32 copy of the factors (enables H2_FP32/H2_TF32), default 0 */
     int keep_bf16;       /* also keep a BF16 copy of the factors (enables H2_BF16), default 0 */
     h2_stream_t stream;  /* stream for all build work and operator calls (default NULL) */
+    /* Predicted start counts (learned ranks): optional host array with at least L+1 entries,
+     * indexed by level; entry l > 0 replaces q0 at level l (identity range when it is at
+     * least the largest child-1 box of the level), entries <= 0 keep q0.  The first range
+     * test after such a start uses q_test columns; later growth uses b_inc.  The array is
+     * read during the call only.  Typically filled by h2_rankmodel_q_levels.  Default NULL. */
+    const int32_t* q_level;
+    int q_level_stride;  /* h2_build_batched: Hessian i reads q_level + i * q_level_stride (0: all share) */
+    int q_test;          /* columns of the first range test after a q_level start, 1..16 (default 8) */
 } h2_build_opts;
 
 /* Fill *opts with the defaults above.  Returns H2_ERR_INVALID_ARG if opts is NULL. */
@@ -118,6 +126,12 @@ typedef struct {
     double tau_test;                        /* threshold of the range test */
     int tol_met;                            /* 0 if a cap limited a truncation */
     double t_total, t_norm, t_op, t_peel, t_assemble;   /* seconds (host wall clock, synchronised) */
+    int64_t op_calls;                       /* operator calls of the peeling (excl. norm estimate) */
+    int range_calls[H2_MAX_LEVELS];         /* operator calls of the range pass per level */
+    int range_need[H2_MAX_LEVELS];          /* probes of the range basis that passed the test; range_probes
+                                               when no test passed; largest child-1 box for identity levels */
+    int range_passed[H2_MAX_LEVELS];        /* 1 a range test passed, 0 none passed (cap or fixed count),
+                                               -1 identity range (no range pass) */
 } h2_stats;
 
 /* ---- cluster tree and partition (host only; no CUDA calls) --------------- */
@@ -298,6 +312,72 @@ int h2_get_stats(h2_handle_t h, h2_stats* out);
 
 /* Release a handle and its device memory.  NULL is a no-op. */
 void h2_free(h2_handle_t h);
+
+/* ---- learned rank model ------------------------------------------------------ */
+
+/*
+ * A 3-layer perceptron that predicts, per tree level, the probe count the adaptive range
+ * finder settles on, so that peeling can start there (Section 3.3: the per-level sample
+ * count C_l k is the quantity being tuned; adaptive growth stays the fallback and the judge
+ * of the error).  Not a construct of the paper: a learned replacement for its hand-tuned
+ * sampling parameters.
+ *   x (H2_RM_FEATURES) -> gelu(W1 x + b1) -> gelu(W2 h1 + b2) -> y = W3 h2 + b3, width 64,
+ *   gelu(u) = u/2 (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3))); target y = log2(1 + need).
+ * Parameters (H2_RM_NPARAM floats, this order): W1 (64 x 8 row-major), b1 (64), W2 (64 x 64
+ * row-major, W2[o][i]), b2 (64), W3 (64), b3 (1).  Master weights, Adam moments and all
+ * arithmetic are FP32; with bf16 != 0 the forward and backward passes use the master
+ * weights rounded to bfloat16 (nearest even).  Training: mean squared error, Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  A model lives on the device that was
+ * current at creation; it is not thread-safe.
+ */
+#define H2_RM_FEATURES 8
+#define H2_RM_WIDTH 64
+#define H2_RM_NPARAM (64 * 8 + 64 + 64 * 64 + 64 + 64 + 1)
+typedef struct h2_rankmodel_s* h2_rankmodel_t;
+
+/* Create a model with weights drawn U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from the counter-based
+ * generator seeded with seed, zero biases, zero Adam state.  Errors: INVALID_ARG, CUDA, OOM. */
+int h2_rankmodel_create(uint64_t seed, int bf16, h2_rankmodel_t* out);
+void h2_rankmodel_free(h2_rankmodel_t m);
+
+/* Host copies of the master parameters, Adam moments (H2_RM_NPARAM floats each) and the Adam
+ * step count.  Any pointer may be NULL (get: skipped; set: that part is left unchanged, except
+ * step < 0 which keeps the count).  Synchronous. */
+int h2_rankmodel_get(h2_rankmodel_t m, float* params_host, float* adam_m_host, float* adam_v_host,
+                     int64_t* step);
+int h2_rankmodel_set(h2_rankmodel_t m, const float* params_host, const float* adam_m_host,
+                     const float* adam_v_host, int64_t step);
+
+/* Features of every level l = 0..L of tree (row l of out_host, (L+1) x H2_RM_FEATURES, row-major,
+ * host): l/L, log2(mean box size)/20, mean box diameter / root diameter, log10(kappa_T)/4,
+ * density, log10(tol)/10, log10(sqrt(kappa_T) / mean box diameter)/2, log2(n)/20, where
+ * kappa_T is the diffusivity times the final time of the heat Hessian and density the
+ * sensor fraction m/n.  Errors: INVALID_ARG (NULL, kappa_T <= 0, tol <= 0). */
+int h2_rankmodel_features(h2_tree_t tree, double kappa_T, double density, double tol, double* out_host);
+
+/* Mean squared error and its gradient with respect to the (effective) parameters over the n
+ * rows of X (device, n x H2_RM_FEATURES row-major, FP32) and targets t (device, n).  Outputs
+ * on the host (grad_host: H2_RM_NPARAM floats, may be NULL).  No update.  Synchronous. */
+int h2_rankmodel_loss_grad(h2_rankmodel_t m, const float* X, const float* t, int64_t n, float* loss_host,
+                           float* grad_host);
+
+/* steps Adam steps on minibatches of `batch` rows (1..1024) of (X, t) (device, as above), all
+ * in one launch on one CTA.  idx (device, steps x batch int32 in [0, n)) lists the rows of
+ * every minibatch; NULL draws them from the model's counter-based generator.  loss_out
+ * (device, steps floats, may be NULL) receives each minibatch's loss before its update.
+ * Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+int h2_rankmodel_train(h2_rankmodel_t m, const float* X, const float* t, int64_t n, const int32_t* idx,
+                       int steps, int batch, float lr, float* loss_out, h2_stream_t stream);
+
+/* y (device, n floats) = model(X) (device, n x H2_RM_FEATURES).  Asynchronous on stream. */
+int h2_rankmodel_predict(h2_rankmodel_t m, const float* X, int64_t n, float* y, h2_stream_t stream);
+
+/* Start counts for h2_build_opts.q_level: q_host[l] (host, L+1 entries) = ceil(2^y_l) - 1 + pad
+ * rounded up to a multiple of 8 and clamped to [8, q_max], y_l the prediction for level l of
+ * h2_rankmodel_features(tree, kappa_T, density, tol); q_host[0] = 0.  y_host (L+1 floats,
+ * may be NULL) receives the raw predictions.  Synchronous. */
+int h2_rankmodel_q_levels(h2_rankmodel_t m, h2_tree_t tree, double kappa_T, double density, double tol,
+                          int pad, int q_max, int32_t* q_host, float* y_host);
 
 /* ---- synthetic Hessians shipped with the library ------------------------- */
 

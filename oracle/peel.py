@@ -31,6 +31,9 @@ the paper's implementation uses:
   when that test fails, growth by b_inc resumes as above, so the prediction
   only changes where the adaptive finder starts (Section 3.3: the per-level
   sample count C_l k is the quantity being tuned).
+* The first test batch is drawn in the same operator call as the start block
+  (the probes are indexed by column, so this changes the number of calls, not
+  the arithmetic).
 
 Pieces of level l are stored in one N x q_l array P_l (tree order): rows of
 child-1 boxes hold Q_b, rows of child-0 boxes hold Z[a], so that for every
@@ -158,17 +161,24 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
                 return opt(Om) - apply_pieces(res.pieces, below, tree, Om)
 
             q = ql
-            Y = probe(0, q)
+            inc = q_test if predicted else b_inc
+            # the first test batch is drawn together with the start block (one operator call)
+            c1 = min(inc, q_max - q) if (adaptive and q < q_max and q < mb) else 0
+            Y = probe(0, q + c1)
             res.range_calls[l] += 1
+            pending = Y[:, q:] if c1 else None
+            Y = Y[:, :q]
             Ys = [Y[b] for b in B]
             Qs = [np.linalg.qr(y)[0] for y in Ys]
             res.need[l] = q
-            inc = q_test if predicted else b_inc
             while adaptive and q < q_max and q < mb:
                 c = min(inc, q_max - q)
                 inc = b_inc
-                Yn = probe(q, c)
-                res.range_calls[l] += 1
+                if pending is not None:
+                    Yn, pending = pending, None
+                else:
+                    Yn = probe(q, c)
+                    res.range_calls[l] += 1
                 errs = []
                 for i, b in enumerate(B):
                     yb = Yn[b]

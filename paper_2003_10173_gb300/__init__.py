@@ -45,6 +45,7 @@ class BuildOpts(ctypes.Structure):
         ("adaptive", ctypes.c_int), ("seed", ctypes.c_uint64), ("norm_est", ctypes.c_double),
         ("norm_maxit", ctypes.c_int), ("norm_rtol", ctypes.c_double), ("keep_fp32", ctypes.c_int),
         ("keep_bf16", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("q_level", ctypes.c_void_p), ("q_level_stride", ctypes.c_int), ("q_test", ctypes.c_int),
     ]
 
 
@@ -61,12 +62,15 @@ class Stats(ctypes.Structure):
         ("tol_met", ctypes.c_int),
         ("t_total", ctypes.c_double), ("t_norm", ctypes.c_double), ("t_op", ctypes.c_double),
         ("t_peel", ctypes.c_double), ("t_assemble", ctypes.c_double),
+        ("op_calls", ctypes.c_int64),
+        ("range_calls", ctypes.c_int * H2_MAX_LEVELS), ("range_need", ctypes.c_int * H2_MAX_LEVELS),
+        ("range_passed", ctypes.c_int * H2_MAX_LEVELS),
     ]
 
     def as_dict(self) -> dict:
         L = self.levels
         d = {f: getattr(self, f) for f, _ in self._fields_}
-        for k in ("range_probes", "proj_probes", "max_rank"):
+        for k in ("range_probes", "proj_probes", "max_rank", "range_calls", "range_need", "range_passed"):
             d[k] = [int(x) for x in getattr(self, k)[: L + 1]]
         return d
 
@@ -102,6 +106,15 @@ _SIGS = {
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P]),
     "h2_free": (None, [_P]),
+    "h2_rankmodel_create": (_I, [ctypes.c_uint64, _I, ctypes.POINTER(_P)]),
+    "h2_rankmodel_free": (None, [_P]),
+    "h2_rankmodel_get": (_I, [_P, _P, _P, _P, _P]),
+    "h2_rankmodel_set": (_I, [_P, _P, _P, _P, _I64]),
+    "h2_rankmodel_features": (_I, [_P, _D, _D, _D, _P]),
+    "h2_rankmodel_loss_grad": (_I, [_P, _P, _P, _I64, _P, _P]),
+    "h2_rankmodel_train": (_I, [_P, _P, _P, _I64, _P, _I, _I, ctypes.c_float, _P, _P]),
+    "h2_rankmodel_predict": (_I, [_P, _P, _I64, _P, _P]),
+    "h2_rankmodel_q_levels": (_I, [_P, _P, _D, _D, _D, _I, _I, _P, _P]),
     "h2_heat2d_create": (_I, [_I, _D, _D, _D, _P, ctypes.POINTER(_P)]),
     "h2_heat2d_apply": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P]),
     "h2_heat2d_destroy": (None, [_P]),
@@ -174,6 +187,13 @@ def default_opts(**kw) -> BuildOpts:
     for k, v in kw.items():
         if k == "stream":
             v = _stream_ptr(v)
+        if k == "q_level":
+            if v is None:
+                v = 0
+            else:
+                arr = np.ascontiguousarray(v, dtype=np.int32)
+                o._q_level_keep = arr          # the library reads it during the build call
+                v = arr.ctypes.data
         setattr(o, k, v)
     return o
 
@@ -439,6 +459,85 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+RM_FEATURES = 8
+RM_WIDTH = 64
+RM_NPARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def rank_features(tree: Tree, kappa_T: float, density: float, tol: float) -> np.ndarray:
+    """Per-level features of the rank model ((L+1) x 8, host FP64), computed by the library."""
+    out = np.empty((tree.L + 1, RM_FEATURES))
+    _check(lib().h2_rankmodel_features(tree.handle, kappa_T, density, tol, out.ctypes.data))
+    return out
+
+
+class RankModel:
+    """Learned per-level probe counts (MLP with hand-written forward/backward/Adam kernels)."""
+
+    def __init__(self, seed: int = 0, bf16: bool = True):
+        h = ctypes.c_void_p()
+        _check(lib().h2_rankmodel_create(seed, int(bf16), ctypes.byref(h)))
+        self._m = h
+        self.bf16 = bool(bf16)
+
+    def get(self):
+        p, m, v = (np.empty(RM_NPARAM, dtype=np.float32) for _ in range(3))
+        st = _I64()
+        _check(lib().h2_rankmodel_get(self._m, p.ctypes.data, m.ctypes.data, v.ctypes.data, ctypes.byref(st)))
+        return p, m, v, st.value
+
+    def set(self, params=None, adam_m=None, adam_v=None, step: int = -1):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, adam_m, adam_v)]
+        for a in arrs:
+            if a is not None and a.size != RM_NPARAM:
+                raise ValueError("parameter arrays need RM_NPARAM entries")
+        _check(lib().h2_rankmodel_set(self._m, *[a.ctypes.data if a is not None else None for a in arrs], step))
+
+    def loss_grad(self, X, t):
+        """Loss and gradient over all rows of X (device float32 n x 8) and t (device float32 n)."""
+        loss = ctypes.c_float()
+        g = np.empty(RM_NPARAM, dtype=np.float32)
+        _check(lib().h2_rankmodel_loss_grad(self._m, _ptr(X), _ptr(t), X.shape[0], ctypes.byref(loss), g.ctypes.data))
+        return float(loss.value), g
+
+    def train(self, X, t, steps: int, batch: int, lr: float, idx=None, loss_out=None, stream=None):
+        _check(lib().h2_rankmodel_train(self._m, _ptr(X), _ptr(t), X.shape[0], _ptr(idx), steps, batch, lr,
+                                        _ptr(loss_out), _stream_ptr(stream)))
+
+    def predict(self, X, y, stream=None):
+        _check(lib().h2_rankmodel_predict(self._m, _ptr(X), X.shape[0], _ptr(y), _stream_ptr(stream)))
+
+    def q_levels(self, tree: Tree, kappa_T: float, density: float, tol: float, pad: int = 8, q_max: int = 256):
+        """Start counts per level for BuildOpts.q_level and the raw predictions."""
+        q = np.empty(tree.L + 1, dtype=np.int32)
+        y = np.empty(tree.L + 1, dtype=np.float32)
+        _check(lib().h2_rankmodel_q_levels(self._m, tree.handle, kappa_T, density, tol, pad, q_max, q.ctypes.data,
+                                           y.ctypes.data))
+        return q, y
+
+    def close(self):
+        if self._m:
+            lib().h2_rankmodel_free(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rank_targets(stats: dict):
+    """(levels, log2(1 + need)) of the sampled levels of a build's statistics (identity levels skipped)."""
+    lv, tg = [], []
+    for l in range(1, stats["levels"] + 1):
+        if stats["range_passed"][l] < 0:
+            continue
+        lv.append(l)
+        tg.append(float(np.log2(1.0 + stats["range_need"][l])))
+    return lv, tg
 
 
 def launch_count() -> int:

@@ -162,6 +162,7 @@ int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tr
             try {
                 h2_build_opts oi = o;
                 oi.stream = (h2_stream_t)s;
+                if (o.q_level) oi.q_level = o.q_level + (int64_t)i * o.q_level_stride;
                 const int st = build_handle(ops[i], ctxs ? ctxs[i] : nullptr, trees[i], tol, oi, h);
                 finish_handle(h, oi, s);
                 std::lock_guard<std::mutex> lock(mu);

@@ -95,18 +95,18 @@ class Builder {
     DevBuf<BlkDesc> d_blk_;
     Pinned pin_;
     int cmax_ = 0;
-    int64_t samples_ = 0, norm_products_ = 0;
+    int64_t samples_ = 0, norm_products_ = 0, op_calls_ = 0;
     double t_op_ = 0.0;
     double norm_ = 0.0, tau_basis_ = 0.0, tau_test_ = 0.0;
     bool cap_hit_ = false;
-    std::vector<int> range_probes_, proj_probes_;
+    std::vector<int> range_probes_, proj_probes_, range_calls_, range_need_, range_passed_;
 
     void call_op(const double* X, double* Y, int ncols, bool count_sample);
-    void check_flag();
+    void check_flag(const char* where, int level);
     double norm_estimate();
     void subtract(const double* Omt, double* Yt, int c, int lmax);
     void project(int l, const std::vector<int>& pairs, int c, int c0, int passes);
-    std::vector<double> colnorm(int l, const std::vector<int>& pairs, int c);
+    std::vector<double> colnorm(int l, const std::vector<int>& pairs, int c, int c0);
     void panel(int l, const std::vector<int>& pairs, int c0, int w);
     void identity(int l, const std::vector<int>& pairs);
     void blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst);
@@ -119,6 +119,9 @@ class Builder {
         return buf.p;
     }
     double* Pl(int l) { return Pcap_.p + pcol_[l] * N_; }
+    // start count of the range pass at level l (predicted, else q0)
+    bool predicted(int l) const { return o_.q_level && o_.q_level[l] > 0; }
+    int q_start(int l) const { return predicted(l) ? o_.q_level[l] : o_.q0; }
     int64_t bstart(int l, int b) const { return T_.start[l][b]; }
     int bsize(int l, int b) const { return (int)T_.size[l][b]; }
 };
@@ -130,15 +133,21 @@ void Builder::call_op(const double* X, double* Y, int ncols, bool count_sample) 
     if (r != 0) fail(H2_ERR_OP_FAILED, "Hessian operator returned " + std::to_string(r));
     t_op_ += now_s() - t0;
     scan_finite(N_, ncols, Y, N_, d_flag_.p, s_);
-    if (count_sample) samples_ += ncols;
-    else norm_products_ += ncols;
+    if (count_sample) {
+        samples_ += ncols;
+        ++op_calls_;
+    } else {
+        norm_products_ += ncols;
+    }
 }
 
-void Builder::check_flag() {
+void Builder::check_flag(const char* where, int level) {
     int* f = pin_.get<int>(1);
     H2_CUDA(cudaMemcpyAsync(f, d_flag_.p, sizeof(int), cudaMemcpyDeviceToHost, s_));
     H2_CUDA(cudaStreamSynchronize(s_));
-    if (*f) fail(H2_ERR_NAN, "non-finite values in Hessian-vector products");
+    if (*f)
+        fail(H2_ERR_NAN, std::string("non-finite values in Hessian-vector products (") + where + ", level " +
+                             std::to_string(level) + ")");
 }
 
 // ||H||_2 by power iteration (Section 3.2) from a Gaussian start vector.
@@ -166,7 +175,7 @@ double Builder::norm_estimate() {
     double lam = 0.0, prev = 0.0;
     for (int it = 1; it <= o_.norm_maxit; ++it) {
         call_op(v, w, 1, false);
-        check_flag();
+        check_flag("norm estimate", 0);
         lam = std::sqrt(sqnorm(w));
         if (lam == 0.0) break;
         scale(w, 1.0 / lam);
@@ -233,11 +242,11 @@ void Builder::project(int l, const std::vector<int>& pairs, int c, int c0, int p
     }
 }
 
-std::vector<double> Builder::colnorm(int l, const std::vector<int>& pairs, int c) {
+std::vector<double> Builder::colnorm(int l, const std::vector<int>& pairs, int c, int c0) {
     std::vector<int64_t> off;
     std::vector<int> m;
     for (int i : pairs) {
-        off.push_back(bstart(l, 2 * i + 1));
+        off.push_back(bstart(l, 2 * i + 1) + (int64_t)c0 * N_);
         m.push_back(bsize(l, 2 * i + 1));
     }
     std::vector<double> out(pairs.size(), 0.0);
@@ -304,8 +313,9 @@ void Builder::peel_level(int l) {
         gather_rows(N_, c, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
         subtract(Ot_.p, Yt_.p, c, l - 1);
     };
-    // orthonormalise a batch of c new columns of Yt into the bases; returns max residual of the test
-    auto orth_batch = [&](int c, bool test) {
+    // orthonormalise the c new columns [off, off + c) of Yt into the bases; returns the max
+    // residual of the test
+    auto orth_batch = [&](int c, bool test, int off) {
         std::vector<int> active, full;
         for (int i : all) {
             const int m = bsize(l, 2 * i + 1);
@@ -317,32 +327,60 @@ void Builder::peel_level(int l) {
         if (test) {
             std::vector<int> tp = active;
             tp.insert(tp.end(), full.begin(), full.end());
-            project(l, tp, c, 0, 2);
-            for (double e : colnorm(l, tp, c)) err = std::max(err, e);
+            project(l, tp, c, off, 2);
+            for (double e : colnorm(l, tp, c, off)) err = std::max(err, e);
         }
         identity(l, full);
         for (int c0 = 0; c0 < c; c0 += PANEL) {
             const int w = std::min(PANEL, c - c0);
-            panel(l, active, c0, w);
+            panel(l, active, off + c0, w);
         }
         return err;
     };
-    if (o_.q0 >= mb) {
+    const int q1 = q_start(l);
+    int calls = 0, need = 0, passed = 0;
+    if (q1 >= mb) {
         identity(l, all);
+        need = mb;
+        passed = -1;
     } else {
-        range_batch(0, o_.q0);
-        orth_batch(o_.q0, false);
-        int q = o_.q0;
+        // after a predicted start the first test uses q_test columns, later growth b_inc
+        int inc = predicted(l) ? o_.q_test : o_.b_inc;
+        // the first test batch is drawn with the start block: one operator call for both
+        const int c1 = (o_.adaptive && q1 < o_.q_max && q1 < mb) ? std::min(inc, o_.q_max - q1) : 0;
+        range_batch(0, q1 + c1);
+        ++calls;
+        orth_batch(q1, false, 0);
+        int q = q1;
+        need = q;
+        bool pending = c1 > 0;
         while (o_.adaptive && q < o_.q_max && q < mb) {
-            const int c = std::min(o_.b_inc, o_.q_max - q);
-            range_batch(q, c);
-            const double err = orth_batch(c, true);
+            const int c = std::min(inc, o_.q_max - q);
+            inc = o_.b_inc;
+            int off = 0;
+            if (pending) {
+                off = q1;          // columns [q1, q1 + c1) of the first call
+                pending = false;
+            } else {
+                range_batch(q, c);
+                ++calls;
+            }
+            const double err = orth_batch(c, true, off);
+            need = q;
             q += c;
-            if (err <= thr) break;
+            if (err <= thr) {
+                passed = 1;
+                break;
+            }
         }
+        if (passed != 1) need = q;
         range = q;
         if (o_.adaptive && q >= o_.q_max && q < mb) cap_hit_ = true;
     }
+    range_calls_[l] = calls;
+    range_need_[l] = need;
+    range_passed_[l] = passed;
+    check_flag("range pass", l);
     int qp = 0;
     for (int i : all) qp = std::max(qp, kb_[l][i]);
     // projection pass: Psi (tree order) is P_l itself (Q_b on child-1 rows, zero elsewhere)
@@ -360,7 +398,7 @@ void Builder::peel_level(int l) {
     qw_[l] = qp;
     range_probes_[l] = range;
     proj_probes_[l] = qp;
-    check_flag();
+    check_flag("projection pass", l);
 }
 
 // Identity probes on every leaf give the dense diagonal blocks once all pieces are removed.
@@ -386,7 +424,7 @@ void Builder::leaf_pass() {
     for (int t = 0; t < nleaf; ++t)
         d.push_back(BlkDesc{bstart(L_, t), ddiag_off_[t], bsize(L_, t), bsize(L_, t), (int)N_, bsize(L_, t)});
     blocks(BLK_SYMMETRIZE, d, Yt_.p, Ddiag_.p);
-    check_flag();
+    check_flag("leaf pass", L_);
 }
 
 // Recompression of the sampled pieces into nested orthonormal bases, couplings and
@@ -675,13 +713,19 @@ void Builder::run(h2_handle_s* h) {
     kb_.assign(L_ + 1, {});
     range_probes_.assign(L_ + 1, 0);
     proj_probes_.assign(L_ + 1, 0);
+    range_calls_.assign(L_ + 1, 0);
+    range_need_.assign(L_ + 1, 0);
+    range_passed_.assign(L_ + 1, 0);
     int64_t pc = 0;
     int qcmax = 1;
-    cmax_ = std::max({o_.q0, o_.b_inc, T_.leaf_max, 1});
+    cmax_ = std::max({o_.q0, o_.b_inc, o_.q_test, T_.leaf_max, 1});
     for (int l = 1; l <= L_; ++l) {
         int mb = 0;
         for (int i = 0; i < (1 << (l - 1)); ++i) mb = std::max(mb, bsize(l, 2 * i + 1));
-        qcap_[l] = (o_.q0 >= mb) ? mb : std::min(std::max(o_.q_max, o_.q0), mb);
+        const int q1 = q_start(l);
+        qcap_[l] = (q1 >= mb) ? mb : std::min(std::max(o_.q_max, q1), mb);
+        // the first call draws the start block and the first test batch
+        if (q1 < mb) cmax_ = std::max(cmax_, q1 + std::max(o_.q_test, o_.b_inc));
         pcol_[l] = pc;
         pc += qcap_[l];
         qcmax = std::max(qcmax, qcap_[l]);
@@ -718,9 +762,13 @@ void Builder::run(h2_handle_s* h) {
     st.leaf_max = T_.leaf_max;
     st.samples = samples_;
     st.norm_products = norm_products_;
+    st.op_calls = op_calls_;
     for (int l = 0; l <= L_ && l < H2_MAX_LEVELS; ++l) {
         st.range_probes[l] = range_probes_[l];
         st.proj_probes[l] = proj_probes_[l];
+        st.range_calls[l] = range_calls_[l];
+        st.range_need[l] = range_need_[l];
+        st.range_passed[l] = range_passed_[l];
         int mx = 0;
         for (int b = 0; b < (1 << l); ++b) mx = std::max(mx, h->k[h->koff[l] + b]);
         st.max_rank[l] = mx;

@@ -15,6 +15,17 @@ h2_batch_s* batch_create(int count, const h2_handle_t* hs);
 void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
                   int64_t nrhs, int mode, cudaStream_t s);
 int batch_tuned(h2_batch_s* b, int64_t nrhs, int mode);
+h2_rankmodel_s* rm_create(uint64_t seed, int bf16);
+void rm_free(h2_rankmodel_s* m);
+void rm_get(h2_rankmodel_s* m, float* p, float* am, float* av, int64_t* step);
+void rm_set(h2_rankmodel_s* m, const float* p, const float* am, const float* av, int64_t step);
+void rm_features(const h2_tree_s* t, double kT, double dens, double tol, double* out);
+void rm_train(h2_rankmodel_s* m, const float* X, const float* T, int64_t n, const int32_t* idx, int steps, int batch,
+              float lr, float* loss_out, cudaStream_t s);
+void rm_loss_grad(h2_rankmodel_s* m, const float* X, const float* T, int64_t n, float* loss, float* grad);
+void rm_predict(h2_rankmodel_s* m, const float* X, int64_t n, float* Y, cudaStream_t s);
+void rm_q_levels(h2_rankmodel_s* m, const h2_tree_s* t, double kT, double dens, double tol, int pad, int q_max,
+                 int32_t* q, float* y_host);
 
 // Device permutation, matvec plan, reduced-precision copies and statistics of a built handle.
 void finish_handle(h2_handle_s* h, const h2_build_opts& o, cudaStream_t s) {
@@ -72,6 +83,8 @@ h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
     require(o.kmax >= 1, "h2_build: kmax must be >= 1");
     require(o.q0 >= 1 && o.q_max >= 1, "h2_build: probe counts must be >= 1");
     require(o.b_inc >= 1 && o.b_inc <= 16, "h2_build: b_inc must be in 1..16");
+    require(o.q_test >= 1 && o.q_test <= 16, "h2_build: q_test must be in 1..16");
+    require(o.q_level_stride >= 0, "h2_build: q_level_stride must be >= 0");
     require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
     require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
     return o;
@@ -96,6 +109,9 @@ int h2_build_opts_default(h2_build_opts* o) {
     o->keep_fp32 = 0;
     o->keep_bf16 = 0;
     o->stream = nullptr;
+    o->q_level = nullptr;
+    o->q_level_stride = 0;
+    o->q_test = 8;
     return H2_OK;
 }
 
@@ -240,6 +256,86 @@ void h2_batch_free(h2_batch_t b) {
         cudaDeviceSynchronize();
         delete b;
     }
+}
+
+int h2_rankmodel_create(uint64_t seed, int bf16, h2_rankmodel_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_rankmodel_create: out is NULL");
+        *out = nullptr;
+        *out = h2::rm_create(seed, bf16);
+        return H2_OK;
+    });
+}
+
+void h2_rankmodel_free(h2_rankmodel_t m) {
+    if (m) {
+        cudaDeviceSynchronize();
+        h2::rm_free(m);
+    }
+}
+
+int h2_rankmodel_get(h2_rankmodel_t m, float* p, float* am, float* av, int64_t* step) {
+    return guard([&] {
+        require(m != nullptr, "h2_rankmodel_get: NULL model");
+        h2::rm_get(m, p, am, av, step);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_set(h2_rankmodel_t m, const float* p, const float* am, const float* av, int64_t step) {
+    return guard([&] {
+        require(m != nullptr, "h2_rankmodel_set: NULL model");
+        h2::rm_set(m, p, am, av, step);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_features(h2_tree_t tree, double kappa_T, double density, double tol, double* out) {
+    return guard([&] {
+        require(tree && out, "h2_rankmodel_features: NULL argument");
+        require(kappa_T > 0.0 && std::isfinite(kappa_T), "h2_rankmodel_features: kappa_T must be positive");
+        require(tol > 0.0 && std::isfinite(tol), "h2_rankmodel_features: tol must be positive");
+        require(std::isfinite(density), "h2_rankmodel_features: density must be finite");
+        h2::rm_features(tree, kappa_T, density, tol, out);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_loss_grad(h2_rankmodel_t m, const float* X, const float* t, int64_t n, float* loss, float* grad) {
+    return guard([&] {
+        require(m != nullptr, "h2_rankmodel_loss_grad: NULL model");
+        h2::rm_loss_grad(m, X, t, n, loss, grad);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_train(h2_rankmodel_t m, const float* X, const float* t, int64_t n, const int32_t* idx, int steps,
+                       int batch, float lr, float* loss_out, h2_stream_t stream) {
+    return guard([&] {
+        require(m != nullptr, "h2_rankmodel_train: NULL model");
+        h2::rm_train(m, X, t, n, idx, steps, batch, lr, loss_out, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_predict(h2_rankmodel_t m, const float* X, int64_t n, float* y, h2_stream_t stream) {
+    return guard([&] {
+        require(m != nullptr, "h2_rankmodel_predict: NULL model");
+        h2::rm_predict(m, X, n, y, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_q_levels(h2_rankmodel_t m, h2_tree_t tree, double kappa_T, double density, double tol, int pad,
+                          int q_max, int32_t* q, float* y) {
+    return guard([&] {
+        require(m && tree && q, "h2_rankmodel_q_levels: NULL argument");
+        require(kappa_T > 0.0 && std::isfinite(kappa_T) && tol > 0.0 && std::isfinite(tol) && std::isfinite(density),
+                "h2_rankmodel_q_levels: bad kappa_T, density or tol");
+        require(pad >= 0 && q_max >= 8, "h2_rankmodel_q_levels: need pad >= 0 and q_max >= 8");
+        h2::rm_q_levels(m, tree, kappa_T, density, tol, pad, q_max, q, y);
+        return H2_OK;
+    });
 }
 
 int h2_import(h2_tree_t tree, const int32_t* ranks, const double* U, const double* E, const double* S,

@@ -24,6 +24,21 @@ struct Error : std::runtime_error {
 void check_cuda(cudaError_t e, const char* what);
 #define H2_CUDA(call) ::h2::check_cuda((call), #call)
 
+// SplitMix64 (Steele, Lea, Flood 2014): output finaliser and the i-th output of
+// a generator seeded with `key`.
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+__host__ __device__ inline uint64_t splitmix_at(uint64_t key, uint64_t idx) {
+    return mix64(key + (idx + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
 extern std::atomic<int64_t> g_launches;
 // Call after every kernel launch: counts it and turns a launch error into an Error.
 void after_launch(const char* name);

@@ -457,9 +457,11 @@ __global__ void __launch_bounds__(NT) tsqr_apply_kernel(const TsqrChunk* __restr
     // qs position: Qs block rows [kc*c, kc*c+c) of the panel's Qs with leading dimension ldqs
     const int64_t base = d.qs_off;
     const int ldqs = d.ldqs;
-    for (int e = threadIdx.x; e < c * c; e += NT) {
-        const int i = e % c, k = e / c;
-        B[i + k * MAXC] = Qs[base + i + (int64_t)k * ldqs];
+    // the whole MAXC x MAXC tile is written (zeros outside c x c): the product below runs over
+    // all MAXC rows, and stale shared memory times a zero factor could be NaN
+    for (int e = threadIdx.x; e < MAXC * MAXC; e += NT) {
+        const int i = e % MAXC, k = e / MAXC;
+        B[e] = (i < c && k < c) ? Qs[base + i + (int64_t)k * ldqs] : 0.0;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < d.rows; i += NT) {

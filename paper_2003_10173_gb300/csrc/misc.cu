@@ -9,21 +9,6 @@ namespace {
 
 constexpr int NT = 256;
 
-// SplitMix64 (Steele, Lea, Flood 2014): output finaliser and the i-th output of
-// a generator seeded with `key`.
-__host__ __device__ inline uint64_t mix64(uint64_t z) {
-    z ^= z >> 30;
-    z *= 0xBF58476D1CE4E5B9ull;
-    z ^= z >> 27;
-    z *= 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return z;
-}
-
-__host__ __device__ inline uint64_t splitmix_at(uint64_t key, uint64_t idx) {
-    return mix64(key + (idx + 1ull) * 0x9E3779B97F4A7C15ull);
-}
-
 // Gaussian of entry (row, col) by Box-Muller from two SplitMix64 outputs.
 __device__ inline double gauss_at(uint64_t key, uint64_t row, uint64_t col) {
     const uint64_t c = (col << 32) + row;

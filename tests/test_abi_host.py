@@ -92,3 +92,31 @@ def test_argument_validation(h2):
     L.h2_tree_free(None)
     o = h2.default_opts()
     assert (o.kmax, o.q0, o.b_inc, o.q_max, o.adaptive) == (32, 32, 16, 256, 1)
+    assert (o.q_level, o.q_level_stride, o.q_test) == (None, 0, 8)
+
+
+@pytest.mark.parametrize("n,leaf,adm", [(4, 4, ADM_WEAK), (37, 16, ADM_STRONG), (64, 64, ADM_STRONG)])
+def test_rank_features_match_oracle(h2, n, leaf, adm):
+    """The library's per-level rank-model features equal the oracle's (host code, no GPU)."""
+    from oracle import mlp
+    coords = W.grid_coords(n)
+    t = h2.Tree(coords, leaf, adm, 0.7)
+    got = h2.rank_features(t, 0.005, 0.125, 1e-6)
+    want = mlp.level_features(ClusterTree(coords, leaf), 0.005, 0.125, 1e-6)
+    assert got.shape == want.shape
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+
+
+def test_rank_model_argument_validation(h2):
+    L = h2.lib()
+    t = h2.Tree(W.grid_coords(8), 8)
+    out = np.empty((t.L + 1, 8))
+    assert L.h2_rankmodel_features(t.handle, -1.0, 0.1, 1e-6, out.ctypes.data) == h2.H2_ERR_INVALID_ARG
+    assert L.h2_rankmodel_features(t.handle, 0.01, 0.1, 0.0, out.ctypes.data) == h2.H2_ERR_INVALID_ARG
+    assert L.h2_rankmodel_features(None, 0.01, 0.1, 1e-6, out.ctypes.data) == h2.H2_ERR_INVALID_ARG
+    assert L.h2_rankmodel_train(None, None, None, 1, None, 1, 1, 1e-3, None, None) == h2.H2_ERR_INVALID_ARG
+    assert L.h2_rankmodel_create(0, 1, None) == h2.H2_ERR_INVALID_ARG
+    L.h2_rankmodel_free(None)
+    o = h2.default_opts(q_test=0)
+    assert L.h2_build(None, None, None, 1e-6, ctypes.byref(o), ctypes.byref(ctypes.c_void_p())) == \
+        h2.H2_ERR_INVALID_ARG
