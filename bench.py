@@ -235,6 +235,94 @@ def batching_section(h2, torch, stream) -> dict:
     return out
 
 
+def rel_err_2norm(h2, torch, gop, G, N: int, norm_est: float, stream) -> float:
+    """||H - H~||_2 / ||H||_2 by power iteration through the GPU operator and the FP64 matvec."""
+    v = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    w1 = torch.empty_like(v)
+    w2 = torch.empty_like(v)
+    lam, prev = 0.0, 0.0
+    v /= v.norm()
+    for it in range(60):
+        gop.apply(v, w1, 1, stream=stream)
+        G.matvec(v, w2, 1, h2.H2_FP64, stream=stream)
+        w = w1 - w2
+        lam = float(w.norm())
+        if lam == 0:
+            break
+        v = w / lam
+        if it > 0 and abs(lam - prev) <= 1e-2 * lam:
+            break
+        prev = lam
+    return lam / norm_est
+
+
+def learned_ranks_section(h2, torch, stream, gop, tree, opts, st_adaptive, build_s_adaptive) -> dict:
+    """Rank model trained on adaptive builds of 64 heat Hessians at 128 x 128 (kappa ~ U[0.002, 0.05],
+    5-20 % sensors; fine probing q0 16, b_inc 8), then the benchmark Hessian built from the predicted
+    per-level start counts (pad 8, first test 8 columns) against plain adaptive peeling."""
+    p, b = CFG["problem"], CFG["build"]
+    probs = W.batch_problems(64, seed=2025, n_lo=128, n_hi=128)
+    ops = [h2.HeatOperator(q.n, q.kappa, q.T, q.sigma, W.sensor_mask(q.N, q.m, q.sensor_seed)) for q in probs]
+    trees = [h2.Tree(W.grid_coords(q.n), b.leaf, b.adm, b.eta) for q in probs]
+    fine = h2.default_opts(kmax=b.kmax, q0=16, b_inc=8, q_max=b.q_max, adaptive=1, seed=b.seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gs = h2.build_batched(ops, trees, b.tol, fine)
+    t_data = time.perf_counter() - t0
+    feats, targ = [], []
+    for q, t, G in zip(probs, trees, Gs):
+        f = h2.rank_features(t, q.kappa * q.T, q.m / q.N, b.tol)
+        lv, tg = h2.rank_targets(G.stats())
+        feats.append(f[lv])
+        targ += tg
+        G.close()
+    X = torch.from_numpy(np.concatenate(feats).astype(np.float32)).cuda()
+    y = torch.from_numpy(np.asarray(targ, dtype=np.float32)).cuda()
+    model = h2.RankModel(seed=1, bf16=True)
+    p0 = model.get()[0]
+    p0[-1] = float(y.mean())
+    model.set(p0)
+    steps = 3000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    model.train(X, y, steps, 64, 3e-3, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_train_ms = e0.elapsed_time(e1)
+    loss, _ = model.loss_grad(X, y)
+    ql, yl = model.q_levels(tree, p.kappa * p.T, p.m / p.N, b.tol, pad=8, q_max=b.q_max)
+    lopts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=1, seed=b.seed,
+                            stream=stream, q_level=ql, q_test=8)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Gm = h2.H2.build(gop, tree, b.tol, lopts)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        sm = Gm.stats()
+        if len(times) < 3:
+            Gm.close()
+    err = rel_err_2norm(h2, torch, gop, Gm, p.N, sm["norm_est"], stream)
+    out = {"train_workload": "heat2d_n128 x 64 (adaptive q0 16, b_inc 8)", "train_rows": int(y.numel()),
+           "train_data_build_s": t_data, "train_steps": steps, "train_batch": 64, "train_ms": t_train_ms,
+           "train_launches": 1, "train_loss_log2": loss,
+           "q_start": [int(v) for v in ql], "predicted_log2": [round(float(v), 3) for v in yl],
+           "adaptive": {"op_calls": st_adaptive["op_calls"], "samples": st_adaptive["samples"],
+                        "range_calls": st_adaptive["range_calls"], "range_probes": st_adaptive["range_probes"],
+                        "build_s": build_s_adaptive, "t_peel": st_adaptive["t_peel"]},
+           "learned": {"op_calls": sm["op_calls"], "samples": sm["samples"], "range_calls": sm["range_calls"],
+                       "range_probes": sm["range_probes"], "range_passed": sm["range_passed"],
+                       "build_s": float(np.median(times)), "t_peel": sm["t_peel"], "rel_err_2norm": err}}
+    out["op_calls_saved"] = 1.0 - sm["op_calls"] / st_adaptive["op_calls"]
+    out["samples_saved"] = 1.0 - sm["samples"] / st_adaptive["samples"]
+    out["build_speedup"] = build_s_adaptive / out["learned"]["build_s"]
+    Gm.close()
+    model.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
     """The oracle as it stands on a bounded sample of the workload: the same operator family
     (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
@@ -325,6 +413,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -485,23 +574,11 @@ def main():
     # accuracy of the last build (2-norm, power iteration through the GPU matvec and operator)
     rel_err = None
     if rank == 0:
-        v = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
-        w1 = torch.empty_like(v)
-        w2 = torch.empty_like(v)
-        lam, prev = 0.0, 0.0
-        v /= v.norm()
-        for it in range(60):
-            gop.apply(v, w1, 1, stream=stream)
-            Gp2.matvec(v, w2, 1, h2.H2_FP64, stream=stream)
-            w = w1 - w2
-            lam = float(w.norm())
-            if lam == 0:
-                break
-            v = w / lam
-            if it > 0 and abs(lam - prev) <= 1e-2 * lam:
-                break
-            prev = lam
-        rel_err = lam / st["norm_est"]
+        rel_err = rel_err_2norm(h2, torch, gop, Gp2, N, st["norm_est"], stream)
+
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_ranks_section(h2, torch, stream, gop, tree, opts, st, float(np.mean(build_ms)) / 1e3)
 
     if rank == 0:
         line = {
@@ -529,6 +606,8 @@ def main():
             line["precision"] = precision
         if batching is not None:
             line["batching"] = batching
+        if learned is not None:
+            line["learned_ranks"] = learned
         if cpu is not None:
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(line), flush=True)
