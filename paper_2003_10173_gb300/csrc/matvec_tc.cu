@@ -10,8 +10,10 @@
 // padded operand buffer (X in tree order, xh and yh of every box, K-major per right-hand
 // side); B operands are the factors' blocks, one tile per use, pre-rounded and pre-laid out
 // in the canonical K-major core-matrix layout so that a tile load is a contiguous copy.
-// Operands are staged in shared memory by cp.async (3-stage ring); one thread issues the MMAs
-// and commits them to a per-stage mbarrier that releases the stage.  The accumulator is read
+// One producer thread stages each item's A and B tiles in shared memory with bulk asynchronous
+// copies (cp.async.bulk, completion counted in bytes on a per-stage mbarrier) into a ring of
+// 4 (BF16) or 3 (TF32) stages; one thread issues the MMAs and commits them to a per-stage
+// mbarrier that releases the stage.  The accumulator is read
 // with tcgen05.ld, transposed through shared memory and written to Y (through the tree
 // permutation) or to the coefficient workspace.  Every mbarrier wait is bounded: on timeout
 // the kernel records a device error, drains its copies, frees its tensor memory and returns.
@@ -47,11 +49,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;   // descriptor version of tcgen05; no swizzle, base offset 0
     return d;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n));
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
