@@ -19,6 +19,7 @@ same workload (see cpu_baseline) and the same JSON line is printed with
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -35,6 +36,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
 CFG = W.MEDIUM_N256
+# DRAM bytes (read + write) per gemm_tiles_kernel launch of a bench step, from an ncu capture
+# of the same kernel (null until taken for the current kernel)
+GEMM_TRAFFIC_PER_LAUNCH = None
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
@@ -111,12 +115,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def precision_section(h2, torch, stream, bf16_peak: float) -> dict:
+def scaled(cfg: dict, n: int) -> dict:
+    """The configuration on an n x n grid with the same sensor fraction (profiling captures)."""
+    p = cfg["problem"]
+    if n == p.n:
+        return cfg
+    m = max(1, round(p.m * n * n / p.N))
+    return dict(cfg, name=f"{cfg['name']}_at_n{n}", problem=dataclasses.replace(p, n=n, m=m))
+
+
+def precision_section(h2, torch, stream, bf16_peak: float, n: int = 512) -> dict:
     """512 x 512 heat Hessian (N = 262,144, 16,384 sensors, kappa 0.005, rank cap 48): FP64
     construction, then the matvec with nrhs = 1024 in FP64, TF32 and BF16 (FP32 accumulation,
     near field on tcgen05).  Errors of the reduced-precision results are stated against the
-    FP64 matvec of the same H^2."""
-    c = W.LARGE_N512
+    FP64 matvec of the same H^2.  n other than 512 (profiling) keeps the sensor fraction."""
+    c = scaled(W.LARGE_N512, n)
     p, b = c["problem"], c["build"]
     N = p.N
     nrhs = c["nrhs"][0]
@@ -414,7 +427,13 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
+    ap.add_argument("--precision-n", type=int, default=512, help="grid size of the precision section")
     args = ap.parse_args()
+    global CFG
+    if args.n is not None:
+        CFG = scaled(CFG, args.n)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -518,15 +537,20 @@ def main():
     nr_ms, nr_n = prof["near"]
     nr_s = nr_ms / nr_n / 1e3
     achieved = near_flops(st, sizes, 1) / nr_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64, "unit": "TFLOP/s", "frac": achieved / fp64,
-                "traffic": None, "kernel": "mv_scatter_kernel<double,...,1,true> (near field, nrhs=1)",
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                "hbm_GBps": st["entries_D"] * 8 / nr_s / 1e9}
+    roofline_matvec = {"bound": "alu", "achieved": achieved, "peak": fp64, "unit": "TFLOP/s",
+                       "frac": achieved / fp64, "traffic": None,
+                       "kernel": "mv_scatter_kernel<double,...,1,true> (near field, nrhs=1)",
+                       "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                       "hbm_GBps": st["entries_D"] * 8 / nr_s / 1e9}
+    # dominant kernel of a step (about two thirds of the device time): the construction's FP64
+    # batched GEMM, timed per launch with events on the build stream over the timed steps
     gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
-    roofline_build = {"bound": "alu", "achieved": gemm_tf, "peak": fp64, "unit": "TFLOP/s",
-                      "frac": (gemm_tf / fp64) if gemm_tf else None, "traffic": None,
-                      "kernel": "gemm_tiles_kernel (FP64 batched GEMM: operator DSTs, piece subtraction, Gram)",
-                      "launches": gemm_n, "ms": gemm_ms}
+    roofline = {"bound": "alu", "achieved": gemm_tf, "peak": fp64, "unit": "TFLOP/s",
+                "frac": (gemm_tf / fp64) if gemm_tf else None, "traffic": GEMM_TRAFFIC_PER_LAUNCH,
+                "kernel": "gemm_tiles_kernel (FP64 batched GEMM: operator DSTs, piece subtraction, Gram)",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                "launches": gemm_n, "ms": gemm_ms,
+                "flops_per_launch": gemm_flops / max(gemm_n, 1), "ms_per_launch": gemm_ms / max(gemm_n, 1)}
     near_bytes = st["entries_D"] * 8
     hbm_view = {"nrhs1_matvec_GBps": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9,
                 "frac_of_hbm": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9 / hbm, "hbm_peak_GBps": hbm,
@@ -540,7 +564,7 @@ def main():
                 bf16_peak = float(json.load(f)["bf16_tflops"])
         except Exception:
             pass
-        precision = precision_section(h2, torch, stream, bf16_peak)
+        precision = precision_section(h2, torch, stream, bf16_peak, args.precision_n)
 
     batching = None
     if rank == 0 and not args.no_batching:
@@ -597,7 +621,7 @@ def main():
             "matvec_GBps": {str(nr): by[nr] / (np.mean(mv_ms[nr]) / 1e3) / 1e9 for nr in nrhs_list},
             "stored_bytes_fp64": (st["entries_D"] + st["entries_S"] + st["entries_U"] + st["entries_E"]) * 8,
             "hbm_view": hbm_view,
-            "roofline": roofline, "roofline_build": roofline_build,
+            "roofline": roofline, "roofline_matvec": roofline_matvec,
             "stage_ms_nrhs1": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
             "build_phase_s": {k: st[k] for k in ("t_norm", "t_op", "t_peel", "t_assemble")},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,

@@ -9,7 +9,8 @@
 // is low enough that a register-blocked 4x4 per thread keeps it busy).  Long
 // reductions with few output tiles are split along k into slots of a
 // workspace and summed in a fixed order afterwards, so results do not depend
-// on scheduling.
+// on scheduling.  Launches with fewer output tiles than two per SM split every reduction so
+// that the grid covers the GPU (e.g. the heat operator on one or a few vectors).
 #include <algorithm>
 #include <mutex>
 
@@ -20,6 +21,8 @@ namespace h2 {
 namespace {
 
 constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+constexpr int64_t kFillCtas = 2 * 152;   // two resident CTAs on each of the 152 SMs
+constexpr int kMinChunk = 32;            // shortest k range of a split
 
 __global__ void __launch_bounds__(NT) gemm_tiles_kernel(const GemmProb* __restrict__ probs,
                                                          const int4* __restrict__ tiles,
@@ -197,6 +200,12 @@ void GemmBatch::run(cudaStream_t s) {
     if (probs_.empty()) return;
     std::vector<int4> tiles, red, scale;
     int slots = 0;
+    // output tiles of the whole launch; below two CTAs per SM every reduction is split (chunks of
+    // at least kMinChunk) until the launch fills the GPU
+    int64_t base_tiles = 0;
+    for (const GemmProb& p : probs_)
+        if (p.k > 0) base_tiles += (int64_t)((p.m + TM - 1) / TM) * ((p.n + TN - 1) / TN);
+    const int fill = (base_tiles > 0 && base_tiles < kFillCtas) ? (int)((kFillCtas + base_tiles - 1) / base_tiles) : 1;
     for (size_t pi = 0; pi < probs_.size(); ++pi) {
         const GemmProb& p = probs_[pi];
         if (p.m >= (1 << 16) * TM || p.n >= (1 << 16) * TN)
@@ -207,13 +216,11 @@ void GemmBatch::run(cudaStream_t s) {
                 for (int b = 0; b < nt; ++b) scale.push_back(make_int4((int)pi, a | (b << 16), 0, -1));
             continue;
         }
-        // split long reductions when the problem has few output tiles
-        int ns = 1;
+        int ns = std::min(fill, std::max(1, p.k / kMinChunk));
+        // long reductions with few output tiles are split further
         const int ntile = mt * nt;
-        if (p.k >= 2048 && ntile < 64) {
-            ns = std::min(std::max(1, p.k / 1024), std::max(1, 128 / ntile));
-            ns = std::min(ns, 64);
-        }
+        if (p.k >= 2048 && ntile < 64) ns = std::max(ns, std::min(std::max(1, p.k / 1024), std::max(1, 128 / ntile)));
+        ns = std::min(ns, 64);
         for (int a = 0; a < mt; ++a)
             for (int b = 0; b < nt; ++b) {
                 const int tyx = a | (b << 16);
