@@ -270,70 +270,74 @@ def rel_err_2norm(h2, torch, gop, G, N: int, norm_est: float, stream) -> float:
     return lam / norm_est
 
 
-def learned_ranks_section(h2, torch, stream, gop, tree, opts, st_adaptive, build_s_adaptive) -> dict:
-    """Rank model trained on adaptive builds of 64 heat Hessians at 128 x 128 (kappa ~ U[0.002, 0.05],
-    5-20 % sensors; fine probing q0 16, b_inc 8), then the benchmark Hessian built from the predicted
-    per-level start counts (pad 8, first test 8 columns) against plain adaptive peeling."""
-    p, b = CFG["problem"], CFG["build"]
-    probs = W.batch_problems(64, seed=2025, n_lo=128, n_hi=128)
-    ops = [h2.HeatOperator(q.n, q.kappa, q.T, q.sigma, W.sensor_mask(q.N, q.m, q.sensor_seed)) for q in probs]
-    trees = [h2.Tree(W.grid_coords(q.n), b.leaf, b.adm, b.eta) for q in probs]
+def learned_ranks_section(h2, torch, stream) -> dict:
+    """Rank model trained on adaptive builds of 500 heat Hessians at 128 x 128 (kappa ~ U[0.002,
+    0.05], 5-20 % sensors; fine probing q0 16, b_inc 8), then the 256 x 256 and 512 x 512
+    Hessians built from the predicted per-level start counts (pad 8, first test 8 columns)
+    against plain adaptive peeling (q0 32, b_inc 16), each at tol 1e-6."""
+    b = CFG["build"]
+    probs = W.batch_problems(500, seed=2025, n_lo=128, n_hi=128)
     fine = h2.default_opts(kmax=b.kmax, q0=16, b_inc=8, q_max=b.q_max, adaptive=1, seed=b.seed)
+    feats, targ = [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Gs = h2.build_batched(ops, trees, b.tol, fine)
+    for c0 in range(0, len(probs), 100):          # 100 Hessians per batched call
+        chunk = probs[c0:c0 + 100]
+        ops = [h2.HeatOperator(q.n, q.kappa, q.T, q.sigma, W.sensor_mask(q.N, q.m, q.sensor_seed)) for q in chunk]
+        trees = [h2.Tree(W.grid_coords(q.n), b.leaf, b.adm, b.eta) for q in chunk]
+        Gs = h2.build_batched(ops, trees, b.tol, fine)
+        for q, t, G in zip(chunk, trees, Gs):
+            f = h2.rank_features(t, q.kappa * q.T, q.m / q.N, b.tol)
+            lv, tg = h2.rank_targets(G.stats())
+            feats.append(f[lv])
+            targ += tg
+            G.close()
+        del ops, trees, Gs
     t_data = time.perf_counter() - t0
-    feats, targ = [], []
-    for q, t, G in zip(probs, trees, Gs):
-        f = h2.rank_features(t, q.kappa * q.T, q.m / q.N, b.tol)
-        lv, tg = h2.rank_targets(G.stats())
-        feats.append(f[lv])
-        targ += tg
-        G.close()
     X = torch.from_numpy(np.concatenate(feats).astype(np.float32)).cuda()
     y = torch.from_numpy(np.asarray(targ, dtype=np.float32)).cuda()
     model = h2.RankModel(seed=1, bf16=True)
     p0 = model.get()[0]
     p0[-1] = float(y.mean())
     model.set(p0)
-    steps = 3000
+    steps = 4000
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    model.train(X, y, steps, 64, 3e-3, stream=stream)
+    model.train(X, y, steps, 128, 3e-3, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t_train_ms = e0.elapsed_time(e1)
     loss, _ = model.loss_grad(X, y)
-    ql, yl = model.q_levels(tree, p.kappa * p.T, p.m / p.N, b.tol, pad=8, q_max=b.q_max)
-    lopts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=1, seed=b.seed,
-                            stream=stream, q_level=ql, q_test=8)
-    times = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Gm = h2.H2.build(gop, tree, b.tol, lopts)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-        sm = Gm.stats()
-        if len(times) < 3:
-            Gm.close()
-    err = rel_err_2norm(h2, torch, gop, Gm, p.N, sm["norm_est"], stream)
-    out = {"train_workload": "heat2d_n128 x 64 (adaptive q0 16, b_inc 8)", "train_rows": int(y.numel()),
-           "train_data_build_s": t_data, "train_steps": steps, "train_batch": 64, "train_ms": t_train_ms,
-           "train_launches": 1, "train_loss_log2": loss,
-           "q_start": [int(v) for v in ql], "predicted_log2": [round(float(v), 3) for v in yl],
-           "adaptive": {"op_calls": st_adaptive["op_calls"], "samples": st_adaptive["samples"],
-                        "range_calls": st_adaptive["range_calls"], "range_probes": st_adaptive["range_probes"],
-                        "build_s": build_s_adaptive, "t_peel": st_adaptive["t_peel"]},
-           "learned": {"op_calls": sm["op_calls"], "samples": sm["samples"], "range_calls": sm["range_calls"],
-                       "range_probes": sm["range_probes"], "range_passed": sm["range_passed"],
-                       "build_s": float(np.median(times)), "t_peel": sm["t_peel"], "rel_err_2norm": err}}
-    out["op_calls_saved"] = 1.0 - sm["op_calls"] / st_adaptive["op_calls"]
-    out["samples_saved"] = 1.0 - sm["samples"] / st_adaptive["samples"]
-    out["build_speedup"] = build_s_adaptive / out["learned"]["build_s"]
-    Gm.close()
+    out = {"train_workload": "heat2d_n128 x 500 (adaptive q0 16, b_inc 8)", "train_rows": int(y.numel()),
+           "train_data_build_s": t_data, "train_steps": steps, "train_batch": 128, "train_ms": t_train_ms,
+           "train_launches": 1, "train_loss_log2": loss, "eval": {}}
+    for cfg in (W.MEDIUM_N256, W.LARGE_N512):
+        p, bb = cfg["problem"], cfg["build"]
+        gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+        tree = h2.Tree(W.grid_coords(p.n), bb.leaf, bb.adm, bb.eta)
+        ql, yl = model.q_levels(tree, p.kappa * p.T, p.m / p.N, bb.tol, pad=8, q_max=bb.q_max)
+        base = dict(kmax=bb.kmax, q0=bb.q0, b_inc=bb.b_inc, q_max=bb.q_max, adaptive=1, seed=bb.seed, stream=stream)
+        res = {"q_start": [int(v) for v in ql], "predicted_log2": [round(float(v), 3) for v in yl]}
+        for key, opts in (("adaptive", h2.default_opts(**base)),
+                          ("learned", h2.default_opts(**base, q_level=ql, q_test=8))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = h2.H2.build(gop, tree, bb.tol, opts)
+            torch.cuda.synchronize()
+            bt = time.perf_counter() - t0
+            st = G.stats()
+            res[key] = {"op_calls": st["op_calls"], "samples": st["samples"], "range_calls": st["range_calls"],
+                        "range_probes": st["range_probes"], "range_passed": st["range_passed"], "build_s": bt,
+                        "t_peel": st["t_peel"],
+                        "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, p.N, st["norm_est"], stream)}
+            G.close()
+        res["op_calls_saved"] = 1.0 - res["learned"]["op_calls"] / res["adaptive"]["op_calls"]
+        res["samples_saved"] = 1.0 - res["learned"]["samples"] / res["adaptive"]["samples"]
+        res["build_speedup"] = res["adaptive"]["build_s"] / res["learned"]["build_s"]
+        out["eval"][cfg["name"]] = res
+        del gop, tree
+        torch.cuda.empty_cache()
     model.close()
-    torch.cuda.empty_cache()
     return out
 
 
@@ -603,7 +607,7 @@ def main():
 
     learned = None
     if rank == 0 and not args.no_learned:
-        learned = learned_ranks_section(h2, torch, stream, gop, tree, opts, st, float(np.mean(build_ms)) / 1e3)
+        learned = learned_ranks_section(h2, torch, stream)
 
     if rank == 0:
         line = {
