@@ -307,6 +307,13 @@ int h2_batch_matvec(h2_batch_t b, const void* const* X, const int64_t* ldx, void
 int h2_batch_tuned(h2_batch_t b, int64_t nrhs, int mode, int* rhs_tile);
 void h2_batch_free(h2_batch_t b);
 
+/* One-shot batched application: h2_batch_create, h2_batch_matvec and h2_batch_free in one
+ * call (the autotuning and capture run on this call and are not kept; callers that apply the
+ * same handles repeatedly should keep an h2_batch_t).  Returns after the products are complete
+ * (the device is synchronised).  Arguments and errors as h2_batch_create / h2_batch_matvec. */
+int h2_matvec_batched(int count, const h2_handle_t* hs, const void* const* X, const int64_t* ldx, void* const* Y,
+                      const int64_t* ldy, int64_t nrhs, int mode, h2_stream_t stream);
+
 /* Statistics of the construction of h (host struct). */
 int h2_get_stats(h2_handle_t h, h2_stats* out);
 
@@ -372,6 +379,13 @@ int h2_rankmodel_train(h2_rankmodel_t m, const float* X, const float* t, int64_t
 /* y (device, n floats) = model(X) (device, n x H2_RM_FEATURES).  Asynchronous on stream. */
 int h2_rankmodel_predict(h2_rankmodel_t m, const float* X, int64_t n, float* y, h2_stream_t stream);
 
+/* Save a model (bf16 flag, seed, Adam step, parameters and both Adam moments) to a binary file
+ * (host path; native byte order, magic "H2RM0001"), and create a model on the current device from
+ * such a file.  Synchronous.  Errors: INVALID_ARG (NULL arguments, file not writable/readable,
+ * wrong magic or size), CUDA, OOM. */
+int h2_rankmodel_save(h2_rankmodel_t m, const char* path);
+int h2_rankmodel_load(const char* path, h2_rankmodel_t* out);
+
 /* Start counts for h2_build_opts.q_level: q_host[l] (host, L+1 entries) = ceil(2^y_l) - 1 + pad
  * rounded up to a multiple of 8 and clamped to [8, q_max], y_l the prediction for level l of
  * h2_rankmodel_features(tree, kappa_T, density, tol); q_host[0] = 0.  y_host (L+1 floats,
@@ -385,9 +399,11 @@ int h2_rankmodel_q_levels(h2_rankmodel_t m, h2_tree_t tree, double kappa_T, doub
  * Misfit Hessian of 2-D heat-equation initial-condition inversion on the unit
  * square: H = F diag(mask) F / sigma^2, F = exp(T kappa Lap_h) with the 5-point
  * Dirichlet Laplacian on the n x n interior grid (node p = i*n + j at ((i+1)h,
- * (j+1)h), h = 1/(n+1)), applied exactly through the orthonormal DST-I.  mask_host
- * holds n*n entries (1 at sensor nodes, 0 elsewhere).  Creates device state on the
- * current device.  Errors: INVALID_ARG, CUDA, OOM.
+ * (j+1)h), h = 1/(n+1)), applied through the orthonormal DST-I: F = F1 (x) F1 with
+ * F1 = S diag(exp(-T kappa mu)) S, restricted to the sine modes whose factor is at least
+ * 2^-60 times the largest (the rest is below FP64 resolution).  mask_host holds n*n
+ * entries (1 at sensor nodes, 0 elsewhere).  Creates device state on the current device.
+ * Errors: INVALID_ARG, CUDA, OOM.
  */
 int h2_heat2d_create(int n, double kappa, double T, double sigma, const double* mask_host,
                      void** ctx_out);

@@ -98,6 +98,9 @@ _SIGS = {
     "h2_batch_matvec": (_I, [_P, _P, _P, _P, _P, _I64, _I, _P]),
     "h2_batch_tuned": (_I, [_P, _I64, _I, _P]),
     "h2_batch_free": (None, [_P]),
+    "h2_matvec_batched": (_I, [_I, _P, _P, _P, _P, _P, _I64, _I, _P]),
+    "h2_rankmodel_save": (_I, [_P, ctypes.c_char_p]),
+    "h2_rankmodel_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "h2_matvec_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
     "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "h2_profile": (_I, [_P, _I]),
@@ -426,6 +429,16 @@ def build_batched(ops, trees, tol: float, opts: BuildOpts | None = None):
     return [H2(ctypes.c_void_p(outs[i]), st) for i in range(n)]
 
 
+def matvec_batched(handles, Xs, Ys, nrhs: int, mode: int = H2_FP64, stream=None):
+    """One-shot batched application of several handles (h2_matvec_batched)."""
+    n = len(handles)
+    hp = (ctypes.c_void_p * n)(*[h._h.value for h in handles])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in Xs])
+    yp = (ctypes.c_void_p * n)(*[_ptr(y) for y in Ys])
+    lx = (ctypes.c_int64 * n)(*[h.stats()["n"] for h in handles])
+    _check(lib().h2_matvec_batched(n, hp, xp, lx, yp, lx, nrhs, mode, _stream_ptr(stream)))
+
+
 class Batch:
     """Merged, autotuned and graph-captured matvec over several handles (which must stay alive)."""
 
@@ -516,6 +529,17 @@ class RankModel:
         _check(lib().h2_rankmodel_q_levels(self._m, tree.handle, kappa_T, density, tol, pad, q_max, q.ctypes.data,
                                            y.ctypes.data))
         return q, y
+
+    def save(self, path: str):
+        _check(lib().h2_rankmodel_save(self._m, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "RankModel":
+        h = ctypes.c_void_p()
+        _check(lib().h2_rankmodel_load(os.fsencode(path), ctypes.byref(h)))
+        m = cls.__new__(cls)
+        m._m = h
+        return m
 
     def close(self):
         if self._m:

@@ -26,6 +26,8 @@ void rm_loss_grad(h2_rankmodel_s* m, const float* X, const float* T, int64_t n, 
 void rm_predict(h2_rankmodel_s* m, const float* X, int64_t n, float* Y, cudaStream_t s);
 void rm_q_levels(h2_rankmodel_s* m, const h2_tree_s* t, double kT, double dens, double tol, int pad, int q_max,
                  int32_t* q, float* y_host);
+void rm_save(h2_rankmodel_s* m, const char* path);
+h2_rankmodel_s* rm_load(const char* path);
 
 // Device permutation, matvec plan, reduced-precision copies and statistics of a built handle.
 void finish_handle(h2_handle_s* h, const h2_build_opts& o, cudaStream_t s) {
@@ -258,6 +260,16 @@ void h2_batch_free(h2_batch_t b) {
     }
 }
 
+int h2_matvec_batched(int count, const h2_handle_t* hs, const void* const* X, const int64_t* ldx, void* const* Y,
+                      const int64_t* ldy, int64_t nrhs, int mode, h2_stream_t stream) {
+    h2_batch_t b = nullptr;
+    int st = h2_batch_create(count, hs, &b);
+    if (st != H2_OK) return st;
+    st = h2_batch_matvec(b, X, ldx, Y, ldy, nrhs, mode, stream);
+    h2_batch_free(b);
+    return st;
+}
+
 int h2_rankmodel_create(uint64_t seed, int bf16, h2_rankmodel_t* out) {
     return guard([&] {
         require(out != nullptr, "h2_rankmodel_create: out is NULL");
@@ -286,6 +298,24 @@ int h2_rankmodel_set(h2_rankmodel_t m, const float* p, const float* am, const fl
     return guard([&] {
         require(m != nullptr, "h2_rankmodel_set: NULL model");
         h2::rm_set(m, p, am, av, step);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_save(h2_rankmodel_t m, const char* path) {
+    return guard([&] {
+        require(m && path, "h2_rankmodel_save: NULL argument");
+        h2::rm_save(m, path);
+        return H2_OK;
+    });
+}
+
+int h2_rankmodel_load(const char* path, h2_rankmodel_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_rankmodel_load: out is NULL");
+        *out = nullptr;
+        require(path != nullptr, "h2_rankmodel_load: NULL path");
+        *out = h2::rm_load(path);
         return H2_OK;
     });
 }

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "handle.h"
@@ -438,6 +439,58 @@ void rm_set(h2_rankmodel_s* m, const float* p, const float* am, const float* av,
     if (am) H2_CUDA(cudaMemcpy(m->adam_m.p, am, NP * sizeof(float), cudaMemcpyHostToDevice));
     if (av) H2_CUDA(cudaMemcpy(m->adam_v.p, av, NP * sizeof(float), cudaMemcpyHostToDevice));
     if (step >= 0) m->step = step;
+}
+
+namespace {
+constexpr char RM_MAGIC[8] = {'H', '2', 'R', 'M', '0', '0', '0', '1'};
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+}  // namespace
+
+void rm_save(h2_rankmodel_s* m, const char* path) {
+    std::vector<float> p(NP), am(NP), av(NP);
+    int64_t step = 0;
+    rm_get(m, p.data(), am.data(), av.data(), &step);
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) fail(H2_ERR_INVALID_ARG, std::string("h2_rankmodel_save: cannot open ") + path);
+    const int32_t np = NP, bf16 = m->bf16;
+    bool ok = fwrite(RM_MAGIC, 1, 8, fc.f) == 8 && fwrite(&np, 4, 1, fc.f) == 1 && fwrite(&bf16, 4, 1, fc.f) == 1 &&
+              fwrite(&m->seed, 8, 1, fc.f) == 1 && fwrite(&step, 8, 1, fc.f) == 1 &&
+              fwrite(p.data(), 4, NP, fc.f) == (size_t)NP && fwrite(am.data(), 4, NP, fc.f) == (size_t)NP &&
+              fwrite(av.data(), 4, NP, fc.f) == (size_t)NP;
+    ok = (fclose(fc.f) == 0) && ok;
+    fc.f = nullptr;
+    if (!ok) fail(H2_ERR_INVALID_ARG, std::string("h2_rankmodel_save: write to ") + path + " failed");
+}
+
+h2_rankmodel_s* rm_load(const char* path) {
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) fail(H2_ERR_INVALID_ARG, std::string("h2_rankmodel_load: cannot open ") + path);
+    char magic[8];
+    int32_t np = 0, bf16 = 0;
+    uint64_t seed = 0;
+    int64_t step = 0;
+    std::vector<float> p(NP), am(NP), av(NP);
+    bool ok = fread(magic, 1, 8, fc.f) == 8 && std::memcmp(magic, RM_MAGIC, 8) == 0 && fread(&np, 4, 1, fc.f) == 1 &&
+              np == NP && fread(&bf16, 4, 1, fc.f) == 1 && fread(&seed, 8, 1, fc.f) == 1 &&
+              fread(&step, 8, 1, fc.f) == 1 && step >= 0 && fread(p.data(), 4, NP, fc.f) == (size_t)NP &&
+              fread(am.data(), 4, NP, fc.f) == (size_t)NP && fread(av.data(), 4, NP, fc.f) == (size_t)NP;
+    char extra;
+    ok = ok && fread(&extra, 1, 1, fc.f) == 0;
+    if (!ok) fail(H2_ERR_INVALID_ARG, std::string("h2_rankmodel_load: ") + path + " is not a rank model file");
+    h2_rankmodel_s* m = rm_create(seed, bf16);
+    try {
+        rm_set(m, p.data(), am.data(), av.data(), step);
+    } catch (...) {
+        delete m;
+        throw;
+    }
+    return m;
 }
 
 void rm_features(const h2_tree_s* t, double kT, double dens, double tol, double* out) {

@@ -120,3 +120,18 @@ def test_rank_model_argument_validation(h2):
     o = h2.default_opts(q_test=0)
     assert L.h2_build(None, None, None, 1e-6, ctypes.byref(o), ctypes.byref(ctypes.c_void_p())) == \
         h2.H2_ERR_INVALID_ARG
+
+
+def test_rank_model_load_rejects_bad_files(h2, tmp_path):
+    """A file that is not a saved rank model is rejected before any device work."""
+    L = h2.lib()
+    out = ctypes.c_void_p()
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"H2RM0002" + bytes(64))
+    assert L.h2_rankmodel_load(str(bad).encode(), ctypes.byref(out)) == h2.H2_ERR_INVALID_ARG
+    assert b"not a rank model" in L.h2_last_error()
+    short = tmp_path / "short.bin"
+    short.write_bytes(b"H2RM0001" + bytes(12))
+    assert L.h2_rankmodel_load(str(short).encode(), ctypes.byref(out)) == h2.H2_ERR_INVALID_ARG
+    assert L.h2_rankmodel_load(str(tmp_path / "missing.bin").encode(), ctypes.byref(out)) == h2.H2_ERR_INVALID_ARG
+    assert not out.value

@@ -58,3 +58,19 @@ def test_batch_matvec_equals_individual(setup, mode, nrhs):
             tol = 1e-12 if mode == h2.H2_FP64 else 1e-5
             assert float((R - Y).norm() / R.norm()) < tol
     B.close()
+
+
+def test_one_shot_batched_matvec_equals_batch(setup):
+    h2, probs, ops, trees, batched, single = setup
+    nrhs = 16
+    Xs = [torch.from_numpy(np.ascontiguousarray(W.rhs(p.N, nrhs, 70 + i).T)).to("cuda", torch.float32)
+          for i, p in enumerate(probs)]
+    Y1 = [torch.empty_like(x) for x in Xs]
+    Y2 = [torch.empty_like(x) for x in Xs]
+    B = h2.Batch(batched)
+    B.matvec(Xs, Y1, nrhs, h2.H2_FP32)
+    h2.matvec_batched(batched, Xs, Y2, nrhs, h2.H2_FP32)
+    torch.cuda.synchronize()
+    for a, b in zip(Y1, Y2):
+        assert torch.equal(a, b)      # same tuned tile candidates, same kernels, same order
+    B.close()

@@ -269,3 +269,22 @@ def test_learned_start_saves_operator_calls(h2):
     print("adaptive calls/samples/t_peel", tot["ad"], "learned", tot["ml"])
     assert tot["ml"][0] <= tot["ad"][0]
     assert tot["ml"][1] <= 0.9 * tot["ad"][1]
+
+
+def test_save_and_load_round_trip(h2, tmp_path):
+    m, p = _model(h2, True, seed=21)
+    X, t = _data(200, 3)
+    m.train(_dev(X), _dev(t), 5, 32, 1e-3)
+    path = str(tmp_path / "model.bin")
+    m.save(path)
+    m2 = h2.RankModel.load(path)
+    a, b = m.get(), m2.get()
+    for u, v in zip(a[:3], b[:3]):
+        assert np.array_equal(u, v)
+    assert a[3] == b[3] == 5
+    y1 = torch.empty(200, device="cuda")
+    y2 = torch.empty(200, device="cuda")
+    m.predict(_dev(X), y1)
+    m2.predict(_dev(X), y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
