@@ -39,7 +39,7 @@ CFG = W.MEDIUM_N256
 # DRAM bytes (read + write) per gemm_tiles_kernel launch of the bench command, from an ncu capture
 # of every launch of that kernel (dram__bytes_read.sum + dram__bytes_write.sum, 1,147 launches);
 # reset to None whenever the kernel changes
-GEMM_TRAFFIC_PER_LAUNCH = 35.66e6
+GEMM_TRAFFIC_PER_LAUNCH = None
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
@@ -180,6 +180,22 @@ def precision_section(h2, torch, stream, bf16_peak: float, n: int = 512) -> dict
                               "peak_TFLOPs": peak, "rel_err_vs_fp64_matvec": err,
                               "stage_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
         del X, Y
+    # FP32 storage at nrhs = 1: the HBM-bound form of the matvec
+    x1 = X64[:1].float().contiguous()
+    y1 = torch.empty_like(x1)
+    G.matvec(x1, y1, 1, h2.H2_FP32, stream=stream)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        G.matvec(x1, y1, 1, h2.H2_FP32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / reps
+    by1 = matvec_bytes(st, N, 1, 4)
+    hbm = peaks()[0]
+    out["modes"]["FP32_nrhs1"] = {"ms": ms1, "GBps": by1 / (ms1 / 1e3) / 1e9,
+                                  "frac_of_hbm": by1 / (ms1 / 1e3) / 1e9 / hbm, "hbm_peak_GBps": hbm}
     assert G.device_status() == h2.H2_OK
     del X64, Y64
     G.close()

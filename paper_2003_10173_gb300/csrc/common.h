@@ -109,6 +109,8 @@ struct GemmProb {
     int lda, ldb, ldc;
     int ta, tb;
     double alpha, beta;
+    int tm = 64;   // tile rows (64, 32 or 16), chosen by GemmBatch::run
+    int tc = 0;    // 1: the problem is computed transposed (C^T = op(B)^T op(A)^T), stored back as C
 };
 
 // Runs a list of independent problems (their C regions must not overlap) in

@@ -7,8 +7,13 @@
 // F = F1 (x) F1 with F1 = exp(T kappa Lap_1) = S diag(exp(-T kappa mu)) S, S the
 // orthonormal type-I sine transform and mu_a = (4/h^2) sin^2(a pi h / 2).  With the
 // vector x read as the column-major n x n array X (X[j, i] = x[i n + j]),
-//     F x  <->  F1 X F1,
-// two FP64 GEMMs per application; F1 is formed once on the device from S.
+//     F x  <->  F1 X F1.
+// The factors exp(-T kappa mu_b) decay like exp(-T kappa pi^2 b^2): only the r modes with
+// exp(-T kappa mu_b) >= 2^-60 exp(-T kappa mu_1) are representable next to the largest one in
+// FP64, so F1 = S_r diag(e_r) S_r^T to rounding (dropped part below 2^-60 relative), and
+//     F1 X F1 = (S_r diag(e_r)) ((S_r^T X) S_r) diag(e_r) S_r^T
+// costs 8 r n^2 flops instead of 4 n^3 (four FP64 GEMMs).  When 2 r >= n the dense F1 (formed
+// once on the device from S) is used instead.
 //
 // dense: Y = A X with a caller-owned dense matrix.
 #include <cmath>
@@ -44,20 +49,35 @@ unsigned grid_for(int64_t total) {
 
 struct Heat2d {
     int n = 0;
+    int r = 0;               // retained sine modes (r == n: dense F1)
     double inv_s2 = 0.0;
-    DevBuf<double> F1, mask, W1, W2;
+    DevBuf<double> F1, Sr, Sar, mask, W1, W2, W3;
     GemmBatch gb;
 };
 
-// B <- F B = F1 B_r F1 for every column r of B (N x c contiguous); W is scratch.
-void apply_F(Heat2d& H, double* B, double* W, int64_t c, cudaStream_t s) {
+// B <- F B = F1 B_q F1 for every column q of B (N x c contiguous); W, T are scratch
+// (W: N x c, T: r n c).
+void apply_F(Heat2d& H, double* B, double* W, double* T, int64_t c, cudaStream_t s) {
     const int n = H.n;
     const int64_t n2 = (int64_t)n * n;
-    // W = F1 * B_view  (n x n*c)
-    H.gb.add(H.F1.p, n, 0, B, n, 0, W, n, n, (int)(n * c), n, 1.0, 0.0);
+    if (H.r == n) {
+        // W = F1 * B_view  (n x n*c), then B_q = W_q * F1
+        H.gb.add(H.F1.p, n, 0, B, n, 0, W, n, n, (int)(n * c), n, 1.0, 0.0);
+        H.gb.run(s);
+        for (int64_t q = 0; q < c; ++q) H.gb.add(W + q * n2, n, 0, H.F1.p, n, 0, B + q * n2, n, n, n, n, 1.0, 0.0);
+        H.gb.run(s);
+        return;
+    }
+    const int r = H.r;
+    // T = S_r^T B_view (r x n c);  W = (S_r diag(e)) T = F1 B_view
+    H.gb.add(H.Sr.p, n, 1, B, n, 0, T, r, r, (int)(n * c), n, 1.0, 0.0);
     H.gb.run(s);
-    // B_r = W_r * F1
-    for (int64_t r = 0; r < c; ++r) H.gb.add(W + r * n2, n, 0, H.F1.p, n, 0, B + r * n2, n, n, n, n, 1.0, 0.0);
+    H.gb.add(H.Sar.p, n, 0, T, r, 0, W, n, n, (int)(n * c), r, 1.0, 0.0);
+    H.gb.run(s);
+    // T_q = W_q (S_r diag(e))  (n x r);  B_q = T_q S_r^T = W_q F1
+    for (int64_t q = 0; q < c; ++q) H.gb.add(W + q * n2, n, 0, H.Sar.p, n, 0, T + q * n * r, n, n, r, n, 1.0, 0.0);
+    H.gb.run(s);
+    for (int64_t q = 0; q < c; ++q) H.gb.add(T + q * n * r, n, 0, H.Sr.p, n, 1, B + q * n2, n, n, n, r, 1.0, 0.0);
     H.gb.run(s);
 }
 
@@ -85,25 +105,38 @@ int h2_heat2d_create(int n, double kappa, double T, double sigma, const double* 
         H->n = n;
         H->inv_s2 = 1.0 / (sigma * sigma);
         const double h = 1.0 / (n + 1);
-        // S and S diag(exp(-T kappa mu)) on the host, F1 = (S diag(.)) S by the library's GEMM
+        // S and S diag(exp(-T kappa mu)) on the host (mu increases with the mode index b)
         std::vector<double> S((size_t)n * n), Sa((size_t)n * n);
+        std::vector<double> e(n);
         for (int b = 0; b < n; ++b) {
             const double mu = (4.0 / (h * h)) * std::pow(std::sin(0.5 * M_PI * h * (b + 1)), 2);
-            const double ab = std::exp(-T * kappa * mu);
+            e[b] = std::exp(-T * kappa * mu);
             for (int a = 0; a < n; ++a) {
                 S[a + (size_t)b * n] = std::sqrt(2.0 * h) * std::sin(M_PI * h * (double)(a + 1) * (b + 1));
-                Sa[a + (size_t)b * n] = S[a + (size_t)b * n] * ab;
+                Sa[a + (size_t)b * n] = S[a + (size_t)b * n] * e[b];
             }
         }
+        int r = 0;
+        while (r < n && e[r] >= 0x1p-60 * e[0]) ++r;
+        H->r = (2 * r >= n) ? n : std::max(r, 1);
         const int64_t N = (int64_t)n * n;
-        DevBuf<double> dS(S.size()), dSa(Sa.size());
-        H->F1.reserve(S.size());
         H->mask.reserve(N);
-        H2_CUDA(cudaMemcpy(dS.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
-        H2_CUDA(cudaMemcpy(dSa.p, Sa.data(), Sa.size() * sizeof(double), cudaMemcpyHostToDevice));
-        H->gb.add(dSa.p, n, 0, dS.p, n, 0, H->F1.p, n, n, n, n, 1.0, 0.0);
-        H->gb.run(nullptr);
-        H2_CUDA(cudaDeviceSynchronize());
+        if (H->r == n) {
+            // F1 = (S diag(e)) S by the library's GEMM
+            DevBuf<double> dS(S.size()), dSa(Sa.size());
+            H->F1.reserve(S.size());
+            H2_CUDA(cudaMemcpy(dS.p, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+            H2_CUDA(cudaMemcpy(dSa.p, Sa.data(), Sa.size() * sizeof(double), cudaMemcpyHostToDevice));
+            H->gb.add(dSa.p, n, 0, dS.p, n, 0, H->F1.p, n, n, n, n, 1.0, 0.0);
+            H->gb.run(nullptr);
+            H2_CUDA(cudaDeviceSynchronize());
+        } else {
+            // the first r columns of S and S diag(e) (column-major, leading dimension n)
+            H->Sr.reserve((size_t)n * H->r);
+            H->Sar.reserve((size_t)n * H->r);
+            H2_CUDA(cudaMemcpy(H->Sr.p, S.data(), (size_t)n * H->r * sizeof(double), cudaMemcpyHostToDevice));
+            H2_CUDA(cudaMemcpy(H->Sar.p, Sa.data(), (size_t)n * H->r * sizeof(double), cudaMemcpyHostToDevice));
+        }
         H2_CUDA(cudaMemcpy(H->mask.p, mask_host, N * sizeof(double), cudaMemcpyHostToDevice));
         *ctx_out = H;
         return H2_OK;
@@ -126,12 +159,13 @@ int h2_heat2d_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t
         cudaStream_t s = (cudaStream_t)stream;
         H->W1.reserve((size_t)n * nrhs);
         H->W2.reserve((size_t)n * nrhs);
+        if (H->r < H->n) H->W3.reserve((size_t)H->n * H->r * nrhs);
         H2_CUDA(cudaMemcpy2DAsync(H->W1.p, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), nrhs,
                                   cudaMemcpyDeviceToDevice, s));
-        apply_F(*H, H->W1.p, H->W2.p, nrhs, s);
+        apply_F(*H, H->W1.p, H->W2.p, H->W3.p, nrhs, s);
         scale_by_kernel<<<grid_for(n * nrhs), NT, 0, s>>>(H->W1.p, H->mask.p, n, n * nrhs, 1.0);
         after_launch("heat_mask");
-        apply_F(*H, H->W1.p, H->W2.p, nrhs, s);
+        apply_F(*H, H->W1.p, H->W2.p, H->W3.p, nrhs, s);
         store_kernel<<<grid_for(n * nrhs), NT, 0, s>>>(H->W1.p, n, nrhs, H->inv_s2, Y, ldy);
         after_launch("heat_store");
         return H2_OK;
