@@ -130,6 +130,21 @@ struct Workspace {
 
 }  // namespace h2
 
+// A captured h2_matvec launch sequence and what it was captured for.
+struct MvGraph {
+    const void* X = nullptr;
+    const void* Y = nullptr;
+    const void* ws = nullptr;
+    const void* opnd = nullptr;
+    int64_t ldx = 0, ldy = 0, nrhs = 0;
+    int mode = 0;
+    int uses = 0;                      // calls seen with this key (captured on the second)
+    int64_t launches = 0;              // kernels in the graph
+    uint64_t stamp = 0;                // last use (replacement order)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct h2_handle_s {
     std::shared_ptr<h2_tree_s> tree;
     int L = 0;
@@ -159,7 +174,16 @@ struct h2_handle_s {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     double prof_ms[H2_STAGE_COUNT] = {0};
     int64_t prof_n[H2_STAGE_COUNT] = {0};
+    // CUDA graphs of repeated h2_matvec calls (a few keys, least recently used replaced)
+    std::vector<MvGraph> graphs;
+    uint64_t graph_clock = 0;
+    cudaStream_t cap = nullptr;
     ~h2_handle_s() {
+        for (auto& g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+        }
+        if (cap) cudaStreamDestroy(cap);
         for (auto e : ev_pool) cudaEventDestroy(e);
         for (auto& u : ev_used) {
             cudaEventDestroy(u.second.first);
@@ -182,6 +206,7 @@ void profile_read(h2_handle_s* h, double* ms, int64_t* n);
 void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                         int mode, cudaStream_t s);
 bool tc_supported(const h2_handle_s* h);
+void tc_reserve(h2_handle_s* h, int mode, int nrhs);
 void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s);
 void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
                int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,

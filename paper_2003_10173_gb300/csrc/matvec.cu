@@ -13,6 +13,7 @@
 // Only the lower triangle of S and D is stored; upper blocks are used as
 // transposes of the stored ones.
 #include <algorithm>
+#include <functional>
 #include <mutex>
 
 #include "handle.h"
@@ -131,6 +132,65 @@ __global__ void __launch_bounds__(NT) mv_leaf_near_kernel(const MvOut* __restric
                                             accumulate);
 }
 
+// Small-nrhs stages (tree sweeps, leaf upsweep, leaf expansion for nrhs <= 4): one warp per
+// output block, lanes over its rows (at most 96, three per lane), inputs read straight from X or
+// the workspace (the same value for every lane: a broadcast), no shared memory, so that the many
+// tiny blocks of a level run as one wave of warps.
+template <class TS, class TX, class TY, class TA, bool OUT_Y, int NR>
+__global__ void __launch_bounds__(256) mv_small_stage_kernel(const MvOut* __restrict__ outs, int nouts,
+                                                              const MvItem* __restrict__ items,
+                                                              const TS* __restrict__ fac, TA* __restrict__ ws,
+                                                              int64_t ws_ld, const int32_t* __restrict__ perm,
+                                                              const TX* __restrict__ X, int64_t ldx,
+                                                              TY* __restrict__ Y, int64_t ldy, int accumulate) {
+    const int lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (idx >= nouts) return;
+    const MvOut o = outs[idx];
+    const int rows = o.rows;
+    TA acc[3][NR];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[q][r] = (TA)0;
+    for (int it = o.beg; it < o.end; ++it) {
+        const MvItem m = items[it];
+        const TS* M = fac + m.m_off;
+        const bool tr = (m.trans & 1) != 0;
+        for (int j = 0; j < m.cols; ++j) {
+            TA in[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                in[r] = (m.trans & 2) ? cvt<TA>(X[perm[m.in_off + j] + (int64_t)r * ldx])
+                                      : ws[m.in_off + j + (int64_t)r * ws_ld];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int i = lane + 32 * q;
+                if (i < rows) {
+                    const TA d = cvt<TA>(tr ? M[j + (int64_t)i * m.ldm] : M[i + (int64_t)j * m.ldm]);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[q][r] = fma(d, in[r], acc[q][r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = lane + 32 * q;
+        if (i >= rows) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (OUT_Y) {
+                TY* y = Y + perm[o.out_off + i] + (int64_t)r * ldy;
+                *y = accumulate ? (TY)(*y + acc[q][r]) : (TY)acc[q][r];
+            } else {
+                TA* y = ws + o.out_off + i + (int64_t)r * ws_ld;
+                *y = accumulate ? (TA)(*y + acc[q][r]) : acc[q][r];
+            }
+        }
+    }
+}
+
 // Batched stages: outputs of several handles in one launch; each output names its handle and the
 // handle's bases (factors, workspace, permutation, X, Y) come from a device table.
 template <class TS, class TX, class TY, class TA, bool OUT_Y, int RTT>
@@ -204,13 +264,32 @@ __global__ void __launch_bounds__(SW * 32) mv_scatter_kernel(const SymItem* __re
             for (int r = 0; r < NR; ++r)
                 xs[r] = cin ? sc_in<TA, TX, VIA_PERM>(X, ldx, ws, ws_ld, perm, it.in_s, jl, r) : (TA)0;
             const int nc = min(32, it.cols - j0);
-#pragma unroll 8
-            for (int c = 0; c < 32; ++c) {
-                TA d = (TA)0;
-                if (rin && c < nc) d = cvt<TA>(M[i + (int64_t)(j0 + c) * it.ldm]);
-                T[c][lane] = d;
+            if constexpr (sizeof(TS) <= 4) {
+                // bandwidth-bound storage: the whole 32 x 32 tile is requested before any of it is
+                // used (32 independent coalesced loads per warp in flight)
+                TS dv[32];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
+                for (int c = 0; c < 32; ++c) {
+                    dv[c] = TS(0);
+                    if (rin && c < nc) dv[c] = M[i + (int64_t)(j0 + c) * it.ldm];
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const TA d = cvt<TA>(dv[c]);
+                    T[c][lane] = d;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
+                }
+            } else {
+                // FP64 storage is FP64-pipe bound: fewer registers, more resident warps
+#pragma unroll 8
+                for (int c = 0; c < 32; ++c) {
+                    TA d = (TA)0;
+                    if (rin && c < nc) d = cvt<TA>(M[i + (int64_t)(j0 + c) * it.ldm]);
+                    T[c][lane] = d;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
+                }
             }
             if (!it.diag) {
                 __syncwarp();
@@ -257,6 +336,32 @@ void launch_scatter(const SymStage& st, const TS* fac, TA* ws, int64_t ws_ld, co
         case 2: launch_scatter_nr<TS, TX, TY, TA, 2>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
         case 3: launch_scatter_nr<TS, TX, TY, TA, 3>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
         default: launch_scatter_nr<TS, TX, TY, TA, 4>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+    }
+}
+
+template <class TS, class TX, class TY, class TA, int NR>
+void launch_small_stage_nr(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm,
+                           const TX* X, int64_t ldx, TY* Y, int64_t ldy, cudaStream_t s) {
+    const int n = (int)st.outs.size();
+    const unsigned grid = (unsigned)((n + 7) / 8);
+    if (st.out_to_y)
+        mv_small_stage_kernel<TS, TX, TY, TA, true, NR><<<grid, 256, 0, s>>>(st.d_outs.p, n, st.d_items.p, fac, ws,
+                                                                             ws_ld, perm, X, ldx, Y, ldy, st.accumulate);
+    else
+        mv_small_stage_kernel<TS, TX, TY, TA, false, NR><<<grid, 256, 0, s>>>(st.d_outs.p, n, st.d_items.p, fac, ws,
+                                                                              ws_ld, perm, X, ldx, Y, ldy, st.accumulate);
+    after_launch("mv_small_stage");
+}
+
+template <class TS, class TX, class TY, class TA>
+void launch_small_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm, const TX* X,
+                        int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
+    if (st.outs.empty()) return;
+    switch (nrhs) {
+        case 1: launch_small_stage_nr<TS, TX, TY, TA, 1>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        case 2: launch_small_stage_nr<TS, TX, TY, TA, 2>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        case 3: launch_small_stage_nr<TS, TX, TY, TA, 3>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
+        default: launch_small_stage_nr<TS, TX, TY, TA, 4>(st, fac, ws, ws_ld, perm, X, ldx, Y, ldy, s); break;
     }
 }
 
@@ -316,12 +421,12 @@ void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, 
         H2_CUDA(cudaMemset2DAsync(ws + P.yh_row0, wld * sizeof(TA), 0, (wld - P.yh_row0) * sizeof(TA), nrhs, s));
     timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     for (const MvStage& st : P.small_up)
-        timed(st.kind, [&] { launch_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     timed(H2_STAGE_COUPLE, [&] { launch_scatter<TS, TX, TY, TA>(P.couple, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     for (const MvStage& st : P.small_down)
-        timed(st.kind, [&] { launch_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     timed(H2_STAGE_LEAF_NEAR, [&] {
-        launch_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+        launch_small_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
     });
 }
 
@@ -738,44 +843,122 @@ void make_copies(h2_handle_s* h, int keep_fp32, int keep_bf16, cudaStream_t s) {
     tc_prepare(h, keep_bf16, keep_fp32, s);
 }
 
-void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
-                int mode, cudaStream_t s) {
-    if (nrhs <= 0) return;
-    if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec: nrhs above 2,000,000");
+namespace {
+
+// Reserves the buffers of a call and returns the function that enqueues its launches.
+std::function<void(cudaStream_t)> matvec_launches(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                                  int64_t nrhs, int mode) {
     const int64_t need = h->plan.ws_rows * nrhs;
     switch (mode) {
-        case H2_FP64: {
+        case H2_FP64:
             h->ws.f64.reserve((size_t)need);
-            run_all<double, double, double, double>(h, h->fac64.p, h->ws.f64.p, (const double*)X, ldx,
-                                                    (double*)Y, ldy, (int)nrhs, s);
-            break;
-        }
+            return [=](cudaStream_t s) {
+                run_all<double, double, double, double>(h, h->fac64.p, h->ws.f64.p, (const double*)X, ldx, (double*)Y,
+                                                        ldy, (int)nrhs, s);
+            };
         case H2_FP32:
         case H2_TF32: {
             if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: FP32 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
-            if (mode == H2_TF32 && nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W32.p)
-                run_tc<float, float>(h, mode, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y, ldy,
-                                     (int)nrhs, s);
-            else
-                run_all<float, float, float, float>(h, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y,
-                                                    ldy, (int)nrhs, s);
-            break;
+            if (mode == H2_TF32 && nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W32.p) {
+                tc_reserve(h, mode, (int)nrhs);
+                return [=](cudaStream_t s) {
+                    run_tc<float, float>(h, mode, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y, ldy,
+                                         (int)nrhs, s);
+                };
+            }
+            return [=](cudaStream_t s) {
+                run_all<float, float, float, float>(h, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y, ldy,
+                                                    (int)nrhs, s);
+            };
         }
         case H2_BF16: {
             if (!h->fac16.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: BF16 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
-            if (nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W16.p)
-                run_tc<__nv_bfloat16, __nv_bfloat16>(h, mode, h->fac16.p, h->ws.f32.p, (const __nv_bfloat16*)X, ldx,
-                                                     (float*)Y, ldy, (int)nrhs, s);
-            else
-                run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, h->ws.f32.p,
-                                                                    (const __nv_bfloat16*)X, ldx, (float*)Y, ldy,
-                                                                    (int)nrhs, s);
-            break;
+            if (nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W16.p) {
+                tc_reserve(h, mode, (int)nrhs);
+                return [=](cudaStream_t s) {
+                    run_tc<__nv_bfloat16, __nv_bfloat16>(h, mode, h->fac16.p, h->ws.f32.p, (const __nv_bfloat16*)X,
+                                                         ldx, (float*)Y, ldy, (int)nrhs, s);
+                };
+            }
+            return [=](cudaStream_t s) {
+                run_all<__nv_bfloat16, __nv_bfloat16, float, float>(h, h->fac16.p, h->ws.f32.p, (const __nv_bfloat16*)X,
+                                                                    ldx, (float*)Y, ldy, (int)nrhs, s);
+            };
         }
         default:
             fail(H2_ERR_INVALID_ARG, "h2_matvec: mode not supported");
+    }
+}
+
+constexpr size_t kMaxGraphs = 8;
+
+}  // namespace
+
+// The launch sequence of a repeated call (same buffers, sizes and mode) is captured in a CUDA
+// graph on its second occurrence and replayed afterwards, so that the many small launches of a
+// few-right-hand-side product are not paced by the host.  Profiled calls always launch directly.
+void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
+                int mode, cudaStream_t s) {
+    if (nrhs <= 0) return;
+    if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec: nrhs above 2,000,000");
+    auto launch = matvec_launches(h, X, ldx, Y, ldy, nrhs, mode);
+    if (h->prof) {
+        launch(s);
+        return;
+    }
+    const void* ws = (mode == H2_FP64) ? (const void*)h->ws.f64.p : (const void*)h->ws.f32.p;
+    const void* opnd = h->tc.opnd.p;
+    MvGraph* g = nullptr;
+    for (auto& e : h->graphs)
+        if (e.X == X && e.Y == Y && e.ws == ws && e.opnd == opnd && e.ldx == ldx && e.ldy == ldy && e.nrhs == nrhs &&
+            e.mode == mode)
+            g = &e;
+    if (!g) {
+        if (h->graphs.size() >= kMaxGraphs) {
+            auto old = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                        [](const MvGraph& a, const MvGraph& b) { return a.stamp < b.stamp; });
+            if (old->exec) cudaGraphExecDestroy(old->exec);
+            if (old->graph) cudaGraphDestroy(old->graph);
+            h->graphs.erase(old);
+        }
+        MvGraph e;
+        e.X = X;
+        e.Y = Y;
+        e.ws = ws;
+        e.opnd = opnd;
+        e.ldx = ldx;
+        e.ldy = ldy;
+        e.nrhs = nrhs;
+        e.mode = mode;
+        h->graphs.push_back(e);
+        g = &h->graphs.back();
+    }
+    g->stamp = ++h->graph_clock;
+    ++g->uses;
+    if (!g->exec && g->uses >= 2) {
+        if (!h->cap) H2_CUDA(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        const int64_t l0 = g_launches.load();
+        H2_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            launch(h->cap);
+        } catch (...) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(h->cap, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            throw;
+        }
+        H2_CUDA(cudaStreamEndCapture(h->cap, &g->graph));
+        H2_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+        g->launches = g_launches.load() - l0;
+        g_launches.fetch_sub(g->launches);   // counted again at every replay
+    }
+    if (g->exec) {
+        H2_CUDA(cudaGraphLaunch(g->exec, s));
+        g_launches.fetch_add(g->launches);
+    } else {
+        launch(s);
     }
 }
 

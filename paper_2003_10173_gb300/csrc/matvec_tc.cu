@@ -532,6 +532,14 @@ void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
 
 // Tensor-core matvec for BF16 (X bf16) or TF32 (X fp32): leaf upsweep, couplings and near field
 // + leaf expansion on tcgen05; the transfer sweeps on the SIMT stage kernels (run_tree_sweeps).
+// Operand buffer of a tensor-core matvec with nrhs right-hand sides in the precision of mode.
+void tc_reserve(h2_handle_s* h, int mode, int nrhs) {
+    TcPlan& P = h->tc;
+    const int EB = (mode == H2_BF16) ? 2 : 4;
+    const int nrt = (nrhs + TC_M - 1) / TC_M;
+    P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
+}
+
 void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
                int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
                const std::function<void(int, std::function<void()>)>& timed) {
