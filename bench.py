@@ -249,14 +249,29 @@ def batching_section(h2, torch, stream) -> dict:
     torch.cuda.synchronize()
     t_pmv = e0.elapsed_time(e1) / reps
     err = max(float((y32.double() - y64).norm() / y64.norm()) for y32, y64 in zip(Y32, Y64))
+    # TF32 tensor cores: per-handle tcgen05 products between the merged SIMT sweeps
+    YT = [torch.empty_like(x) for x in X32]
+    B.matvec(X32, YT, nrhs, h2.H2_TF32, stream=stream)     # autotune + capture
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        B.matvec(X32, YT, nrhs, h2.H2_TF32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_tc = e0.elapsed_time(e1) / reps
+    err_tc = max(float((yt.double() - y64).norm() / y64.norm()) for yt, y64 in zip(YT, Y64))
     by32 = sum(matvec_bytes(G.stats(), p.N, nrhs, 4) for G, p in zip(Gs, probs))
     by64 = sum(matvec_bytes(G.stats(), p.N, nrhs, 8) for G, p in zip(plain, probs))
+    hbm = peaks()[0]
     out = {"workload": "heat2d_batch64_n64-256", "hessians": len(probs), "N_total": sum(p.N for p in probs),
            "nrhs": nrhs, "build_batched_s": t_batched, "build_plain_fp64_s": t_plain,
            "build_speedup": t_plain / t_batched,
            "matvec_batched_fp32_ms": t_bmv, "matvec_plain_fp64_ms": t_pmv, "matvec_speedup": t_pmv / t_bmv,
            "matvec_batched_GBps": by32 / (t_bmv / 1e3) / 1e9, "matvec_plain_GBps": by64 / (t_pmv / 1e3) / 1e9,
            "rhs_tile_autotuned": B.tuned(nrhs, h2.H2_FP32), "rel_err_fp32_vs_fp64_max": err,
+           "matvec_batched_tf32_tc_ms": t_tc, "matvec_batched_tf32_tc_GBps": by32 / (t_tc / 1e3) / 1e9,
+           "matvec_batched_tf32_tc_frac_of_hbm": by32 / (t_tc / 1e3) / 1e9 / hbm,
+           "matvec_tf32_tc_speedup_vs_plain_fp64": t_pmv / t_tc, "rel_err_tf32_vs_fp64_max": err_tc,
            "samples_total": sum(G.stats()["samples"] for G in Gs)}
     B.close()
     for G in Gs + plain:

@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 
 #include "handle.h"
 
@@ -29,6 +30,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int RMAX = 96;
+constexpr int64_t kBatchTcMinNrhs = 64;   // tensor-core products from this many right-hand sides on
 
 struct BStage {
     int kind = 0, out_y = 0, accumulate = 0;
@@ -40,8 +42,18 @@ struct BStage {
 
 struct Tuned {
     int rt = 32;
+    int64_t launches = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+};
+
+// Key of a captured batch sequence: right-hand sides, mode, and for the tensor-core sequence
+// (whose per-handle launches take X and Y as arguments) a digest of the X/Y pointers and strides.
+struct TuneKey {
+    int64_t nrhs;
+    int mode;
+    uint64_t io;
+    bool operator<(const TuneKey& o) const { return std::tie(nrhs, mode, io) < std::tie(o.nrhs, o.mode, o.io); }
 };
 
 }  // namespace
@@ -52,13 +64,20 @@ struct h2_batch_s {
     std::vector<h2::BStage> stages;
     h2::DevBuf<h2::BatchBase> d_bases;
     h2::Stager st_bases;
-    std::map<std::pair<int64_t, int>, h2::Tuned> tuned;
+    std::map<h2::TuneKey, h2::Tuned> tuned;
     cudaStream_t cap = nullptr;
+    // side streams of the per-handle tensor-core phases (fork/join with events, also when captured)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;
+    cudaEvent_t fork_ev = nullptr;
     ~h2_batch_s() {
         for (auto& kv : tuned) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
             if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
         }
+        for (auto st : side) cudaStreamDestroy(st);
+        for (auto e : side_ev) cudaEventDestroy(e);
+        if (fork_ev) cudaEventDestroy(fork_ev);
         if (cap) cudaStreamDestroy(cap);
     }
 };
@@ -131,6 +150,49 @@ void launch_all(h2_batch_s* b, int mode, int rt, int nrhs, cudaStream_t s) {
         launch_batch_stage(mode, rt, m.out_y, m.accumulate, m.d_outs.p, (int)m.outs.size(), m.d_items.p,
                            b->d_bases.p, nrhs, s);
     }
+}
+
+// Tensor-core sequence (TF32 / BF16, nrhs >= 64): every handle's leaf upsweep, couplings and
+// near field + leaf expansion on tcgen05, between the merged SIMT transfer sweeps of all handles.
+void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* const* X, const int64_t* ldx,
+               void* const* Y, const int64_t* ldy, cudaStream_t s) {
+    constexpr int kSide = 8;
+    if (b->side.empty()) {
+        b->side.resize(kSide);
+        b->side_ev.resize(kSide);
+        for (int k = 0; k < kSide; ++k) {
+            H2_CUDA(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+            H2_CUDA(cudaEventCreateWithFlags(&b->side_ev[k], cudaEventDisableTiming));
+        }
+        H2_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+    }
+    // the handles' phase launches are independent (own operand buffers and workspaces): spread
+    // them over the side streams so that the small grids of different Hessians run together
+    auto phase = [&](int ph) {
+        H2_CUDA(cudaEventRecord(b->fork_ev, s));
+        for (int k = 0; k < kSide; ++k) H2_CUDA(cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            h2_handle_s* h = b->hs[i];
+            tc_phase(h, mode, ph, X[i], ldx[i], (float*)Y[i], ldy[i], nrhs, h->ws.f32.p, h->plan.ws_rows,
+                     b->side[i % kSide]);
+        }
+        for (int k = 0; k < kSide; ++k) {
+            H2_CUDA(cudaEventRecord(b->side_ev[k], b->side[k]));
+            H2_CUDA(cudaStreamWaitEvent(s, b->side_ev[k], 0));
+        }
+    };
+    auto sweeps = [&](int kind) {
+        for (BStage& m : b->stages) {
+            if (m.outs.empty() || m.kind != kind) continue;
+            launch_batch_stage(md, rt, m.out_y, m.accumulate, m.d_outs.p, (int)m.outs.size(), m.d_items.p,
+                               b->d_bases.p, nrhs, s);
+        }
+    };
+    phase(0);
+    sweeps(H2_STAGE_UP);
+    phase(1);
+    sweeps(H2_STAGE_DOWN);
+    phase(2);
 }
 
 }  // namespace
@@ -246,11 +308,28 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
         x.ldy = ldy[i];
     }
     upload(b->d_bases, bases, s, b->st_bases);
+    // SIMT arithmetic type of the merged stages (TF32 factors are the FP32 copy)
     const int md = (mode == H2_TF32) ? H2_FP32 : mode;
-    auto key = std::make_pair(nrhs, md);
+    bool tc = (mode == H2_TF32 || mode == H2_BF16) && nrhs >= kBatchTcMinNrhs;
+    for (auto* h : b->hs) tc = tc && tc_supported(h) && ((mode == H2_BF16) ? h->tc.W16.p : h->tc.W32.p);
+    uint64_t io = 0;
+    if (tc) {
+        for (int i = 0; i < n; ++i) {
+            tc_reserve(b->hs[i], mode, (int)nrhs);
+            // buffers the per-handle launches take as arguments (the captured graph holds them)
+            for (uint64_t v : {(uint64_t)(uintptr_t)X[i], (uint64_t)ldx[i], (uint64_t)(uintptr_t)Y[i], (uint64_t)ldy[i],
+                               (uint64_t)(uintptr_t)b->hs[i]->ws.f32.p, (uint64_t)(uintptr_t)b->hs[i]->tc.opnd.p})
+                io = mix64(io ^ v);
+        }
+    }
+    auto seq = [&](int rt, cudaStream_t st) {
+        if (tc) launch_tc(b, mode, md, rt, (int)nrhs, X, ldx, Y, ldy, st);
+        else launch_all(b, md, rt, (int)nrhs, st);
+    };
+    const TuneKey key{nrhs, tc ? mode : md, io};
     auto it = b->tuned.find(key);
     if (it == b->tuned.end()) {
-        // autotune the right-hand-side tile on this call's data, then capture the sequence
+        // autotune the right-hand-side tile of the SIMT stages on this call's data, then capture
         H2_CUDA(cudaStreamSynchronize(s));
         Tuned t;
         float best = 1e30f;
@@ -258,9 +337,9 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
         H2_CUDA(cudaEventCreate(&e0));
         H2_CUDA(cudaEventCreate(&e1));
         for (int rt : {8, 16, 32}) {
-            launch_all(b, md, rt, (int)nrhs, s);   // warm-up
+            seq(rt, s);   // warm-up
             H2_CUDA(cudaEventRecord(e0, s));
-            launch_all(b, md, rt, (int)nrhs, s);
+            seq(rt, s);
             H2_CUDA(cudaEventRecord(e1, s));
             H2_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -269,22 +348,31 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        const int64_t l0 = g_launches.load();
         H2_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-        launch_all(b, md, t.rt, (int)nrhs, b->cap);
+        try {
+            seq(t.rt, b->cap);
+        } catch (...) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(b->cap, &junk);
+            if (junk) cudaGraphDestroy(junk);
+            throw;
+        }
         H2_CUDA(cudaStreamEndCapture(b->cap, &t.graph));
         H2_CUDA(cudaGraphInstantiate(&t.exec, t.graph, 0));
+        t.launches = g_launches.load() - l0;
+        g_launches.fetch_sub(t.launches);   // counted at every replay
         it = b->tuned.emplace(key, t).first;
     }
     H2_CUDA(cudaGraphLaunch(it->second.exec, s));
-    int64_t nk = 0;
-    for (const BStage& m : b->stages) nk += m.outs.empty() ? 0 : 1;
-    g_launches.fetch_add(nk, std::memory_order_relaxed);
+    g_launches.fetch_add(it->second.launches, std::memory_order_relaxed);
 }
 
 int batch_tuned(h2_batch_s* b, int64_t nrhs, int mode) {
     const int md = (mode == H2_TF32) ? H2_FP32 : mode;
-    auto it = b->tuned.find(std::make_pair(nrhs, md));
-    return it == b->tuned.end() ? 0 : it->second.rt;
+    for (const auto& kv : b->tuned)
+        if (kv.first.nrhs == nrhs && (kv.first.mode == mode || kv.first.mode == md)) return kv.second.rt;
+    return 0;
 }
 
 }  // namespace h2

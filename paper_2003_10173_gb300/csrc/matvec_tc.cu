@@ -10,10 +10,10 @@
 // padded operand buffer (X in tree order, xh and yh of every box, K-major per right-hand
 // side); B operands are the factors' blocks, one tile per use, pre-rounded and pre-laid out
 // in the canonical K-major core-matrix layout so that a tile load is a contiguous copy.
-// One producer thread stages each item's A and B tiles in shared memory with bulk asynchronous
+// A producer thread stages each item's A and B tiles in shared memory with bulk asynchronous
 // copies (cp.async.bulk, completion counted in bytes on a per-stage mbarrier) into a ring of
-// 4 (BF16) or 3 (TF32) stages; one thread issues the MMAs and commits them to a per-stage
-// mbarrier that releases the stage.  The accumulator is read
+// 4 (BF16) or 3 (TF32) stages; a thread of another warp issues the MMAs as the operands land and
+// commits them to a per-stage mbarrier that releases the stage to the producer.  The accumulator is read
 // with tcgen05.ld, transposed through shared memory and written to Y (through the tree
 // permutation) or to the coefficient workspace.  Every mbarrier wait is bounded: on timeout
 // the kernel records a device error, drains its copies, frees its tensor memory and returns.
@@ -32,6 +32,7 @@ constexpr int TC_M = 128;      // right-hand sides per CTA (MMA M)
 constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // about one second
+constexpr int TC_ITEM_CACHE = 256;                   // item descriptors staged in shared memory
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ uint32_t tmem_slot;
-    __shared__ int okflag;
+    __shared__ int okflag, prod_issued, cons_done;
+    __shared__ TcItem sitems[TC_ITEM_CACHE];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int rt = blockIdx.x;
@@ -139,12 +141,18 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     const int nitem = o.end - o.beg;
     const int N = o.n;
 
+    // the output's item descriptors, staged once in shared memory (off the producer's critical path)
+    const bool cached = nitem <= TC_ITEM_CACHE;
+    if (cached)
+        for (int i = tid; i < nitem; i += TC_THREADS) sitems[i] = items[o.beg + i];
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
         }
         okflag = 1;
+        prod_issued = 0;
+        cons_done = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -156,13 +164,16 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    auto item_at = [&](int it) -> TcItem { return cached ? sitems[it] : items[o.beg + it]; };
 
-    // one thread produces (bulk copies) and consumes (MMAs); the others wait for the epilogue
+    // warp-specialised pipeline: thread 0 copies operands into the stage ring, thread 32 issues
+    // the MMAs; a stage is refilled as soon as the MMAs that read it have completed
     if (tid == 0) {
-        const uint32_t idesc = (1u << 4) | (Tr::ab_fmt << 7) | (Tr::ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-                               ((uint32_t)(TC_M >> 4) << 24);
-        auto issue = [&](int it, int st) {
-            const TcItem m = items[o.beg + it];
+        int issued = 0;
+        for (; issued < nitem; ++issued) {
+            const int st = issued % S;
+            if (issued >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((issued / S) - 1) & 1), err)) break;
+            const TcItem m = item_at(issued);
             const uint32_t abytes = (uint32_t)(TC_M * m.k * EB);
             const uint32_t bbytes = (uint32_t)(N * m.k * EB);
             const uint32_t sa = smem_u32(smem + st * C::STAGE_BYTES);
@@ -172,17 +183,17 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
             const int64_t aoff = ((int64_t)m.a_row * gridDim.x * TC_M + (int64_t)rt * TC_M * m.k) * EB;
             bulk_g2s(sa, opnd + aoff, abytes, fb);
             bulk_g2s(sa + C::A_BYTES, W + m.b_off, bbytes, fb);
-        };
-        bool ok = true;
-        int issued = 0;
-        for (; issued < S && issued < nitem; ++issued) issue(issued, issued);
-        int done = 0;
-        for (int it = 0; it < nitem; ++it) {
+        }
+        prod_issued = issued;
+    } else if (tid == 32) {
+        const uint32_t idesc = (1u << 4) | (Tr::ab_fmt << 7) | (Tr::ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        int it = 0;
+        for (; it < nitem; ++it) {
             const int st = it % S;
-            const uint32_t ph = (uint32_t)((it / S) & 1);
-            if (!mbar_wait(smem_u32(&full[st]), ph, err)) { ok = false; break; }
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((it / S) & 1), err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int K = items[o.beg + it].k;
+            const int K = item_at(it).k;
             const uint32_t a0 = smem_u32(smem + st * C::STAGE_BYTES);
             const uint32_t b0 = a0 + C::A_BYTES;
             const uint32_t SBO = (uint32_t)(K * EB / 16) * 128;
@@ -193,24 +204,18 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&empty[st])));
-            done = it + 1;
-            if (issued < nitem) {
-                // the stage is free again once the MMAs just issued have read it
-                if (!mbar_wait(smem_u32(&empty[st]), ph, err)) { ok = false; break; }
-                issue(issued, st);
-                ++issued;
-            }
         }
-        if (ok && nitem > 0) {
-            const int last = nitem - 1;
-            ok = mbar_wait(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1), err);
-        }
-        if (!ok) {
-            // let copies already issued land before the shared memory is reused or released
-            for (int it = done; it < issued; ++it)
-                mbar_wait(smem_u32(&full[it % S]), (uint32_t)((it / S) & 1), err);
-            okflag = 0;
-        }
+        cons_done = it;
+        // every MMA issued completes before the accumulator is read or released
+        if (it > 0 && !mbar_wait(smem_u32(&empty[(it - 1) % S]), (uint32_t)(((it - 1) / S) & 1), err)) it = -1;
+        if (it != nitem) okflag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // copies issued for items that were never consumed land before the memory is reused
+        for (int j = cons_done; j < prod_issued; ++j)
+            mbar_wait(smem_u32(&full[j % S]), (uint32_t)((j / S) & 1), err);
+        if (prod_issued != nitem) okflag = 0;
     }
     __syncthreads();
     const bool ok = okflag != 0;
@@ -540,17 +545,17 @@ void tc_reserve(h2_handle_s* h, int mode, int nrhs) {
     P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
 }
 
-void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
-               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
-               const std::function<void(int, std::function<void()>)>& timed) {
+// One phase of the tensor-core matvec: 0 packs X and computes the leaf coefficients xh, 1 packs
+// xh and computes the couplings into yh, 2 packs yh and computes Y = U yh + near field.  The
+// transfer sweeps between the phases run on the SIMT path.
+void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs,
+              float* ws, int64_t ws_ld, cudaStream_t s) {
     TcPlan& P = h->tc;
     const int EB = (mode == H2_BF16) ? 2 : 4;
     const int nrt = (nrhs + TC_M - 1) / TC_M;
     P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
     const unsigned char* W = (mode == H2_BF16) ? P.W16.p : P.W32.p;
     if (!W) fail(H2_ERR_INVALID_ARG, "h2_matvec: tensor-core tiles of this precision were not kept");
-    const int64_t xel = (int64_t)P.nleaf * P.LP * nrt * TC_M;
-    const unsigned g = (unsigned)std::min<int64_t>((xel + 255) / 256, 152 * 32);
     auto run = [&](TcStage& st) {
         if (st.outs.empty()) return;
         if (EB == 2)
@@ -567,7 +572,9 @@ void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, i
         after_launch("tc_pack_coef");
     };
     P.cur_eb = EB;
-    timed(H2_STAGE_LEAF_UP, [&] {
+    if (phase == 0) {
+        const int64_t xel = (int64_t)P.nleaf * P.LP * nrt * TC_M;
+        const unsigned g = (unsigned)std::min<int64_t>((xel + 255) / 256, 152 * 32);
         if (EB == 2)
             tc_pack_x_kernel<__nv_bfloat16, 2><<<g, 256, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p,
                                                                   P.d_leaf_start.p, P.d_leaf_size.p, P.LP, P.nleaf,
@@ -577,17 +584,23 @@ void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, i
                                                          P.d_leaf_size.p, P.LP, P.nleaf, nrhs, nrt, P.opnd.p);
         after_launch("tc_pack_x");
         run(P.leaf_up);
-    });
-    sweeps(0);   // transfer upsweep (SIMT)
-    timed(H2_STAGE_COUPLE, [&] {
+    } else if (phase == 1) {
         pack_coef(P.xh_boxes, P.d_xh_boxes, P.d_xh_src);
         run(P.couple);
-    });
-    sweeps(1);   // transfer downsweep (SIMT)
-    timed(H2_STAGE_NEAR, [&] {
+    } else {
         pack_coef(P.yh_boxes, P.d_yh_boxes, P.d_yh_src);
         run(P.near);
-    });
+    }
+}
+
+void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
+               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
+               const std::function<void(int, std::function<void()>)>& timed) {
+    timed(H2_STAGE_LEAF_UP, [&] { tc_phase(h, mode, 0, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
+    sweeps(0);   // transfer upsweep (SIMT)
+    timed(H2_STAGE_COUPLE, [&] { tc_phase(h, mode, 1, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
+    sweeps(1);   // transfer downsweep (SIMT)
+    timed(H2_STAGE_NEAR, [&] { tc_phase(h, mode, 2, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
 }
 
 int tc_device_error(h2_handle_s* h) {

@@ -21,7 +21,7 @@ def setup():
              for n, k, kap in ((24, 9, 0.02), (31, 12, 0.01), (40, 7, 0.005), (48, 16, 0.03), (57, 10, 0.01))]
     ops = [h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed)) for p in probs]
     trees = [h2.Tree(W.grid_coords(p.n), 32, h2.H2_ADM_STRONG, 0.7) for p in probs]
-    opts = h2.default_opts(kmax=32, q0=32, b_inc=16, q_max=128, adaptive=1, seed=3, keep_fp32=1)
+    opts = h2.default_opts(kmax=32, q0=32, b_inc=16, q_max=128, adaptive=1, seed=3, keep_fp32=1, keep_bf16=1)
     batched = h2.build_batched(ops, trees, 1e-6, opts)
     single = [h2.H2.build(op, t, 1e-6, opts) for op, t in zip(ops, trees)]
     return h2, probs, ops, trees, batched, single
@@ -73,4 +73,27 @@ def test_one_shot_batched_matvec_equals_batch(setup):
     torch.cuda.synchronize()
     for a, b in zip(Y1, Y2):
         assert torch.equal(a, b)      # same tuned tile candidates, same kernels, same order
+    B.close()
+
+
+@pytest.mark.parametrize("mode,nrhs", [(2, 64), (2, 130), (3, 64), (3, 130)])
+def test_batch_tensor_core_matvec_equals_individual(setup, mode, nrhs):
+    """TF32 / BF16 with nrhs >= 64: per-handle tensor-core phases between merged SIMT sweeps; the
+    result equals each handle's own tensor-core matvec (same products, same summation order),
+    also when the graph is replayed and when the buffers change (recaptured)."""
+    h2, probs, ops, trees, batched, single = setup
+    xdt = torch.float32 if mode == h2.H2_TF32 else torch.bfloat16
+    B = h2.Batch(batched)
+    for trial in range(2):
+        Xs = [torch.from_numpy(np.ascontiguousarray(W.rhs(p.N, nrhs, 90 + i + 7 * trial).T)).to("cuda", xdt)
+              for i, p in enumerate(probs)]
+        Ys = [torch.full((nrhs, p.N), float("nan"), dtype=torch.float32, device="cuda") for p in probs]
+        B.matvec(Xs, Ys, nrhs, mode)
+        B.matvec(Xs, Ys, nrhs, mode)      # replay
+        torch.cuda.synchronize()
+        for G, X, Y in zip(single, Xs, Ys):
+            R = torch.empty_like(Y)
+            G.matvec(X, R, nrhs, mode)
+            torch.cuda.synchronize()
+            assert torch.equal(R, Y)
     B.close()
