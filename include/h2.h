@@ -320,6 +320,55 @@ int h2_get_stats(h2_handle_t h, h2_stats* out);
 /* Release a handle and its device memory.  NULL is a no-op. */
 void h2_free(h2_handle_t h);
 
+/* ---- iterative inversion --------------------------------------------------------- */
+
+/*
+ * Approximate inverse of A = H + shift I (H an H^2 handle, symmetric positive definite with the
+ * shift) by the hierarchical hyperpower iteration of Appendix A: X_{k+1} = X_k sum_{i<l} R_k^i,
+ * R_k = I - A X_k (order l = 2: Newton-Schulz, Algorithm 1), every iterate constructed by peeling
+ * (h2_build's method, Section 3.3) from a sampler that applies the iteration to probe blocks with
+ * H^2 matvecs of A and X_k (Algorithms 2 and 4).  X_0 = I / ||A||_2 (power iteration).  Iterate k
+ * is constructed to the relative threshold eps_k = max(eps / (||A|| ||X_k||), min(eps_loose,
+ * theta E^2)) with E = ||A X_k - I||_2 (power iteration on (X A - I)(A X - I), stopped at
+ * res_rtol relative change); eps_loose = eps gives the static threshold.  The iteration stops at
+ * E <= eps, after max_iter iterates, or when an iterate stalls (E_{k+1} > 0.9 E_k while the exact
+ * iteration would reach E_k^l < 0.5 E_{k+1}).  Not a construct of this library's paper beyond
+ * Appendix A; the readings above are the library's.
+ */
+#define H2_MAX_INVERT_ITERS 64
+typedef struct {
+    int order;           /* hyperpower order l >= 2 (default 2: Newton-Schulz) */
+    double eps;          /* target ||A X - I||_2 (default 1e-6) */
+    double eps_loose;    /* loosest construction threshold (default 1e-6, i.e. static) */
+    double theta;        /* factor of E^2 in the dynamic threshold (default 0.1) */
+    int max_iter;        /* iterate cap, 0..H2_MAX_INVERT_ITERS (default 50) */
+    double shift;        /* A = H + shift I (default 0) */
+    int res_maxit;       /* power-iteration cap of the norm and residual estimates (default 50) */
+    double res_rtol;     /* their stop: relative change (default 1e-2) */
+    uint64_t seed;       /* seed of the power-iteration start vectors (default 9) */
+} h2_invert_opts;
+
+typedef struct {
+    int iterations;                              /* iterates constructed */
+    int converged;                               /* 1 if the final E <= eps */
+    double norm_A, alpha;                        /* ||A||_2 estimate; X_0 = alpha I */
+    double err[H2_MAX_INVERT_ITERS + 1];         /* E before iterate k (k < iterations), then the final E */
+    double eps_k[H2_MAX_INVERT_ITERS];           /* construction threshold of iterate k */
+    int64_t samples[H2_MAX_INVERT_ITERS];        /* peeling products of iterate k */
+    double t_build[H2_MAX_INVERT_ITERS];         /* seconds of iterate k's construction */
+    double final_err, t_total;
+} h2_invert_stats;
+
+/* Fill *opts with the defaults above.  Returns H2_ERR_INVALID_ARG if opts is NULL. */
+int h2_invert_opts_default(h2_invert_opts* opts);
+
+/* X_out receives the last iterate (a new handle on A's tree; free with h2_free); build_opts (may
+ * be NULL) configure every construction (their stream carries all work).  stats may be NULL.
+ * Errors: INVALID_ARG, CUDA, OOM, NAN, OP_FAILED; the result of a run that stopped unconverged
+ * is still returned with H2_WARN_TOL_NOT_MET. */
+int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* build_opts, h2_handle_t* X_out,
+              h2_invert_stats* stats);
+
 /* ---- learned rank model ------------------------------------------------------ */
 
 /*

@@ -49,6 +49,34 @@ class BuildOpts(ctypes.Structure):
     ]
 
 
+H2_MAX_INVERT_ITERS = 64
+
+
+class InvertOpts(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int), ("eps", ctypes.c_double), ("eps_loose", ctypes.c_double),
+        ("theta", ctypes.c_double), ("max_iter", ctypes.c_int), ("shift", ctypes.c_double),
+        ("res_maxit", ctypes.c_int), ("res_rtol", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+class InvertStats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("norm_A", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("err", ctypes.c_double * (H2_MAX_INVERT_ITERS + 1)),
+        ("eps_k", ctypes.c_double * H2_MAX_INVERT_ITERS), ("samples", ctypes.c_int64 * H2_MAX_INVERT_ITERS),
+        ("t_build", ctypes.c_double * H2_MAX_INVERT_ITERS), ("final_err", ctypes.c_double),
+        ("t_total", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        k = self.iterations
+        return {"iterations": k, "converged": bool(self.converged), "norm_A": self.norm_A, "alpha": self.alpha,
+                "err": [float(x) for x in self.err[:k + 1]], "eps_k": [float(x) for x in self.eps_k[:k]],
+                "samples": [int(x) for x in self.samples[:k]], "t_build": [float(x) for x in self.t_build[:k]],
+                "final_err": self.final_err, "t_total": self.t_total}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int64), ("levels", ctypes.c_int), ("leaf_max", ctypes.c_int),
@@ -109,6 +137,9 @@ _SIGS = {
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P]),
     "h2_free": (None, [_P]),
+    "h2_invert_opts_default": (_I, [ctypes.POINTER(InvertOpts)]),
+    "h2_invert": (_I, [_P, ctypes.POINTER(InvertOpts), ctypes.POINTER(BuildOpts), ctypes.POINTER(_P),
+                       ctypes.POINTER(InvertStats)]),
     "h2_rankmodel_create": (_I, [ctypes.c_uint64, _I, ctypes.POINTER(_P)]),
     "h2_rankmodel_free": (None, [_P]),
     "h2_rankmodel_get": (_I, [_P, _P, _P, _P, _P]),
@@ -405,6 +436,23 @@ class H2:
             self.close()
         except Exception:
             pass
+
+
+def invert(A: "H2", shift: float = 0.0, order: int = 2, eps: float = 1e-6, eps_loose: float | None = None,
+           theta: float = 0.1, max_iter: int = 50, build_opts: BuildOpts | None = None, **kw):
+    """Hierarchical hyperpower (order 2: Newton-Schulz) inverse of A + shift I; returns (H2, stats)."""
+    o = InvertOpts()
+    _check(lib().h2_invert_opts_default(ctypes.byref(o)))
+    o.order, o.eps, o.theta, o.max_iter, o.shift = order, eps, theta, max_iter, shift
+    o.eps_loose = eps if eps_loose is None else eps_loose
+    for k, v in kw.items():
+        setattr(o, k, v)
+    st = InvertStats()
+    h = ctypes.c_void_p()
+    status = lib().h2_invert(A._h, ctypes.byref(o), ctypes.byref(build_opts) if build_opts is not None else None,
+                             ctypes.byref(h), ctypes.byref(st))
+    _check(status, allow_warn=True)
+    return H2(h, status), st.as_dict()
 
 
 def gemm_profile(enable: bool = True):

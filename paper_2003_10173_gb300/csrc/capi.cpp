@@ -27,6 +27,7 @@ void rm_predict(h2_rankmodel_s* m, const float* X, int64_t n, float* Y, cudaStre
 void rm_q_levels(h2_rankmodel_s* m, const h2_tree_s* t, double kT, double dens, double tol, int pad, int q_max,
                  int32_t* q, float* y_host);
 void rm_save(h2_rankmodel_s* m, const char* path);
+void invert(h2_handle_s* A, const h2_invert_opts& io, const h2_build_opts& bo, h2_handle_s** Xout, h2_invert_stats* st);
 h2_rankmodel_s* rm_load(const char* path);
 
 // Device permutation, matvec plan, reduced-precision copies and statistics of a built handle.
@@ -299,6 +300,46 @@ int h2_rankmodel_set(h2_rankmodel_t m, const float* p, const float* am, const fl
         require(m != nullptr, "h2_rankmodel_set: NULL model");
         h2::rm_set(m, p, am, av, step);
         return H2_OK;
+    });
+}
+
+int h2_invert_opts_default(h2_invert_opts* o) {
+    if (!o) return H2_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->order = 2;
+    o->eps = 1e-6;
+    o->eps_loose = 1e-6;
+    o->theta = 0.1;
+    o->max_iter = 50;
+    o->shift = 0.0;
+    o->res_maxit = 50;
+    o->res_rtol = 1e-2;
+    o->seed = 9;
+    return H2_OK;
+}
+
+int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* build_opts, h2_handle_t* X_out,
+              h2_invert_stats* stats) {
+    return guard([&] {
+        require(X_out != nullptr, "h2_invert: X_out is NULL");
+        *X_out = nullptr;
+        require(A != nullptr, "h2_invert: NULL handle");
+        h2_invert_opts io;
+        h2_invert_opts_default(&io);
+        if (opts) io = *opts;
+        require(io.order >= 2 && io.order <= 64, "h2_invert: order must be in 2..64");
+        require(io.eps > 0.0 && std::isfinite(io.eps), "h2_invert: eps must be positive");
+        require(io.eps_loose >= io.eps && std::isfinite(io.eps_loose), "h2_invert: need eps_loose >= eps");
+        require(io.theta > 0.0 && std::isfinite(io.theta), "h2_invert: theta must be positive");
+        require(io.max_iter >= 0 && io.max_iter <= H2_MAX_INVERT_ITERS, "h2_invert: max_iter out of range");
+        require(std::isfinite(io.shift), "h2_invert: shift must be finite");
+        require(io.res_maxit >= 1 && io.res_rtol > 0.0, "h2_invert: bad power-iteration settings");
+        h2_build_opts bo = checked_opts(io.eps, build_opts);
+        h2_invert_stats local;
+        h2_handle_s* X = nullptr;
+        h2::invert(A, io, bo, &X, stats ? stats : &local);
+        *X_out = X;
+        return (stats ? stats : &local)->converged ? (int)H2_OK : (int)H2_WARN_TOL_NOT_MET;
     });
 }
 
