@@ -372,6 +372,40 @@ def learned_ranks_section(h2, torch, stream) -> dict:
     return out
 
 
+def inversion_section(h2, torch, stream) -> dict:
+    """Appendix A on the regularised 128 x 128 heat Hessian (N = 16,384, the paper's inversion size):
+    A = H~ + beta I with H~ the H^2 approximation (tol 1e-6, leaf 64, strong 0.7) and beta =
+    0.01 ||H~|| (condition number about 100); Newton-Schulz with the static threshold, with the
+    dynamic threshold (loosest 1e-2), and order-8 hyperpower with the dynamic threshold, each from
+    X_0 = I / ||A||_2 to ||A X - I||_2 <= 1e-4 (construction floor 1e-4 / (||A|| ||X_k||), about
+    1e-6 near convergence: the paper's construction threshold)."""
+    c = scaled(W.MEDIUM_N256, 128)
+    p, b = c["problem"], c["build"]
+    gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+    tree = h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta)
+    HA = h2.H2.build(gop, tree, b.tol, h2.default_opts(kmax=b.kmax, stream=stream))
+    beta = 0.01 * HA.stats()["norm_est"]
+    bopts = h2.default_opts(kmax=48, q0=16, b_inc=8, q_max=512, adaptive=1, seed=b.seed, stream=stream)
+    eps = 1e-4
+    out = {"workload": f"heat2d_n128 regularised, A = H~ + {beta:.4g} I", "N": p.N, "eps": eps, "runs": {}}
+    for key, order, loose in (("ns_static", 2, eps), ("ns_dynamic", 2, 1e-2), ("hyperpower8_dynamic", 8, 1e-2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, st = h2.invert(HA, shift=beta, order=order, eps=eps, eps_loose=loose, build_opts=bopts)
+        torch.cuda.synchronize()
+        out["runs"][key] = {"order": order, "eps_loose": loose, "iterations": st["iterations"],
+                            "converged": st["converged"], "final_err": st["final_err"],
+                            "samples_total": int(sum(st["samples"])), "samples": st["samples"],
+                            "seconds": time.perf_counter() - t0, "build_seconds": float(sum(st["t_build"]))}
+        X.close()
+    out["context_paper_p100_s"] = {"ns_static": 178, "ns_dynamic": 51, "hyperpower8": 20,
+                                   "note": "minimal-surface Hessian at n = 16,384 on a P100 (Appendix A); "
+                                           "another operator and machine: context only"}
+    HA.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
     """The oracle as it stands on a bounded sample of the workload: the same operator family
     (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
@@ -463,6 +497,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-inversion", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
     ap.add_argument("--precision-n", type=int, default=512, help="grid size of the precision section")
@@ -640,6 +675,10 @@ def main():
     if rank == 0 and not args.no_learned:
         learned = learned_ranks_section(h2, torch, stream)
 
+    inversion = None
+    if rank == 0 and not args.no_inversion:
+        inversion = inversion_section(h2, torch, stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -668,6 +707,8 @@ def main():
             line["batching"] = batching
         if learned is not None:
             line["learned_ranks"] = learned
+        if inversion is not None:
+            line["inversion"] = inversion
         if cpu is not None:
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(line), flush=True)
