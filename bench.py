@@ -37,9 +37,9 @@ import workloads as W  # noqa: E402
 METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
 CFG = W.MEDIUM_N256
 # DRAM bytes (read + write) per gemm_tiles_kernel launch of the bench command, from an ncu capture
-# of every launch of that kernel (dram__bytes_read.sum + dram__bytes_write.sum, 1,147 launches);
+# of every launch of that kernel (dram__bytes_read.sum + dram__bytes_write.sum, 1,510 launches);
 # reset to None whenever the kernel changes
-GEMM_TRAFFIC_PER_LAUNCH = None
+GEMM_TRAFFIC_PER_LAUNCH = 27.32e6
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
