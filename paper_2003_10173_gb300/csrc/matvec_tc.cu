@@ -12,8 +12,9 @@
 // in the canonical K-major core-matrix layout so that a tile load is a contiguous copy.
 // A producer thread stages each item's A and B tiles in shared memory with bulk asynchronous
 // copies (cp.async.bulk, completion counted in bytes on a per-stage mbarrier) into a ring of
-// 4 (BF16) or 3 (TF32) stages; a thread of another warp issues the MMAs as the operands land and
-// commits them to a per-stage mbarrier that releases the stage to the producer.  The accumulator is read
+// 2 stages (so that several CTAs share an SM and one CTA's epilogue overlaps another's main loop);
+// a thread of another warp issues the MMAs as the operands land and commits them to a per-stage
+// mbarrier that releases the stage to the producer.  The accumulator is read
 // with tcgen05.ld, transposed through shared memory and written to Y (through the tree
 // permutation) or to the coefficient workspace.  Every mbarrier wait is bounded: on timeout
 // the kernel records a device error, drains its copies, frees its tensor memory and returns.
@@ -102,7 +103,7 @@ constexpr int TC_NMAX = 64, TC_KMAX = 64;
 
 template <int EB>
 struct TcCfg {
-    static constexpr int STAGES = EB == 2 ? 4 : 3;
+    static constexpr int STAGES = 2;
     static constexpr int A_BYTES = TC_M * TC_KMAX * EB;
     static constexpr int B_BYTES = TC_NMAX * TC_KMAX * EB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
