@@ -572,7 +572,8 @@ void Builder::assemble(h2_handle_s* h) {
             std::vector<int> nn(nleaf);
             for (int t = 0; t < nleaf; ++t) nn[t] = bsize(L, t);
             d_k.reserve(nleaf);
-            jacobi_eig_trunc(nleaf, dev_list(d_i64a_, goff, 0), dev_list(d_i32a_, nn, 1), Gbuf.p,
+            jacobi_eig_trunc(nleaf, dev_list(d_i64a_, goff, 0), dev_list(d_i32a_, nn, 1),
+                             *std::max_element(nn.begin(), nn.end()), Gbuf.p,
                              dev_list(d_i64b_, utmp_off, 2), Utmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nleaf);
             for (int t = 0; t < nleaf; ++t) K(L, t) = kk[t];
@@ -630,7 +631,8 @@ void Builder::assemble(h2_handle_s* h) {
             }
             gb_.run(s_);
             d_k.reserve(nb);
-            jacobi_eig_trunc(nb, dev_list(d_i64a_, go, 0), dev_list(d_i32a_, nn, 1), Gbuf.p, dev_list(d_i64b_, uo, 2),
+            jacobi_eig_trunc(nb, dev_list(d_i64a_, go, 0), dev_list(d_i32a_, nn, 1), *std::max_element(nn.begin(), nn.end()),
+                             Gbuf.p, dev_list(d_i64b_, uo, 2),
                              Uhtmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nb);
             for (int p = 0; p < nb; ++p) K(l, p) = kk[p];

@@ -171,7 +171,8 @@ void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c,
                        int ldy, double* out, cudaStream_t s);
 // Symmetric eigen-decomposition (cyclic Jacobi) of count n_i x n_i matrices, keeping the
 // eigenvectors with eigenvalue > thr (at most kmax), sorted descending.
-void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, const double* A,
+// max_n: the largest n_i (host value; sizes the kernel's shared memory).
+void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, int max_n, const double* A,
                       const int64_t* d_u_off, double* U, int* d_k_out, double thr, int kmax,
                       int* d_cap_flag, cudaStream_t s);
 

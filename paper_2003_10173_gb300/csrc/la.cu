@@ -552,16 +552,19 @@ void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c,
     after_launch("colnorm_max");
 }
 
-void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, const double* A,
+void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, int max_n, const double* A,
                       const int64_t* d_u_off, double* U, int* d_k_out, double thr, int kmax,
                       int* d_cap_flag, cudaStream_t s) {
     if (count <= 0) return;
-    const int np = EIG_MAXN;
-    const size_t smem = 2 * (size_t)np * (np + 1) * sizeof(double);
+    if (max_n < 0 || max_n > EIG_MAXN) fail(H2_ERR_INVALID_ARG, "jacobi: matrix order above 96");
     static std::once_flag attr_set;
     std::call_once(attr_set, [&] {
-        H2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int top = 2 * EIG_MAXN * (EIG_MAXN + 1) * (int)sizeof(double);
+        H2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, top));
     });
+    // shared memory for the largest matrix of this launch only: more CTAs per SM when they are small
+    const int np = max_n + (max_n & 1);
+    const size_t smem = std::max<size_t>(2 * (size_t)np * (np + 1) * sizeof(double), 16);
     jacobi_kernel<<<count, NT, smem, s>>>(d_a_off, d_n, A, d_u_off, U, d_k_out, thr, kmax, d_cap_flag);
     after_launch("jacobi_eig");
 }
