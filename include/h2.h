@@ -64,7 +64,9 @@ enum {
     H2_FP64 = 0,   /* X, Y double; FP64 storage and arithmetic */
     H2_FP32 = 1,   /* X, Y float; FP32 storage and arithmetic */
     H2_TF32 = 2,   /* X float, Y float; FP32 storage, TF32 tensor-core products, FP32 accumulation */
-    H2_BF16 = 3    /* X bf16 (uint16 storage), Y float; BF16 storage, tensor-core products, FP32 accumulation */
+    H2_BF16 = 3,   /* X bf16 (uint16 storage), Y float; BF16 storage, tensor-core products, FP32 accumulation */
+    H2_TF32X3 = 4  /* X float, Y float; FP32 storage, split-TF32 tensor-core products (hi*hi + hi*lo + lo*hi,
+                      about 22 significant bits, FP32-grade) from nrhs >= 64, FP32 arithmetic below */
 };
 
 #define H2_MAX_LEVELS 32

@@ -32,6 +32,7 @@ H2_FP64 = 0
 H2_FP32 = 1
 H2_TF32 = 2
 H2_BF16 = 3
+H2_TF32X3 = 4
 
 H2_MAX_LEVELS = 32
 

@@ -285,6 +285,7 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
                 break;
             case H2_FP32:
             case H2_TF32:
+            case H2_TF32X3:
                 if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_batch_matvec: FP32 copy of the factors was not kept");
                 h->ws.f32.reserve((size_t)need);
                 x.fac = h->fac32.p;
@@ -309,8 +310,8 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
     }
     upload(b->d_bases, bases, s, b->st_bases);
     // SIMT arithmetic type of the merged stages (TF32 factors are the FP32 copy)
-    const int md = (mode == H2_TF32) ? H2_FP32 : mode;
-    bool tc = (mode == H2_TF32 || mode == H2_BF16) && nrhs >= kBatchTcMinNrhs;
+    const int md = (mode == H2_TF32 || mode == H2_TF32X3) ? H2_FP32 : mode;
+    bool tc = (mode == H2_TF32 || mode == H2_TF32X3 || mode == H2_BF16) && nrhs >= kBatchTcMinNrhs;
     for (auto* h : b->hs) tc = tc && tc_supported(h) && ((mode == H2_BF16) ? h->tc.W16.p : h->tc.W32.p);
     uint64_t io = 0;
     if (tc) {
@@ -369,7 +370,7 @@ void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void*
 }
 
 int batch_tuned(h2_batch_s* b, int64_t nrhs, int mode) {
-    const int md = (mode == H2_TF32) ? H2_FP32 : mode;
+    const int md = (mode == H2_TF32 || mode == H2_TF32X3) ? H2_FP32 : mode;
     for (const auto& kv : b->tuned)
         if (kv.first.nrhs == nrhs && (kv.first.mode == mode || kv.first.mode == md)) return kv.second.rt;
     return 0;

@@ -240,7 +240,7 @@ int h2_batch_matvec(h2_batch_t b, const void* const* X, const int64_t* ldx, void
         require(nrhs >= 0 && nrhs <= 2000000, "h2_batch_matvec: nrhs out of range");
         if (nrhs == 0) return H2_OK;
         require(X && Y && ldx && ldy, "h2_batch_matvec: NULL arrays");
-        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_batch_matvec: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_batch_matvec: unknown mode");
         h2::batch_matvec(b, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });
@@ -550,7 +550,7 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
         if (nrhs == 0) return H2_OK;
         require(X != nullptr && Y != nullptr, "h2_matvec: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec: leading dimension smaller than n");
-        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_matvec: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec: unknown mode");
         h2::run_matvec(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });
@@ -564,7 +564,7 @@ int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_
         if (nrhs == 0) return H2_OK;
         require(X != nullptr && Y != nullptr, "h2_matvec_noalloc: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec_noalloc: leading dimension smaller than n");
-        require(mode >= H2_FP64 && mode <= H2_BF16, "h2_matvec_noalloc: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec_noalloc: unknown mode");
         h2::run_matvec_noalloc(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });

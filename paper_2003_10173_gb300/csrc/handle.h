@@ -104,8 +104,8 @@ struct TcTileSrc {     // how a B tile is made from the FP64 factors
 struct TcStage {
     std::vector<TcOut> outs;
     std::vector<TcItem> items;     // b_off holds the tile index until packing
-    DevBuf<TcOut> d_outs;
-    DevBuf<TcItem> d_items16, d_items32;
+    DevBuf<TcOut> d_outs, d_outs32x3;
+    DevBuf<TcItem> d_items16, d_items32, d_items32x3;   // split TF32: three items per product
 };
 struct TcPlan {
     int LP = 0;              // padded leaf rows

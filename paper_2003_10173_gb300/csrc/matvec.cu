@@ -515,7 +515,7 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
     if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: nrhs above 2,000,000");
     const size_t elt = (mode == H2_FP64) ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)h->plan.ws_rows * (size_t)nrhs * elt;
-    if (mode == H2_TF32) mode = H2_FP32;   // the tensor-core path needs a staged operand copy: not here
+    if (mode == H2_TF32 || mode == H2_TF32X3) mode = H2_FP32;   // the tensor-core path needs a staged operand copy: not here
     if (need > kNoAllocScratchBytes)
         fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: needs " + std::to_string(need) + " bytes of scratch (" +
                                      std::to_string(h->plan.ws_rows) + " coefficient rows x " + std::to_string(nrhs) +
@@ -857,10 +857,11 @@ std::function<void(cudaStream_t)> matvec_launches(h2_handle_s* h, const void* X,
                                                         ldy, (int)nrhs, s);
             };
         case H2_FP32:
-        case H2_TF32: {
+        case H2_TF32:
+        case H2_TF32X3: {
             if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: FP32 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
-            if (mode == H2_TF32 && nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W32.p) {
+            if (mode != H2_FP32 && nrhs >= kTcMinNrhs && tc_supported(h) && h->tc.W32.p) {
                 tc_reserve(h, mode, (int)nrhs);
                 return [=](cudaStream_t s) {
                     run_tc<float, float>(h, mode, h->fac32.p, h->ws.f32.p, (const float*)X, ldx, (float*)Y, ldy,

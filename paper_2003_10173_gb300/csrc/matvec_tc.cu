@@ -256,11 +256,20 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     }
 }
 
+// TF32 rounding (nearest, ties away) as an FP32 bit pattern, and the rounded low part of the rest:
+// v = hi + lo + O(2^-22 |v|) (the three-pass "split TF32" products).
+__device__ __forceinline__ uint32_t tf32_rna(float f) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
+    return u;
+}
+
 // B tiles: tile b is op(M) (valid rows x cols, zero padded to n x k) laid out as an n x k
-// K-major operand at byte offset dst[b] of the pool.
+// K-major operand at byte offset dst[b] of the pool.  With lo_off > 0 (TF32 only) the low part
+// of every entry goes to the same position lo_off bytes further on.
 template <int EB>
 __global__ void tc_pack_tiles_kernel(const double* __restrict__ fac, const TcTileSrc* __restrict__ src,
-                                     unsigned char* __restrict__ W) {
+                                     unsigned char* __restrict__ W, int64_t lo_off) {
     const TcTileSrc d = src[blockIdx.x];
     const double* M = fac + d.m_off;
     unsigned char* out = W + d.dst;
@@ -272,10 +281,10 @@ __global__ void tc_pack_tiles_kernel(const double* __restrict__ fac, const TcTil
         if constexpr (EB == 2) {
             *reinterpret_cast<__nv_bfloat16*>(out + o) = __double2bfloat16(v);
         } else {
-            float f = (float)v;
-            uint32_t u;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(f));
-            *reinterpret_cast<uint32_t*>(out + o) = u;
+            const float f = (float)v;
+            const uint32_t hi = tf32_rna(f);
+            *reinterpret_cast<uint32_t*>(out + o) = hi;
+            if (lo_off > 0) *reinterpret_cast<uint32_t*>(out + lo_off + o) = tf32_rna(f - __uint_as_float(hi));
         }
     }
 }
@@ -283,10 +292,10 @@ __global__ void tc_pack_tiles_kernel(const double* __restrict__ fac, const TcTil
 __device__ __forceinline__ void store_opnd_bf16(unsigned char* dst, float v) {
     *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
 }
-__device__ __forceinline__ void store_opnd_tf32(unsigned char* dst, float v) {
-    uint32_t u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-    *reinterpret_cast<uint32_t*>(dst) = u;
+__device__ __forceinline__ void store_opnd_tf32(unsigned char* dst, float v, int64_t lo_off) {
+    const uint32_t hi = tf32_rna(v);
+    *reinterpret_cast<uint32_t*>(dst) = hi;
+    if (lo_off > 0) *reinterpret_cast<uint32_t*>(dst + lo_off) = tf32_rna(v - __uint_as_float(hi));
 }
 
 // The operand buffer is tiled: operand block b (K rows: the points of a leaf, or the padded
@@ -298,7 +307,7 @@ __device__ __forceinline__ void store_opnd_tf32(unsigned char* dst, float v) {
 template <class TX, int EB>
 __global__ void tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm,
                                  const int64_t* __restrict__ leaf_start, const int* __restrict__ leaf_size, int LP,
-                                 int nleaf, int nrhs, int nrt, unsigned char* __restrict__ opnd) {
+                                 int nleaf, int nrhs, int nrt, unsigned char* __restrict__ opnd, int64_t lo_off) {
     const int64_t per_leaf = (int64_t)nrt * TC_M * LP;
     const int64_t total = per_leaf * nleaf;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -315,7 +324,7 @@ __global__ void tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx, const in
         const int rt = r / TC_M, rr = r % TC_M;
         unsigned char* dst = opnd + ((int64_t)t * LP * TC_M * nrt + (int64_t)rt * TC_M * LP) * EB + kmaj_off<EB>(rr, i, LP);
         if constexpr (EB == 2) store_opnd_bf16(dst, v);
-        else store_opnd_tf32(dst, v);
+        else store_opnd_tf32(dst, v, lo_off);
     }
 }
 
@@ -323,7 +332,7 @@ __global__ void tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx, const in
 template <int EB>
 __global__ void tc_pack_coef_kernel(const int4* __restrict__ boxes, const float* __restrict__ ws, int64_t ws_ld,
                                     const int64_t* __restrict__ src_row, int nrhs, int nrt,
-                                    unsigned char* __restrict__ opnd) {
+                                    unsigned char* __restrict__ opnd, int64_t lo_off) {
     const int b = blockIdx.x;
     const int4 d = boxes[b];   // x: block base row, y: k, z: kpad
     const int64_t s0 = src_row[b];
@@ -335,14 +344,14 @@ __global__ void tc_pack_coef_kernel(const int4* __restrict__ boxes, const float*
         const int rt = r / TC_M, rr = r % TC_M;
         unsigned char* dst = opnd + ((int64_t)d.x * nrt * TC_M + (int64_t)rt * TC_M * kp) * EB + kmaj_off<EB>(rr, i, kp);
         if constexpr (EB == 2) store_opnd_bf16(dst, v);
-        else store_opnd_tf32(dst, v);
+        else store_opnd_tf32(dst, v, lo_off);
     }
 }
 
 template <int EB>
-void launch_products(const TcStage& st, const TcItem* d_items, const unsigned char* W, const unsigned char* opnd,
-                     const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld, int nrhs, int* err,
-                     cudaStream_t s) {
+void launch_products(const TcStage& st, const TcOut* d_outs, const TcItem* d_items, const unsigned char* W,
+                     const unsigned char* opnd, const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld,
+                     int nrhs, int* err, cudaStream_t s) {
     if (st.outs.empty()) return;
     const size_t smem = std::max((size_t)TcCfg<EB>::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
     static std::once_flag attr;
@@ -350,7 +359,7 @@ void launch_products(const TcStage& st, const TcItem* d_items, const unsigned ch
         H2_CUDA(cudaFuncSetAttribute(tc_products_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     });
     dim3 grid((unsigned)((nrhs + TC_M - 1) / TC_M), (unsigned)st.outs.size());
-    tc_products_kernel<EB><<<grid, TC_THREADS, smem, s>>>(st.d_outs.p, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs,
+    tc_products_kernel<EB><<<grid, TC_THREADS, smem, s>>>(d_outs, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs,
                                                           err);
     after_launch("tc_products");
 }
@@ -521,9 +530,11 @@ void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
         for (auto& t : tb) t.dst *= eb;
         upload(d_tiles, tb, s, stg);
         DevBuf<unsigned char>& Wp = (eb == 2) ? P.W16 : P.W32;
-        Wp.reserve((size_t)P.w_elems * eb);
-        if (eb == 2) tc_pack_tiles_kernel<2><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p);
-        else tc_pack_tiles_kernel<4><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p);
+        // the TF32 pool also holds the low parts of the split-TF32 products, after the high parts
+        const int64_t lo_off = (eb == 4) ? P.w_elems * 4 : 0;
+        Wp.reserve((size_t)P.w_elems * eb * (eb == 4 ? 2 : 1));
+        if (eb == 2) tc_pack_tiles_kernel<2><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p, 0);
+        else tc_pack_tiles_kernel<4><<<(unsigned)tb.size(), 256, 0, s>>>(h->fac64.p, d_tiles.p, Wp.p, lo_off);
         after_launch("tc_pack_tiles");
         H2_CUDA(cudaStreamSynchronize(s));
         // per-precision item lists (byte offsets of B tiles)
@@ -532,18 +543,39 @@ void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
             for (auto& x : it) x.b_off = tiles[(size_t)x.b_off].dst * eb;
             upload(eb == 2 ? st->d_items16 : st->d_items32, it, s, stg);
             H2_CUDA(cudaStreamSynchronize(s));
+            if (eb == 4) {
+                // split TF32: hi x hi, hi(A) x lo(B), lo(A) x hi(B), accumulated in one TMEM tile;
+                // low operand rows follow the high ones at op_rows
+                std::vector<TcItem> x3;
+                x3.reserve(it.size() * 3);
+                for (const auto& x : it) {
+                    x3.push_back(x);
+                    x3.push_back(TcItem{x.a_row, x.k, x.b_off + lo_off});
+                    x3.push_back(TcItem{x.a_row + P.op_rows, x.k, x.b_off});
+                }
+                std::vector<TcOut> o3 = st->outs;
+                for (auto& o : o3) {
+                    o.beg *= 3;
+                    o.end *= 3;
+                }
+                upload(st->d_items32x3, x3, s, stg);
+                H2_CUDA(cudaStreamSynchronize(s));
+                upload(st->d_outs32x3, o3, s, stg);
+                H2_CUDA(cudaStreamSynchronize(s));
+            }
         }
     }
 }
 
 // Tensor-core matvec for BF16 (X bf16) or TF32 (X fp32): leaf upsweep, couplings and near field
 // + leaf expansion on tcgen05; the transfer sweeps on the SIMT stage kernels (run_tree_sweeps).
-// Operand buffer of a tensor-core matvec with nrhs right-hand sides in the precision of mode.
+// Operand buffer of a tensor-core matvec with nrhs right-hand sides in the precision of mode
+// (split TF32 keeps a low part of every operand row after the high parts).
 void tc_reserve(h2_handle_s* h, int mode, int nrhs) {
     TcPlan& P = h->tc;
     const int EB = (mode == H2_BF16) ? 2 : 4;
     const int nrt = (nrhs + TC_M - 1) / TC_M;
-    P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
+    P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB) * (mode == H2_TF32X3 ? 2 : 1));
 }
 
 // One phase of the tensor-core matvec: 0 packs X and computes the leaf coefficients xh, 1 packs
@@ -553,23 +585,32 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
               float* ws, int64_t ws_ld, cudaStream_t s) {
     TcPlan& P = h->tc;
     const int EB = (mode == H2_BF16) ? 2 : 4;
+    const bool split = mode == H2_TF32X3;
     const int nrt = (nrhs + TC_M - 1) / TC_M;
-    P.opnd.reserve((size_t)(P.op_rows * nrt * TC_M * EB));
+    tc_reserve(h, mode, nrhs);
     const unsigned char* W = (mode == H2_BF16) ? P.W16.p : P.W32.p;
     if (!W) fail(H2_ERR_INVALID_ARG, "h2_matvec: tensor-core tiles of this precision were not kept");
+    // byte distance from an operand's high part to its low part
+    const int64_t lo_off = split ? P.op_rows * nrt * TC_M * 4 : 0;
     auto run = [&](TcStage& st) {
         if (st.outs.empty()) return;
         if (EB == 2)
-            launch_products<2>(st, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs, P.d_err.p, s);
+            launch_products<2>(st, st.d_outs.p, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs,
+                               P.d_err.p, s);
+        else if (split)
+            launch_products<4>(st, st.d_outs32x3.p, st.d_items32x3.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld,
+                               nrhs, P.d_err.p, s);
         else
-            launch_products<4>(st, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs, P.d_err.p, s);
+            launch_products<4>(st, st.d_outs.p, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs,
+                               P.d_err.p, s);
     };
     auto pack_coef = [&](const std::vector<int4>& bx, const DevBuf<int4>& dbx, const DevBuf<int64_t>& dsrc) {
         if (bx.empty()) return;
         if (EB == 2)
-            tc_pack_coef_kernel<2><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p);
+            tc_pack_coef_kernel<2><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p, 0);
         else
-            tc_pack_coef_kernel<4><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p);
+            tc_pack_coef_kernel<4><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p,
+                                                                       lo_off);
         after_launch("tc_pack_coef");
     };
     P.cur_eb = EB;
@@ -579,10 +620,10 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
         if (EB == 2)
             tc_pack_x_kernel<__nv_bfloat16, 2><<<g, 256, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p,
                                                                   P.d_leaf_start.p, P.d_leaf_size.p, P.LP, P.nleaf,
-                                                                  nrhs, nrt, P.opnd.p);
+                                                                  nrhs, nrt, P.opnd.p, 0);
         else
             tc_pack_x_kernel<float, 4><<<g, 256, 0, s>>>((const float*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
-                                                         P.d_leaf_size.p, P.LP, P.nleaf, nrhs, nrt, P.opnd.p);
+                                                         P.d_leaf_size.p, P.LP, P.nleaf, nrhs, nrt, P.opnd.p, lo_off);
         after_launch("tc_pack_x");
         run(P.leaf_up);
     } else if (phase == 1) {

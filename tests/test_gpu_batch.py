@@ -76,13 +76,13 @@ def test_one_shot_batched_matvec_equals_batch(setup):
     B.close()
 
 
-@pytest.mark.parametrize("mode,nrhs", [(2, 64), (2, 130), (3, 64), (3, 130)])
+@pytest.mark.parametrize("mode,nrhs", [(2, 64), (2, 130), (3, 64), (3, 130), (4, 64)])
 def test_batch_tensor_core_matvec_equals_individual(setup, mode, nrhs):
     """TF32 / BF16 with nrhs >= 64: per-handle tensor-core phases between merged SIMT sweeps; the
     result equals each handle's own tensor-core matvec (same products, same summation order),
     also when the graph is replayed and when the buffers change (recaptured)."""
     h2, probs, ops, trees, batched, single = setup
-    xdt = torch.float32 if mode == h2.H2_TF32 else torch.bfloat16
+    xdt = torch.bfloat16 if mode == h2.H2_BF16 else torch.float32
     B = h2.Batch(batched)
     for trial in range(2):
         Xs = [torch.from_numpy(np.ascontiguousarray(W.rhs(p.N, nrhs, 90 + i + 7 * trial).T)).to("cuda", xdt)

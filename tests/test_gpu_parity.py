@@ -136,7 +136,9 @@ def test_matvec_fp64_matches_oracle(h2, kind, nrhs):
 @pytest.mark.parametrize("nrhs", [64, 130])
 def test_matvec_tensor_cores_match_oracle(h2, kind, nrhs):
     """nrhs >= 64 in BF16 / TF32 runs the near field on tcgen05 (FP32 accumulation in tensor memory).
-    Bounds against the FP64 oracle: BF16 2e-2 (8-bit mantissa), TF32 2e-3 (10-bit mantissa)."""
+    Bounds against the FP64 oracle: BF16 2e-2 (8-bit mantissa), TF32 2e-3 (10-bit mantissa), split
+    TF32 1e-5 (two TF32 parts of each operand, three products: 2^-22 per product, then FP32
+    accumulation over up to ~1,500 terms, sqrt(K) 2^-24 ~ 2e-6: the FP32 storage bound)."""
     if kind == "heat64":
         mask, op = _heat_problem(64, 256, 1002)
         h = O.build(op, W.grid_coords(64), 64, ADM_STRONG, 0.7, 1e-6, 32, 32, 16, 256, True, 7)[0]
@@ -156,6 +158,12 @@ def test_matvec_tensor_cores_match_oracle(h2, kind, nrhs):
     assert G.device_status() == h2.H2_OK
     assert rel(host(Yb), want) < 2e-2
     assert rel(host(Yt), want) < 2e-3
+    # split TF32 (hi*hi + hi*lo + lo*hi): FP32-grade, about 22 significant bits per product
+    Y3 = torch.full((nrhs, n * n), float("nan"), dtype=torch.float32, device="cuda")
+    G.matvec(Xd.float(), Y3, nrhs, h2.H2_TF32X3)
+    torch.cuda.synchronize()
+    assert G.device_status() == h2.H2_OK
+    assert rel(host(Y3), want) < 1e-5
     # same inputs through the SIMT path (nrhs <= 4 columns at a time) agree column by column
     Y4 = torch.empty((4, n * n), dtype=torch.float32, device="cuda")
     G.matvec(Xd[:4].float(), Y4, 4, h2.H2_FP32)
