@@ -282,6 +282,23 @@ def batching_section(h2, torch, stream) -> dict:
     return out
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """The largest value of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank: float, seconds_per_rank: float, dist) -> float:
+    """Whole-job throughput of independent replicas: the units of all ranks over the slowest rank's time."""
+    world = dist.get_world_size() if dist is not None else 1
+    return units_per_rank * world / max_over_ranks(seconds_per_rank, dist)
+
+
 def rel_err_2norm(h2, torch, gop, G, N: int, norm_est: float, stream) -> float:
     """||H - H~||_2 / ||H||_2 by power iteration through the GPU operator and the FP64 matvec."""
     v = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
@@ -584,11 +601,7 @@ def main():
     gemm_ms, gemm_flops, gemm_n = h2.gemm_profile_read()
     h2.gemm_profile(False)
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist)
 
     st = results[-1][0].stats()
     build_ms = [bev[0].elapsed_time(bev[1]) for _, bev, _ in results]
@@ -596,7 +609,7 @@ def main():
     by = {nr: matvec_bytes(st, N, nr) for nr in nrhs_list}
     tot_bytes = sum(by[nr] * len(mv_ms[nr]) for nr in nrhs_list)
     tot_mv_s = sum(sum(mv_ms[nr]) for nr in nrhs_list) / 1e3
-    value = tot_bytes / tot_mv_s / 1e9 * world
+    value = aggregate_throughput(tot_bytes, tot_mv_s, dist) / 1e9
     hbm, hbm_src, fp64 = peaks()
 
     # roofline of the dominant matvec kernel (leaf expansion + near field) at nrhs = 1, FP64
@@ -664,7 +677,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e_bytes = reps * sum(by[nr] for nr in nrhs_list)
-    e2e = {"value": e2e_bytes / e2e_s / 1e9 * world, "unit": "GB/s",
+    e2e = {"value": aggregate_throughput(e2e_bytes, e2e_s, dist) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list),
            "d2h_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list)}
 
