@@ -213,31 +213,34 @@ int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tr
             if (first_status == H2_OK) { first_status = H2_ERR_CUDA; first_err = "stream creation failed"; }
             return;
         }
-        while (true) {
-            int i;
-            {
-                std::lock_guard<std::mutex> lock(mu);
-                if (next >= count || first_status != H2_OK) break;
-                i = next++;
-            }
-            auto* h = new h2_handle_s();
-            try {
-                h2_build_opts oi = o;
-                oi.stream = (h2_stream_t)s;
-                if (o.q_level) oi.q_level = o.q_level + (int64_t)i * o.q_level_stride;
-                const int st = build_handle(ops[i], ctxs ? ctxs[i] : nullptr, trees[i], tol, oi, h);
-                finish_handle(h, oi, s);
-                std::lock_guard<std::mutex> lock(mu);
-                outs[i] = h;
-                worst = std::max(worst, st);
-            } catch (const Error& e) {
-                delete h;
-                std::lock_guard<std::mutex> lock(mu);
-                if (first_status == H2_OK) { first_status = e.status; first_err = e.what(); }
-            } catch (...) {
-                delete h;
-                std::lock_guard<std::mutex> lock(mu);
-                if (first_status == H2_OK) { first_status = H2_ERR_CUDA; first_err = "unknown failure"; }
+        {
+            AllocScope scope(s);   // workspace blocks are reused across this worker's Hessians
+            while (true) {
+                int i;
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    if (next >= count || first_status != H2_OK) break;
+                    i = next++;
+                }
+                auto* h = new h2_handle_s();
+                try {
+                    h2_build_opts oi = o;
+                    oi.stream = (h2_stream_t)s;
+                    if (o.q_level) oi.q_level = o.q_level + (int64_t)i * o.q_level_stride;
+                    const int st = build_handle(ops[i], ctxs ? ctxs[i] : nullptr, trees[i], tol, oi, h);
+                    finish_handle(h, oi, s);
+                    std::lock_guard<std::mutex> lock(mu);
+                    outs[i] = h;
+                    worst = std::max(worst, st);
+                } catch (const Error& e) {
+                    delete h;
+                    std::lock_guard<std::mutex> lock(mu);
+                    if (first_status == H2_OK) { first_status = e.status; first_err = e.what(); }
+                } catch (...) {
+                    delete h;
+                    std::lock_guard<std::mutex> lock(mu);
+                    if (first_status == H2_OK) { first_status = H2_ERR_CUDA; first_err = "unknown failure"; }
+                }
             }
         }
         cudaStreamSynchronize(s);

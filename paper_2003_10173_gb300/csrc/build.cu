@@ -42,16 +42,14 @@ double now_s() {
 struct Pinned {
     void* p = nullptr;
     size_t cap = 0;
-    ~Pinned() {
-        if (p) cudaFreeHost(p);
-    }
+    ~Pinned() { host_free(p); }
     template <class T>
     T* get(size_t n) {
         if (n * sizeof(T) > cap) {
-            if (p) cudaFreeHost(p);
+            host_free(p);
             p = nullptr;
             cap = 0;
-            H2_CUDA(cudaMallocHost(&p, n * sizeof(T) + 64));
+            p = host_alloc_bytes(n * sizeof(T) + 64);
             cap = n * sizeof(T) + 64;
         }
         return static_cast<T*>(p);

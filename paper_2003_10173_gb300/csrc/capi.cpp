@@ -200,6 +200,7 @@ int h2_build(h2_op_fn op, void* ctx, h2_tree_t tree, double tol, const h2_build_
         auto* h = new h2_handle_s();
         try {
             const cudaStream_t s = (cudaStream_t)o.stream;
+            h2::AllocScope scope(s);
             const int st = h2::build_handle(op, ctx, tree, tol, o, h);
             h2::finish_handle(h, o, s);
             *out = h;

@@ -44,7 +44,37 @@ extern std::atomic<int64_t> g_launches;
 void after_launch(const char* name);
 
 // ---- device memory ---------------------------------------------------------
-// Owning device buffer (cudaMalloc / cudaFree).  Allocation failure -> H2_ERR_OOM.
+// Device blocks come from dev_alloc_bytes and go back through dev_free; pinned host
+// blocks from host_alloc_bytes / host_free.  Outside an AllocScope these are plain
+// cudaMalloc / cudaFree and cudaMallocHost / cudaFreeHost (each free waits for the
+// whole device).  Allocation failure -> H2_ERR_OOM.
+void* dev_alloc_bytes(size_t bytes);
+void dev_free(void* p);
+void* host_alloc_bytes(size_t bytes);
+void host_free(void* p);
+
+// While an AllocScope is alive on a thread, the blocks that this thread allocated inside
+// the scope and then frees are kept on per-thread free lists and handed out again to the
+// thread's later allocations (best fit, sizes rounded up by at most a quarter) instead of
+// being returned to the driver: no device-wide wait per free, which lets several threads
+// build on their own streams without serialising one another.  Requirement: all device
+// work that the thread issues on scope blocks runs on the scope's stream (then a reused
+// device block is stream-ordered after its last use), and a pinned block is freed only
+// after the copies from or to it have completed.  The scope's end synchronises the stream
+// and returns the kept blocks.  A scope opened while another is alive on the thread does
+// nothing.
+class AllocScope {
+  public:
+    explicit AllocScope(cudaStream_t s);
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+
+  private:
+    bool owner_ = false;
+};
+
+// Owning device buffer on dev_alloc_bytes / dev_free.
 template <class T>
 struct DevBuf {
     T* p = nullptr;
@@ -61,7 +91,7 @@ struct DevBuf {
     ~DevBuf() { release(); }
     void alloc(size_t count);
     void release() {
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
         p = nullptr;
         n = 0;
     }
@@ -70,8 +100,6 @@ struct DevBuf {
         if (count > n) { release(); alloc(count); }
     }
 };
-
-void* dev_alloc_bytes(size_t bytes);
 
 template <class T>
 void DevBuf<T>::alloc(size_t count) {

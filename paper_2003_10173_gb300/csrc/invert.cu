@@ -139,6 +139,7 @@ void invert(h2_handle_s* A, const h2_invert_opts& io, const h2_build_opts& bo, h
             h2_invert_stats* st) {
     const double t0 = now_s();
     cudaStream_t s = (cudaStream_t)bo.stream;
+    AllocScope scope(s);   // workspace and retired iterates are reused by the next construction
     const int64_t N = A->N;
     Sampler S;
     S.A = A;
