@@ -120,6 +120,94 @@ __global__ void __launch_bounds__(NT) mv_stage_kernel(const MvOut* __restrict__ 
                                              accumulate);
 }
 
+// Transfer stages of the tree sweeps (upsweep x_p = sum_c E_c^T x_c, downsweep y_c += E_c y_p):
+// inputs and outputs are coefficient rows of the workspace, blocks at most KB x KB.  One CTA per
+// (output box, TR_RC right-hand sides), one thread per right-hand side: the thread keeps the
+// box's output column in registers while the item matrices are broadcast from shared memory;
+// inputs and outputs pass through a padded shared tile so that global accesses run along the
+// coefficient rows.
+constexpr int TR_RC = 128;
+
+template <class TS, class TA, int KB>
+__global__ void __launch_bounds__(TR_RC) mv_transfer_kernel(const MvOut* __restrict__ outs,
+                                                            const MvItem* __restrict__ items,
+                                                            const TS* __restrict__ fac, TA* __restrict__ ws,
+                                                            int64_t ws_ld, int nrhs, int accumulate) {
+    constexpr int XS = KB + 1;   // odd stride: a thread's staged column is conflict-free
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* Ms = reinterpret_cast<TA*>(smem_raw);   // item matrix, [col j][row i], rows zero padded to 4
+    TA* XT = Ms + KB * KB;                        // [TR_RC][XS]: input columns, then output columns
+    const MvOut o = outs[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.y * TR_RC;
+    const int nr = min(TR_RC, nrhs - r0);
+    const int rows = o.rows;
+    const int rows4 = (rows + 3) & ~3;
+    TA acc[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = (TA)0;
+    for (int it = o.beg; it < o.end; ++it) {
+        const MvItem m = items[it];
+        const int cols = m.cols;
+        const bool tr = (m.trans & 1) != 0;
+        const TS* M = fac + m.m_off;
+        for (int e = tid; e < rows4 * cols; e += TR_RC) {
+            int i, j;
+            if (!tr) { i = e % rows4; j = e / rows4; }   // contiguous along i
+            else     { j = e % cols; i = e / cols; }     // contiguous along j
+            TA v = (TA)0;
+            if (i < rows) v = cvt<TA>(tr ? M[j + (int64_t)i * m.ldm] : M[i + (int64_t)j * m.ldm]);
+            Ms[j * KB + i] = v;
+        }
+        for (int e = tid; e < cols * nr; e += TR_RC) {
+            const int j = e % cols, r = e / cols;
+            XT[r * XS + j] = ws[m.in_off + j + (int64_t)(r0 + r) * ws_ld];
+        }
+        __syncthreads();
+        if (tid < nr) {
+            const TA* x = XT + tid * XS;
+            for (int j = 0; j < cols; ++j) {
+                const TA xv = x[j];
+                const TA* mj = Ms + j * KB;
+#pragma unroll
+                for (int i4 = 0; i4 < KB / 4; ++i4) {
+                    if (4 * i4 < rows4) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[4 * i4 + q] = fma(mj[4 * i4 + q], xv, acc[4 * i4 + q]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < nr) {
+#pragma unroll
+        for (int i = 0; i < KB; ++i)
+            if (i < rows) XT[tid * XS + i] = acc[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * nr; e += TR_RC) {
+        const int i = e % rows, r = e / rows;
+        TA* y = ws + o.out_off + i + (int64_t)(r0 + r) * ws_ld;
+        const TA v = XT[r * XS + i];
+        *y = accumulate ? (TA)(*y + v) : v;
+    }
+}
+
+template <class TS, class TA, int KB>
+void launch_transfer(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, int nrhs, cudaStream_t s) {
+    const size_t smem = (size_t)(KB * KB + TR_RC * (KB + 1)) * sizeof(TA);
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
+        H2_CUDA(cudaFuncSetAttribute(mv_transfer_kernel<TS, TA, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    });
+    dim3 grid((unsigned)st.outs.size(), (unsigned)((nrhs + TR_RC - 1) / TR_RC));
+    mv_transfer_kernel<TS, TA, KB><<<grid, TR_RC, smem, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ws_ld, nrhs,
+                                                             st.accumulate);
+    after_launch("mv_transfer");
+}
+
 // Final stage: leaf expansion plus the dense near field, written to Y.
 template <class TS, class TX, class TY, class TA>
 __global__ void __launch_bounds__(NT) mv_leaf_near_kernel(const MvOut* __restrict__ outs,
@@ -369,6 +457,13 @@ template <class TS, class TX, class TY, class TA>
 void launch_stage(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, const int32_t* perm,
                   const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs, cudaStream_t s) {
     if (st.outs.empty()) return;
+    // tree sweeps with at least half a tile of right-hand sides: one thread per right-hand side
+    if ((st.kind == H2_STAGE_UP || st.kind == H2_STAGE_DOWN) && !st.out_to_y && !st.in_from_x &&
+        nrhs >= TR_RC / 2 && (nrhs + TR_RC - 1) / TR_RC <= 65535) {
+        const int kb = std::max(st.max_rows, st.max_cols);
+        if (kb <= 32) { launch_transfer<TS, TA, 32>(st, fac, ws, ws_ld, nrhs, s); return; }
+        if (kb <= 64) { launch_transfer<TS, TA, 64>(st, fac, ws, ws_ld, nrhs, s); return; }
+    }
     const size_t smem = (size_t)(RMAX * (RMAX + 1) + RMAX * RT) * sizeof(TA);
     static std::once_flag attr;
     std::call_once(attr, [&] {
@@ -790,8 +885,14 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
     }
     Stager stg;
     auto up_stage = [&](MvStage& st) {
-        for (auto& it : st.items)
+        st.max_rows = st.max_cols = 0;
+        for (auto& it : st.items) {
             if (it.rows > RMAX || it.cols > RMAX) fail(H2_ERR_INVALID_ARG, "matvec: block larger than 96");
+            if (it.trans & 2) st.in_from_x |= 1;
+            st.max_rows = std::max(st.max_rows, it.rows);
+            st.max_cols = std::max(st.max_cols, it.cols);
+        }
+        for (auto& o : st.outs) st.max_rows = std::max(st.max_rows, o.rows);
         upload(st.d_outs, st.outs, s, stg);
         upload(st.d_items, st.items, s, stg);
         H2_CUDA(cudaStreamSynchronize(s));

@@ -303,48 +303,102 @@ __device__ __forceinline__ void store_opnd_tf32(unsigned char* dst, float v, int
 // 128 x K chunk in the canonical K-major layout, at byte base_b * nrt + rt * 128 * K * EB, where
 // base_b is the block's offset in units of 128-column tiles.  A tile load is one bulk copy.
 //
-// X (caller order) -> leaf blocks (zero padded rows and right-hand sides)
-template <class TX, int EB>
-__global__ void tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx, const int32_t* __restrict__ perm,
-                                 const int64_t* __restrict__ leaf_start, const int* __restrict__ leaf_size, int LP,
-                                 int nleaf, int nrhs, int nrt, unsigned char* __restrict__ opnd, int64_t lo_off) {
-    const int64_t per_leaf = (int64_t)nrt * TC_M * LP;
-    const int64_t total = per_leaf * nleaf;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(e / per_leaf);
-        const int64_t w = e % per_leaf;
-        const int i = (int)(w % LP);
-        const int r = (int)(w / LP);          // global right-hand side
-        float v = 0.f;
-        if (i < leaf_size[t] && r < nrhs) {
-            const TX x = X[perm[leaf_start[t] + i] + (int64_t)r * ldx];
-            if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(x);
-            else v = (float)x;
+// Operand packing: one CTA per (operand block, right-hand-side tile) stages a 128 x PK_KS slice
+// of the block in shared memory (coalesced reads along the block's rows), then writes it out
+// as whole 16-byte core-matrix rows, consecutive threads to consecutive addresses.
+constexpr int PK_KS = 64;        // K columns staged per slice
+constexpr int PK_PAD = 4;        // floats of padding per staged row: conflict-free 16-byte reads
+constexpr int PK_THREADS = 256;
+
+// Write columns [ks0, ks0 + w) of the staged 128 x K chunk to dst (the chunk's base, K-major).
+template <int EB>
+__device__ __forceinline__ void pack_store_slice(const float (*tile)[PK_KS + PK_PAD], int K, int ks0, int w,
+                                                 unsigned char* __restrict__ dst, int64_t lo_off) {
+    constexpr int EPC = 16 / EB;   // elements per 16-byte core row
+    const int nkc = w / EPC;
+    for (int u = threadIdx.x; u < TC_M * nkc; u += PK_THREADS) {
+        const int g = u / (8 * nkc), rem = u - g * 8 * nkc;
+        const int kc = rem >> 3, rw = rem & 7;
+        const float* src = &tile[g * 8 + rw][kc * EPC];
+        unsigned char* o = dst + ((int64_t)(g * (K / EPC) + ks0 / EPC + kc) * 8 + rw) * 16;
+        if constexpr (EB == 2) {
+            const float4 a = *reinterpret_cast<const float4*>(src);
+            const float4 b = *reinterpret_cast<const float4*>(src + 4);
+            __nv_bfloat162 q[4] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                                   __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
+            *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(q);
+        } else {
+            const float4 a = *reinterpret_cast<const float4*>(src);
+            const uint4 hi = make_uint4(tf32_rna(a.x), tf32_rna(a.y), tf32_rna(a.z), tf32_rna(a.w));
+            *reinterpret_cast<uint4*>(o) = hi;
+            if (lo_off > 0)
+                *reinterpret_cast<uint4*>(o + lo_off) =
+                    make_uint4(tf32_rna(a.x - __uint_as_float(hi.x)), tf32_rna(a.y - __uint_as_float(hi.y)),
+                               tf32_rna(a.z - __uint_as_float(hi.z)), tf32_rna(a.w - __uint_as_float(hi.w)));
         }
-        const int rt = r / TC_M, rr = r % TC_M;
-        unsigned char* dst = opnd + ((int64_t)t * LP * TC_M * nrt + (int64_t)rt * TC_M * LP) * EB + kmaj_off<EB>(rr, i, LP);
-        if constexpr (EB == 2) store_opnd_bf16(dst, v);
-        else store_opnd_tf32(dst, v, lo_off);
     }
 }
 
-// coefficient rows of the workspace -> box blocks: box list (block base row, k, kpad)
+// X (caller order) -> leaf blocks (zero padded rows and right-hand sides); grid (leaves, tiles)
+template <class TX, int EB>
+__global__ void __launch_bounds__(PK_THREADS) tc_pack_x_kernel(const TX* __restrict__ X, int64_t ldx,
+                                                               const int32_t* __restrict__ perm,
+                                                               const int64_t* __restrict__ leaf_start,
+                                                               const int* __restrict__ leaf_size, int LP, int nrhs,
+                                                               unsigned char* __restrict__ opnd, int64_t lo_off) {
+    __shared__ __align__(16) float tile[TC_M][PK_KS + PK_PAD];
+    const int t = blockIdx.x, rt = blockIdx.y, nrt = gridDim.y;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int m = leaf_size[t];
+    const int64_t s0 = leaf_start[t];
+    const int r0 = rt * TC_M;
+    unsigned char* dst = opnd + ((int64_t)t * LP * TC_M * nrt + (int64_t)rt * TC_M * LP) * EB;
+    for (int ks0 = 0; ks0 < LP; ks0 += PK_KS) {
+        const int w = min(PK_KS, LP - ks0);
+        for (int i = tx; i < w; i += 32) {
+            const int p = ks0 + i;
+            const int64_t row = p < m ? (int64_t)perm[s0 + p] : -1;
+            for (int rr = ty; rr < TC_M; rr += PK_THREADS / 32) {
+                float v = 0.f;
+                if (row >= 0 && r0 + rr < nrhs) {
+                    const TX x = X[row + (int64_t)(r0 + rr) * ldx];
+                    if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(x);
+                    else v = (float)x;
+                }
+                tile[rr][i] = v;
+            }
+        }
+        __syncthreads();
+        pack_store_slice<EB>(tile, LP, ks0, w, dst, lo_off);
+        __syncthreads();
+    }
+}
+
+// coefficient rows of the workspace -> box blocks: box list (block base row, k, kpad); grid
+// (boxes, tiles)
 template <int EB>
-__global__ void tc_pack_coef_kernel(const int4* __restrict__ boxes, const float* __restrict__ ws, int64_t ws_ld,
-                                    const int64_t* __restrict__ src_row, int nrhs, int nrt,
-                                    unsigned char* __restrict__ opnd, int64_t lo_off) {
-    const int b = blockIdx.x;
+__global__ void __launch_bounds__(PK_THREADS) tc_pack_coef_kernel(const int4* __restrict__ boxes,
+                                                                  const float* __restrict__ ws, int64_t ws_ld,
+                                                                  const int64_t* __restrict__ src_row, int nrhs,
+                                                                  unsigned char* __restrict__ opnd, int64_t lo_off) {
+    __shared__ __align__(16) float tile[TC_M][PK_KS + PK_PAD];
+    const int b = blockIdx.x, rt = blockIdx.y, nrt = gridDim.y;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int4 d = boxes[b];   // x: block base row, y: k, z: kpad
     const int64_t s0 = src_row[b];
     const int kp = d.z;
-    const int64_t n = (int64_t)nrt * TC_M * kp;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const int i = (int)(e % kp), r = (int)(e / kp);
-        const float v = (i < d.y && r < nrhs) ? ws[s0 + i + (int64_t)r * ws_ld] : 0.f;
-        const int rt = r / TC_M, rr = r % TC_M;
-        unsigned char* dst = opnd + ((int64_t)d.x * nrt * TC_M + (int64_t)rt * TC_M * kp) * EB + kmaj_off<EB>(rr, i, kp);
-        if constexpr (EB == 2) store_opnd_bf16(dst, v);
-        else store_opnd_tf32(dst, v, lo_off);
+    const int r0 = rt * TC_M;
+    unsigned char* dst = opnd + ((int64_t)d.x * nrt * TC_M + (int64_t)rt * TC_M * kp) * EB;
+    for (int ks0 = 0; ks0 < kp; ks0 += PK_KS) {
+        const int w = min(PK_KS, kp - ks0);
+        for (int i = tx; i < w; i += 32) {
+            const bool valid = ks0 + i < d.y;
+            for (int rr = ty; rr < TC_M; rr += PK_THREADS / 32)
+                tile[rr][i] = (valid && r0 + rr < nrhs) ? ws[s0 + ks0 + i + (int64_t)(r0 + rr) * ws_ld] : 0.f;
+        }
+        __syncthreads();
+        pack_store_slice<EB>(tile, kp, ks0, w, dst, lo_off);
+        __syncthreads();
     }
 }
 
@@ -604,26 +658,26 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
             launch_products<4>(st, st.d_outs.p, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs,
                                P.d_err.p, s);
     };
+    if (nrt > 65535) fail(H2_ERR_INVALID_ARG, "h2_matvec: more than 65535 tiles of 128 right-hand sides");
     auto pack_coef = [&](const std::vector<int4>& bx, const DevBuf<int4>& dbx, const DevBuf<int64_t>& dsrc) {
         if (bx.empty()) return;
+        const dim3 g((unsigned)bx.size(), (unsigned)nrt);
         if (EB == 2)
-            tc_pack_coef_kernel<2><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p, 0);
+            tc_pack_coef_kernel<2><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, P.opnd.p, 0);
         else
-            tc_pack_coef_kernel<4><<<(unsigned)bx.size(), 256, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, nrt, P.opnd.p,
-                                                                       lo_off);
+            tc_pack_coef_kernel<4><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, P.opnd.p, lo_off);
         after_launch("tc_pack_coef");
     };
     P.cur_eb = EB;
     if (phase == 0) {
-        const int64_t xel = (int64_t)P.nleaf * P.LP * nrt * TC_M;
-        const unsigned g = (unsigned)std::min<int64_t>((xel + 255) / 256, 152 * 32);
+        const dim3 g((unsigned)P.nleaf, (unsigned)nrt);
         if (EB == 2)
-            tc_pack_x_kernel<__nv_bfloat16, 2><<<g, 256, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p,
-                                                                  P.d_leaf_start.p, P.d_leaf_size.p, P.LP, P.nleaf,
-                                                                  nrhs, nrt, P.opnd.p, 0);
+            tc_pack_x_kernel<__nv_bfloat16, 2><<<g, PK_THREADS, 0, s>>>((const __nv_bfloat16*)X, ldx, h->d_perm.p,
+                                                                        P.d_leaf_start.p, P.d_leaf_size.p, P.LP,
+                                                                        nrhs, P.opnd.p, 0);
         else
-            tc_pack_x_kernel<float, 4><<<g, 256, 0, s>>>((const float*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
-                                                         P.d_leaf_size.p, P.LP, P.nleaf, nrhs, nrt, P.opnd.p, lo_off);
+            tc_pack_x_kernel<float, 4><<<g, PK_THREADS, 0, s>>>((const float*)X, ldx, h->d_perm.p, P.d_leaf_start.p,
+                                                               P.d_leaf_size.p, P.LP, nrhs, P.opnd.p, lo_off);
         after_launch("tc_pack_x");
         run(P.leaf_up);
     } else if (phase == 1) {

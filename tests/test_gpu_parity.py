@@ -96,6 +96,9 @@ def _oracle_h2(kind):
     if kind == "ragged":   # 37 x 37 grid: leaves of 42/43 points
         mask, op = _heat_problem(37, 150, 5)
         return O.build(op, W.grid_coords(37), 48, ADM_STRONG, 0.7, 1e-6, 24, 32, 16, 128, True, 3)[0], 37, 48, ADM_STRONG
+    if kind == "weak_k48":   # HSS partition at a tight threshold: ranks above 32 (up to the cap 48)
+        mask, op = _heat_problem(32, 200, 11)
+        return O.build(op, W.grid_coords(32), 32, ADM_WEAK, 0.7, 1e-9, 48, 32, 16, 256, True, 3)[0], 32, 32, ADM_WEAK
     if kind == "tiny":     # no levels: a single dense block
         mask, op = _heat_problem(4, 5, 5)
         return O.build(op, W.grid_coords(4), 16, ADM_STRONG, 0.7, 1e-6, 8, 8, 8, 8, False, 3)[0], 4, 16, ADM_STRONG
@@ -103,7 +106,7 @@ def _oracle_h2(kind):
 
 
 @pytest.mark.parametrize("kind", ["heat32_strong", "heat32_weak", "ragged", "tiny"])
-@pytest.mark.parametrize("nrhs", [1, 7, 33])
+@pytest.mark.parametrize("nrhs", [1, 7, 33, 130])
 def test_matvec_fp64_matches_oracle(h2, kind, nrhs):
     h, n, leaf, adm = _oracle_h2(kind)
     tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
@@ -130,6 +133,27 @@ def test_matvec_fp64_matches_oracle(h2, kind, nrhs):
     np.testing.assert_array_equal(rk, r0)
     for a, b in ((U, U0), (E, E0), (S, S0), (D, D0)):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("nrhs", [64, 130, 300])
+def test_matvec_wide_transfer_blocks(h2, nrhs):
+    """Ranks above 32 in the tree sweeps (transfer blocks up to 48 x 48) with many right-hand
+    sides, FP64 and FP32, against the oracle's matvec of the same H^2."""
+    h, n, leaf, adm = _oracle_h2("weak_k48")
+    assert max(int(k.max()) for k in h.k) > 32
+    tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
+    G = h2.H2.from_factors(tree, *factors.oracle_to_import(h), keep_fp32=True)
+    X = W.rhs(n * n, nrhs, 13)
+    want = O.matvec(h, X)
+    Xd = dev(X)
+    Yd = torch.full_like(Xd, float("nan"))
+    G.matvec(Xd, Yd, nrhs, h2.H2_FP64)
+    torch.cuda.synchronize()
+    assert rel(host(Yd), want) < 1e-12
+    Y32 = torch.full((nrhs, n * n), float("nan"), dtype=torch.float32, device="cuda")
+    G.matvec(Xd.float(), Y32, nrhs, h2.H2_FP32)
+    torch.cuda.synchronize()
+    assert rel(host(Y32), want) < 1e-5
 
 
 @pytest.mark.parametrize("kind", ["heat32_strong", "ragged", "heat64"])
