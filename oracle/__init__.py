@@ -11,7 +11,7 @@ as steps.
 """
 from .h2 import H2Matrix, assemble, expand_dense, frobenius_norm, matvec, power_norm, storage_entries
 from .heat import DenseOperator, HeatHessian
-from .peel import PeelResult, TreeOperator, apply_pieces, norm2_estimate, peel
+from .peel import PeelResult, TreeOperator, apply_pieces, global_lowrank, norm2_estimate, peel, psd_cholesky
 from .tree import ADM_STRONG, ADM_WEAK, ClusterTree, Partition
 
 
@@ -26,12 +26,12 @@ def basis_threshold(tol: float, norm_est: float, n_leaves: int) -> float:
 
 
 def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None,
-          q_level=None, q_test=8):
+          q_level=None, q_test=8, global_rank=0):
     """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result)."""
     tree = ClusterTree(coords, leaf)
     part = Partition(tree, adm, eta)
     res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est, q_level=q_level,
-               q_test=q_test)
+               q_test=q_test, global_rank=global_rank)
     res.tau_basis = basis_threshold(tol, res.norm_est, 1 << tree.L)
     h = assemble(tree, part, res, res.tau_basis, kmax)
     return h, res

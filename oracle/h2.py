@@ -83,7 +83,9 @@ def block_row_weights(tree: ClusterTree, part: Partition, pieces):
             groups = {lp: [Rp] for lp, Rp in R[l - 1].get(t >> 1, {}).items()}
             for s in part.far_of[l].get(t, ()):
                 lp = Partition.pair_level(l, t, s)
-                groups.setdefault(lp, []).append(pieces[lp][tree.rows(l, s)])
+                for g in (lp, 0) if 0 in pieces else (lp,):   # the global piece covers every block
+                    if pieces[g].shape[1]:
+                        groups.setdefault(g, []).append(pieces[g][tree.rows(l, s)])
             R[l][t] = {lp: np.linalg.qr(np.vstack(b), mode="r") for lp, b in sorted(groups.items())}
     return R
 
@@ -135,17 +137,23 @@ def assemble(tree: ClusterTree, part: Partition, peel_res, tau: float, kmax: int
     # couplings of the lower far blocks
     for l in range(1, L + 1):
         for t, s in h.far_lower(l):
-            lp = Partition.pair_level(l, t, s)
-            Pt = P[lp][tree.rows(l, t)]
-            Ps = P[lp][tree.rows(l, s)]
-            h.S[(l, t, s)] = (h.Uexp[l][t].T @ Pt) @ (h.Uexp[l][s].T @ Ps).T
+            lps = [Partition.pair_level(l, t, s)] + ([0] if 0 in P else [])
+            S = np.zeros((int(h.k[l][t]), int(h.k[l][s])))
+            for lp in lps:
+                Pt = P[lp][tree.rows(l, t)]
+                Ps = P[lp][tree.rows(l, s)]
+                S += (h.Uexp[l][t].T @ Pt) @ (h.Uexp[l][s].T @ Ps).T
+            h.S[(l, t, s)] = S
     # dense near blocks
     for t, s in h.near_lower():
         if t == s:
             h.D[(t, s)] = peel_res.D_diag[t].copy()
         else:
             lp = Partition.pair_level(L, t, s)
-            h.D[(t, s)] = P[lp][tree.rows(L, t)] @ P[lp][tree.rows(L, s)].T
+            D = P[lp][tree.rows(L, t)] @ P[lp][tree.rows(L, s)].T
+            if 0 in P:
+                D = D + P[0][tree.rows(L, t)] @ P[0][tree.rows(L, s)].T
+            h.D[(t, s)] = D
     return h
 
 

@@ -38,6 +38,22 @@ the paper's implementation uses:
 Pieces of level l are stored in one N x q_l array P_l (tree order): rows of
 child-1 boxes hold Q_b, rows of child-0 boxes hold Z[a], so that for every
 pair H[b, a] ~ P_l[b] P_l[a]^T and H[a, b] ~ P_l[a] P_l[b]^T.
+
+Global low rank first (Section 3.3, end; the hybrid construction): with a
+global rank budget r_max > 0, a randomized range finder on the whole matrix
+(probes Gaussian on every row, from the `global` stream; start q0, growth b_inc
+up to r_max, the same a-posteriori test and fused first test batch as the
+levels) gives an orthonormal Q; one more product gives M = Q^T H Q
+(symmetrised), and its semidefinite Cholesky factor C (C C^T = M) gives
+B = Q C, so that B B^T = Q Q^T H Q Q^T.  B is stored as the level-0 piece
+P_0: every block of B B^T is P_0[t] P_0[s]^T, including the diagonal blocks,
+so it is removed from every later sample together with the level pieces
+(the levels then sample the residual H - B B^T) and added back in the
+assembly, where it joins the block rows of every box as one more group
+(the low-rank update followed by recompression of Section 3.2).  When the
+global range test passes within the budget, the global approximation already
+meets the target and the residual is not sampled at all: every level piece is
+empty (passed = 2) and the diagonal leaf blocks are those of B B^T.
 """
 from __future__ import annotations
 
@@ -86,15 +102,82 @@ def norm2_estimate(opt: TreeOperator, N: int, seed: int, maxit: int = 50, rtol: 
 
 
 def apply_pieces(pieces, levels, tree: ClusterTree, Om: np.ndarray) -> np.ndarray:
-    """K Om for K = sum over the given levels of the sampled sibling pieces (flat low rank)."""
+    """K Om for K = sum over the given levels of the sampled sibling pieces (flat low rank);
+    level 0 is the global piece B, whose block pattern is the whole matrix: K += B B^T."""
     out = np.zeros_like(Om)
     for l in levels:
+        if l not in pieces:
+            continue
         P = pieces[l]
+        if l == 0:
+            out += P @ (P.T @ Om)
+            continue
         for i in range(1 << (l - 1)):
             a, b = tree.rows(l, 2 * i), tree.rows(l, 2 * i + 1)
             out[b] += P[b] @ (P[a].T @ Om[a])
             out[a] += P[a] @ (P[b].T @ Om[b])
     return out
+
+
+def psd_cholesky(M: np.ndarray) -> np.ndarray:
+    """Lower-triangular C with C C^T = M for a symmetric positive semidefinite M (right-looking
+    Cholesky).  A pivot at or below n * 2^-52 * max(diag M) is rounding noise of a zero
+    eigenvalue: its column of C is left zero and the elimination continues."""
+    n = M.shape[0]
+    A = np.array(M, dtype=np.float64)
+    C = np.zeros_like(A)
+    if n == 0:
+        return C
+    drop = n * 2.0 ** -52 * max(float(np.max(np.diag(A))), 0.0)
+    for j in range(n):
+        d = A[j, j]
+        if d <= drop:
+            continue
+        C[j, j] = math.sqrt(d)
+        C[j + 1:, j] = A[j + 1:, j] / C[j, j]
+        A[j + 1:, j + 1:] -= np.outer(C[j + 1:, j], C[j + 1:, j])
+    return C
+
+
+def global_lowrank(opt, N: int, thr: float, q0: int, b_inc: int, r_max: int, adaptive: bool, seed: int, res):
+    """The global piece B (N x r, tree order), B B^T = Q Q^T H Q Q^T (Section 3.3, end)."""
+    def probe(col0, ncols):
+        return opt(rng.gaussian_block(seed, rng.STREAM_GLOBAL, 0, N, col0, ncols))
+
+    q = min(q0, r_max, N)
+    c1 = min(b_inc, r_max - q) if (adaptive and q < r_max and q < N) else 0
+    Y = probe(0, q + c1)
+    calls = 1
+    pending = Y[:, q:] if c1 else None
+    Ys = Y[:, :q]
+    Q = np.linalg.qr(Ys)[0]
+    passed = 0
+    errs = []
+    while adaptive and q < r_max and q < N:
+        c = min(b_inc, r_max - q)
+        if pending is not None:
+            Yn, pending = pending, None
+        else:
+            Yn = probe(q, c)
+            calls += 1
+        r = Yn - Q @ (Q.T @ Yn)
+        err = float(np.linalg.norm(r, axis=0).max())
+        errs.append(err)
+        Ys = np.hstack([Ys, Yn])
+        Q = np.linalg.qr(Ys)[0]
+        q += c
+        if err <= thr:
+            passed = 1
+            break
+    Z = opt(Q)
+    M = Q.T @ Z
+    M = 0.5 * (M + M.T)
+    B = Q @ psd_cholesky(M)
+    res.global_rank = q
+    res.global_calls = calls
+    res.global_passed = passed
+    res.global_test_err = errs
+    return B
 
 
 class PeelResult:
@@ -112,13 +195,19 @@ class PeelResult:
         self.norm_est = 0.0
         self.norm_its = 0
         self.tau = 0.0
+        self.global_rank = 0      # columns of the global range basis (0: no global piece)
+        self.global_calls = 0     # operator calls of its range finder
+        self.global_passed = 0    # 1: its a-posteriori test passed within the budget
+        self.global_test_err = []
 
 
 def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, adaptive: bool,
-         seed: int, norm_est: float | None = None, q_level=None, q_test: int = 8) -> PeelResult:
+         seed: int, norm_est: float | None = None, q_level=None, q_test: int = 8,
+         global_rank: int = 0) -> PeelResult:
     """Construct the sibling pieces and the leaf diagonal blocks from products with op.
 
-    q_level: optional sequence indexed by level (entries <= 0 mean q0) of start counts."""
+    q_level: optional sequence indexed by level (entries <= 0 mean q0) of start counts.
+    global_rank: budget of the global low-rank piece (0: none)."""
     N = tree.N
     opt = TreeOperator(op, tree)
     res = PeelResult()
@@ -129,13 +218,23 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
     tau = tol * res.norm_est
     res.tau = tau
     thr = tau / (10.0 * math.sqrt(2.0 / math.pi))
+    if global_rank > 0:
+        res.pieces[0] = global_lowrank(opt, N, thr, q0, b_inc, global_rank, adaptive, seed, res)
 
+    covered = global_rank > 0 and res.global_passed == 1
     for l in range(1, tree.L + 1):
         npairs = 1 << (l - 1)
+        if covered:
+            res.pieces[l] = np.zeros((N, 0))
+            res.rank[l] = [0] * npairs
+            res.range_probes[l] = res.proj_probes[l] = res.range_calls[l] = res.need[l] = 0
+            res.passed[l] = 2
+            res.test_err[l] = []
+            continue
         A = [tree.rows(l, 2 * i) for i in range(npairs)]
         B = [tree.rows(l, 2 * i + 1) for i in range(npairs)]
         mb = max(b.stop - b.start for b in B)
-        below = range(1, l)
+        below = range(0, l)
         Qs = []
         res.test_err[l] = []
         ql = q0
@@ -216,17 +315,27 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
     # leaf diagonal blocks from identity probes
     L = tree.L
     lm = tree.leaf_max
+    if covered:
+        for t in range(1 << L):
+            B = res.pieces[0][tree.rows(L, t)]
+            res.D_diag.append(B @ B.T)
+        res.samples = opt.samples
+        return res
     Om = np.zeros((N, lm))
     nleaf = 1 << L
     for t in range(nleaf):
         r = tree.rows(L, t)
         m = r.stop - r.start
         Om[r.start + np.arange(m), np.arange(m)] = 1.0
-    Y = opt(Om) - apply_pieces(res.pieces, range(1, L + 1), tree, Om)
+    Y = opt(Om) - apply_pieces(res.pieces, range(0, L + 1), tree, Om)
     for t in range(nleaf):
         r = tree.rows(L, t)
         m = r.stop - r.start
         D = Y[r, :m]
-        res.D_diag.append(0.5 * (D + D.T))
+        D = 0.5 * (D + D.T)
+        if 0 in res.pieces:
+            B = res.pieces[0][r]
+            D = D + B @ B.T
+        res.D_diag.append(D)
     res.samples = opt.samples
     return res

@@ -31,6 +31,7 @@ M2 = np.uint64(0x94D049BB133111EB)
 STREAM_PROBE = 1      # range-finder probes
 STREAM_POWER = 2      # start vector of the 2-norm power iteration
 STREAM_ERR = 3        # start vector of the error power iteration
+STREAM_GLOBAL = 5     # probes of the global low-rank range finder
 
 
 def mix64(z):
