@@ -105,6 +105,17 @@ typedef struct {
     const int32_t* q_level;
     int q_level_stride;  /* h2_build_batched: Hessian i reads q_level + i * q_level_stride (0: all share) */
     int q_test;          /* columns of the first range test after a q_level start, 1..16 (default 8) */
+    /* Hybrid construction (Section 3.3, end: a global low-rank approximation B B^T first, the
+     * hierarchical construction on the residual H - B B^T, B B^T added back as a low-rank
+     * update with recompression).  global_rank > 0 is the budget of the global piece: an
+     * adaptive randomized range finder on the whole matrix (start q0, growth b_inc, the levels'
+     * a-posteriori test) gives an orthonormal Q with at most global_rank columns, one more
+     * product gives M = Q^T H Q, and B = Q C with C C^T = M (semidefinite Cholesky; H must be
+     * symmetric positive semidefinite).  If the range test passes within the budget the
+     * residual is not sampled at all (every level reports range_passed = 2).  0 (default):
+     * plain construction.  Requires 0 <= global_rank < n and, when > 0, n <= 147,456 (the
+     * single-panel QR of the whole matrix) and at least one level. */
+    int global_rank;
 } h2_build_opts;
 
 /* Fill *opts with the defaults above.  Returns H2_ERR_INVALID_ARG if opts is NULL. */
@@ -117,6 +128,10 @@ typedef struct {
     int leaf_max;                           /* largest leaf */
     int64_t samples;                        /* Hessian-vector products of the peeling (excl. norm estimate) */
     int64_t norm_products;                  /* products spent on the ||H||_2 estimate */
+    /* Per-level arrays are indexed by level; index 0 (the root, never sampled by the levels)
+     * describes the global piece of a hybrid construction: range_probes[0] = columns of Q,
+     * proj_probes[0] = products of its projection, range_calls[0] / range_need[0] /
+     * range_passed[0] as for the levels (all 0 without a global piece). */
     int range_probes[H2_MAX_LEVELS];        /* range-pass probes per level (index = level) */
     int proj_probes[H2_MAX_LEVELS];         /* projection-pass probes per level */
     int max_rank[H2_MAX_LEVELS];            /* largest basis rank per level */
@@ -133,7 +148,8 @@ typedef struct {
     int range_need[H2_MAX_LEVELS];          /* probes of the range basis that passed the test; range_probes
                                                when no test passed; largest child-1 box for identity levels */
     int range_passed[H2_MAX_LEVELS];        /* 1 a range test passed, 0 none passed (cap or fixed count),
-                                               -1 identity range (no range pass) */
+                                               -1 identity range (no range pass), 2 not sampled: the
+                                               global piece already met the threshold */
 } h2_stats;
 
 /* ---- cluster tree and partition (host only; no CUDA calls) --------------- */

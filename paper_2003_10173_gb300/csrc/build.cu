@@ -32,6 +32,8 @@ namespace {
 
 constexpr int STREAM_PROBE = 1;
 constexpr int STREAM_POWER = 2;
+constexpr int STREAM_GLOBAL = 5;   // probes of the global low-rank range finder
+constexpr int64_t kGlobalMaxRows = 96 * 1536;   // one TSQR panel of the whole matrix
 constexpr int PANEL = 16;
 
 double now_s() {
@@ -98,6 +100,8 @@ class Builder {
     double norm_ = 0.0, tau_basis_ = 0.0, tau_test_ = 0.0;
     bool cap_hit_ = false;
     std::vector<int> range_probes_, proj_probes_, range_calls_, range_need_, range_passed_;
+    int kb0_ = 0;            // columns of the global range basis Q (level-0 slot of Pcap_)
+    bool covered_ = false;   // the global piece met the threshold: the residual is not sampled
 
     void call_op(const double* X, double* Y, int ncols, bool count_sample);
     void check_flag(const char* where, int level);
@@ -109,7 +113,12 @@ class Builder {
     void identity(int l, const std::vector<int>& pairs);
     void blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst);
     void peel_level(int l);
+    void copy_tall(const double* src, double* dst, int cols);
+    void gproject(int c0, int c, int passes);
+    void gpanel(int c0, int w);
+    void global_pass();
     void leaf_pass();
+    void add_global_diag(double beta);
     void assemble(h2_handle_s* h);
     template <class T>
     T* dev_list(DevBuf<T>& buf, const std::vector<T>& v, int which) {
@@ -191,6 +200,14 @@ void Builder::blocks(int kind, const std::vector<BlkDesc>& d, const double* src,
 
 // Y -= K Omega for the pieces of levels 1..lmax (tree order, N x c, ld N).
 void Builder::subtract(const double* Omt, double* Yt, int c, int lmax) {
+    if (qw_[0] > 0 && lmax >= 0) {
+        // the global piece: Y -= B (B^T Om)
+        const int q = qw_[0];
+        gb_.add(Pl(0), (int)N_, 1, Omt, (int)N_, 0, Tw_.p, q, q, c, (int)N_, 1.0, 0.0);
+        gb_.run(s_);
+        gb_.add(Pl(0), (int)N_, 0, Tw_.p, q, 0, Yt, (int)N_, (int)N_, c, q, -1.0, 1.0);
+        gb_.run(s_);
+    }
     for (int lp = 1; lp <= lmax; ++lp) {
         const int q = qw_[lp];
         if (q == 0) continue;
@@ -399,10 +416,138 @@ void Builder::peel_level(int l) {
     check_flag("projection pass", l);
 }
 
+// dst = src for N x cols tree-order blocks (ld N), in row chunks so that every CTA copies a
+// bounded piece.
+void Builder::copy_tall(const double* src, double* dst, int cols) {
+    std::vector<BlkDesc> d;
+    const int chunk = 2048;
+    for (int64_t r = 0; r < N_; r += chunk)
+        d.push_back(BlkDesc{r, r, (int)std::min<int64_t>(chunk, N_ - r), cols, (int)N_, (int)N_});
+    blocks(BLK_COPY, d, src, dst);
+}
+
+// Block Gram-Schmidt projection of columns [c0, c0+c) of Yt against the global basis Q.
+void Builder::gproject(int c0, int c, int passes) {
+    if (!kb0_) return;
+    for (int pass = 0; pass < passes; ++pass) {
+        gb_.add(Pl(0), (int)N_, 1, Yt_.p + (int64_t)c0 * N_, (int)N_, 0, Cw_.p, kb0_, kb0_, c, (int)N_, 1.0, 0.0);
+        gb_.run(s_);
+        gb_.add(Pl(0), (int)N_, 0, Cw_.p, kb0_, 0, Yt_.p + (int64_t)c0 * N_, (int)N_, (int)N_, c, kb0_, -1.0, 1.0);
+        gb_.run(s_);
+    }
+}
+
+// Appends the panel columns [c0, c0+w) of Yt to the global basis Q (BCGS2 with TSQR, as for
+// the sibling bases, on one panel of all N rows).
+void Builder::gpanel(int c0, int w) {
+    const int64_t yoff = (int64_t)c0 * N_, qoff = (int64_t)kb0_ * N_;
+    const int m = (int)N_;
+    for (int round = 0; round < 2; ++round) {
+        gproject(c0, w, 1);
+        tsqr_panels(1, &yoff, &qoff, &m, w, Yt_.p, (int)N_, Pl(0), (int)N_, tsqr_, s_);
+        if (round == 0) copy_tall(Pl(0) + qoff, Yt_.p + yoff, w);
+    }
+    kb0_ += w;
+}
+
+// Global low-rank piece (Section 3.3, end): adaptive randomized range finder on the whole
+// matrix (Gaussian probes on every row, start q0, growth b_inc up to global_rank, the levels'
+// a-posteriori test with the first test batch drawn in the start call), M = Q^T H Q from one
+// more product, semidefinite Cholesky M = C C^T, and B = Q C stored as the level-0 piece.
+void Builder::global_pass() {
+    const int rmax = o_.global_rank;
+    const double thr = tau_test_;
+    kb0_ = 0;
+    auto batch = [&](int col0, int c) {
+        // shift L: every row's leaf index >> L is 0, so every row gets a Gaussian
+        probe_fill(N_, c, col0, d_perm_.p, d_row_leaf_.p, L_, o_.seed, STREAM_GLOBAL, 0, Om_.p, nullptr, s_);
+        call_op(Om_.p, Yo_.p, c, true);
+        gather_rows(N_, c, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
+    };
+    auto orth = [&](int off, int c) {
+        for (int c0 = 0; c0 < c; c0 += PANEL) gpanel(off + c0, std::min(PANEL, c - c0));
+    };
+    const int q1 = std::min(o_.q0, rmax);
+    const int c1 = (o_.adaptive && q1 < rmax) ? std::min(o_.b_inc, rmax - q1) : 0;
+    batch(0, q1 + c1);
+    int calls = 1, passed = 0, q = q1, need = q1;
+    orth(0, q1);
+    bool pending = c1 > 0;
+    while (o_.adaptive && q < rmax) {
+        const int c = std::min(o_.b_inc, rmax - q);
+        int off = 0;
+        if (pending) {
+            off = q1;
+            pending = false;
+        } else {
+            batch(q, c);
+            ++calls;
+        }
+        gproject(off, c, 2);
+        double err = 0.0;
+        {
+            const int64_t yo = (int64_t)off * N_;
+            const int m = (int)N_;
+            panel_colnorm_max(1, dev_list(d_i64a_, std::vector<int64_t>{yo}, 1), dev_list(d_i32a_, std::vector<int>{m}, 2),
+                              c, Yt_.p, (int)N_, d_red_.p, s_);
+            double* hp = pin_.get<double>(1);
+            H2_CUDA(cudaMemcpyAsync(hp, d_red_.p, sizeof(double), cudaMemcpyDeviceToHost, s_));
+            H2_CUDA(cudaStreamSynchronize(s_));
+            err = *hp;
+        }
+        orth(off, c);
+        need = q;
+        q += c;
+        if (err <= thr) {
+            passed = 1;
+            break;
+        }
+    }
+    if (passed != 1) need = q;
+    check_flag("global range pass", 0);
+    // projection: Z = H Q (tree order), M = Q^T Z, symmetrised, C C^T = M, B = Q C
+    const int r = kb0_;
+    scatter_rows(N_, r, d_perm_.p, Pl(0), N_, Om_.p, N_, s_);
+    call_op(Om_.p, Yo_.p, r, true);
+    gather_rows(N_, r, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
+    check_flag("global projection pass", 0);
+    DevBuf<double> Mg((size_t)r * r * 3);
+    double* M0 = Mg.p;
+    double* M1 = Mg.p + (int64_t)r * r;
+    double* Cc = Mg.p + 2 * (int64_t)r * r;
+    gb_.add(Pl(0), (int)N_, 1, Yt_.p, (int)N_, 0, M0, r, r, r, (int)N_, 1.0, 0.0);
+    gb_.run(s_);
+    blocks(BLK_SYMMETRIZE, {BlkDesc{0, 0, r, r, r, r}}, M0, M1);
+    psd_cholesky(M1, r, Cc, s_);
+    gb_.add(Pl(0), (int)N_, 0, Cc, r, 0, Yt_.p, (int)N_, (int)N_, r, r, 1.0, 0.0);
+    gb_.run(s_);
+    copy_tall(Yt_.p, Pl(0), r);
+    H2_CUDA(cudaStreamSynchronize(s_));
+    qw_[0] = r;
+    covered_ = passed == 1;
+    range_probes_[0] = q;
+    proj_probes_[0] = r;
+    range_calls_[0] = calls;
+    range_need_[0] = need;
+    range_passed_[0] = passed;
+}
+
 // Identity probes on every leaf give the dense diagonal blocks once all pieces are removed.
 void Builder::leaf_pass() {
     const int lm = T_.leaf_max;
     const int nleaf = 1 << L_;
+    if (covered_) {
+        // the global piece met the threshold: the diagonal blocks are those of B B^T
+        ddiag_off_.assign(nleaf, 0);
+        int64_t tot = 0;
+        for (int t = 0; t < nleaf; ++t) {
+            ddiag_off_[t] = tot;
+            tot += (int64_t)bsize(L_, t) * bsize(L_, t);
+        }
+        Ddiag_.reserve((size_t)tot);
+        add_global_diag(0.0);
+        return;
+    }
     fill_zero(Ot_.p, (size_t)N_ * lm, s_);
     std::vector<BlkDesc> d;
     for (int t = 0; t < nleaf; ++t) d.push_back(BlkDesc{0, bstart(L_, t), bsize(L_, t), bsize(L_, t), 0, (int)N_});
@@ -423,6 +568,16 @@ void Builder::leaf_pass() {
         d.push_back(BlkDesc{bstart(L_, t), ddiag_off_[t], bsize(L_, t), bsize(L_, t), (int)N_, bsize(L_, t)});
     blocks(BLK_SYMMETRIZE, d, Yt_.p, Ddiag_.p);
     check_flag("leaf pass", L_);
+    if (qw_[0] > 0) add_global_diag(1.0);
+}
+
+// D_tt = B_t B_t^T + beta D_tt on every leaf (the global piece's diagonal blocks).
+void Builder::add_global_diag(double beta) {
+    const int q = qw_[0];
+    for (int t = 0; t < (1 << L_); ++t)
+        gb_.add(Pl(0) + bstart(L_, t), (int)N_, 0, Pl(0) + bstart(L_, t), (int)N_, 1, Ddiag_.p + ddiag_off_[t],
+                bsize(L_, t), bsize(L_, t), bsize(L_, t), q, 1.0, beta);
+    gb_.run(s_);
 }
 
 // Recompression of the sampled pieces into nested orthonormal bases, couplings and
@@ -432,9 +587,10 @@ void Builder::assemble(h2_handle_s* h) {
     h->koff.assign(L + 2, 0);
     for (int l = 0; l <= L + 1; ++l) h->koff[l] = (1LL << l) - 1;
     h->k.assign((size_t)h->koff[L + 1], 0);
+    // piece columns: level 0 (the global piece of a hybrid construction) then levels 1..L
     std::vector<int64_t> qoff(L + 1, 0);
     int64_t Q = 0;
-    for (int l = 1; l <= L; ++l) {
+    for (int l = 0; l <= L; ++l) {
         qoff[l] = Q;
         Q += qw_[l];
     }
@@ -462,7 +618,7 @@ void Builder::assemble(h2_handle_s* h) {
         {
             std::vector<BlkDesc> d;
             const int chunk = 2048;
-            for (int l = 1; l <= L; ++l)
+            for (int l = 0; l <= L; ++l)
                 for (int64_t r = 0; r < N_; r += chunk)
                     d.push_back(BlkDesc{pcol_[l] * N_ + r, qoff[l] * N_ + r, (int)std::min<int64_t>(chunk, N_ - r),
                                         qw_[l], (int)N_, (int)N_});
@@ -483,16 +639,18 @@ void Builder::assemble(h2_handle_s* h) {
         auto q2 = [&](int lp) { return (int64_t)qw_[lp] * qw_[lp]; };
         for (int l = 1; l <= L; ++l)
             for (auto [r, sb] : T_.far[l]) {
-                const int lp = pair_level(l, r, sb);
-                if (!qw_[lp]) continue;
-                Key kb{l, sb, lp};
-                if (!boff.count(kb)) { boff[kb] = gtot; gtot += q2(lp); }
-                flist[Key{l, r, lp}].push_back(boff[kb]);
+                // the sibling piece of the block's pair level, and the global piece (every block)
+                for (const int lp : {pair_level(l, r, sb), 0}) {
+                    if (!qw_[lp]) continue;
+                    Key kb{l, sb, lp};
+                    if (!boff.count(kb)) { boff[kb] = gtot; gtot += q2(lp); }
+                    flist[Key{l, r, lp}].push_back(boff[kb]);
+                }
             }
         for (auto& [key, lst] : flist) { foff[key] = gtot; gtot += q2(std::get<2>(key)); }
         for (int l = 1; l <= L; ++l)
             for (int t = 0; t < (1 << l); ++t)
-                for (int lp = 1; lp <= l; ++lp) {
+                for (int lp = 0; lp <= l; ++lp) {
                     if (!qw_[lp]) continue;
                     const bool has = foff.count(Key{l, t, lp}) || (l - 1 >= lp && moff.count(Key{l - 1, t >> 1, lp}));
                     if (has) { moff[Key{l, t, lp}] = gtot; gtot += q2(lp); }
@@ -522,7 +680,7 @@ void Builder::assemble(h2_handle_s* h) {
             std::vector<int64_t> oo, io;
             std::vector<int> len, bg, en;
             for (int t = 0; t < (1 << l); ++t)
-                for (int lp = 1; lp <= l; ++lp) {
+                for (int lp = 0; lp <= l; ++lp) {
                     auto it = moff.find(Key{l, t, lp});
                     if (it == moff.end()) continue;
                     oo.push_back(it->second);
@@ -554,7 +712,7 @@ void Builder::assemble(h2_handle_s* h) {
         Gbuf.reserve((size_t)gt);
         Utmp.reserve((size_t)ut);
         for (int t = 0; t < nleaf; ++t)
-            for (int lp = 1; lp <= L; ++lp) {
+            for (int lp = 0; lp <= L; ++lp) {
                 auto it = moff.find(Key{L, t, lp});
                 if (it == moff.end()) continue;
                 const int q = qw_[lp];
@@ -612,7 +770,7 @@ void Builder::assemble(h2_handle_s* h) {
             for (int p = 0; p < nb; ++p) {
                 if (!nn[p]) continue;
                 const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
-                for (int lp = 1; lp <= l; ++lp) {
+                for (int lp = 0; lp <= l; ++lp) {
                     auto it = moff.find(Key{l, p, lp});
                     if (it == moff.end()) continue;
                     const int q = qw_[lp];
@@ -659,26 +817,35 @@ void Builder::assemble(h2_handle_s* h) {
                 if (n && kp) d.push_back(BlkDesc{uhtmp_off[h->koff[l] + p], h->uh_off[h->koff[l] + p], n, kp, n, n});
             }
         blocks(BLK_COPY, d, Uhtmp.p, fac);
-        // couplings S_ts = Pi_lp(t) Pi_lp(s)^T
-        for (int l = 1; l <= L; ++l)
-            for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
-                auto [t, sb] = h->far_lower[l][i];
-                const int lp = pair_level(l, t, sb);
-                const int q = qw_[lp];
-                const int64_t Kl = Krows[l];
-                gb_.add(Pi[l].p + rowoff[l][t] + qoff[lp] * Kl, (int)Kl, 0, Pi[l].p + rowoff[l][sb] + qoff[lp] * Kl, (int)Kl,
-                        1, fac + h->s_off[l][i], std::max(K(l, t), 1), K(l, t), K(l, sb), q, 1.0, 0.0);
-            }
-        gb_.run(s_);
-        // off-diagonal near blocks D_ts = P_lp[t] P_lp[s]^T
-        for (size_t i = 0; i < h->near_lower.size(); ++i) {
-            auto [t, sb] = h->near_lower[i];
-            if (t == sb) continue;
-            const int lp = pair_level(L, t, sb);
-            gb_.add(Pall.p + bstart(L, t) + qoff[lp] * N_, (int)N_, 0, Pall.p + bstart(L, sb) + qoff[lp] * N_, (int)N_, 1,
-                    fac + h->d_off[i], bsize(L, t), bsize(L, t), bsize(L, sb), qw_[lp], 1.0, 0.0);
+        // couplings S_ts = Pi_lp(t) Pi_lp(s)^T (+ Pi_0(t) Pi_0(s)^T for the global piece, added in
+        // a second batch: the problems of one batch must write disjoint blocks)
+        for (const bool global : {false, true}) {
+            if (global && !qw_[0]) break;
+            for (int l = 1; l <= L; ++l)
+                for (size_t i = 0; i < h->far_lower[l].size(); ++i) {
+                    auto [t, sb] = h->far_lower[l][i];
+                    const int lp = global ? 0 : pair_level(l, t, sb);
+                    const int q = qw_[lp];
+                    const int64_t Kl = Krows[l];
+                    gb_.add(Pi[l].p + rowoff[l][t] + qoff[lp] * Kl, (int)Kl, 0, Pi[l].p + rowoff[l][sb] + qoff[lp] * Kl,
+                            (int)Kl, 1, fac + h->s_off[l][i], std::max(K(l, t), 1), K(l, t), K(l, sb), q, 1.0,
+                            global ? 1.0 : 0.0);
+                }
+            gb_.run(s_);
         }
-        gb_.run(s_);
+        // off-diagonal near blocks D_ts = P_lp[t] P_lp[s]^T (+ B_t B_s^T)
+        for (const bool global : {false, true}) {
+            if (global && !qw_[0]) break;
+            for (size_t i = 0; i < h->near_lower.size(); ++i) {
+                auto [t, sb] = h->near_lower[i];
+                if (t == sb) continue;
+                const int lp = global ? 0 : pair_level(L, t, sb);
+                gb_.add(Pall.p + bstart(L, t) + qoff[lp] * N_, (int)N_, 0, Pall.p + bstart(L, sb) + qoff[lp] * N_,
+                        (int)N_, 1, fac + h->d_off[i], bsize(L, t), bsize(L, t), bsize(L, sb), qw_[lp], 1.0,
+                        global ? 1.0 : 0.0);
+            }
+            gb_.run(s_);
+        }
     }
     {
         std::vector<BlkDesc> d;
@@ -719,6 +886,14 @@ void Builder::run(h2_handle_s* h) {
     int64_t pc = 0;
     int qcmax = 1;
     cmax_ = std::max({o_.q0, o_.b_inc, o_.q_test, T_.leaf_max, 1});
+    const bool hybrid = o_.global_rank > 0 && L_ >= 1;
+    if (hybrid) {
+        if (o_.global_rank >= N_) fail(H2_ERR_INVALID_ARG, "h2_build: global_rank must be below n");
+        if (N_ > kGlobalMaxRows) fail(H2_ERR_INVALID_ARG, "h2_build: global_rank needs n <= 147,456");
+        qcap_[0] = o_.global_rank;
+        pc = o_.global_rank;
+        cmax_ = std::max({cmax_, std::min(o_.q0, o_.global_rank) + o_.b_inc, o_.global_rank});
+    }
     for (int l = 1; l <= L_; ++l) {
         int mb = 0;
         for (int i = 0; i < (1 << (l - 1)); ++i) mb = std::max(mb, bsize(l, 2 * i + 1));
@@ -736,7 +911,8 @@ void Builder::run(h2_handle_s* h) {
     Yt_.reserve((size_t)N_ * cmax_);
     Ot_.reserve((size_t)N_ * cmax_);
     Tw_.reserve((size_t)(N_ + nleaf) * cmax_);
-    Cw_.reserve((size_t)std::max(1, nleaf / 2) * qcmax * PANEL);
+    Cw_.reserve(std::max((size_t)std::max(1, nleaf / 2) * qcmax * PANEL,
+                         hybrid ? (size_t)o_.global_rank * std::max(PANEL, o_.b_inc) : (size_t)0));
     Pcap_.reserve((size_t)std::max<int64_t>(N_ * pc, 1));
     fill_zero(Pcap_.p, (size_t)N_ * pc, s_);
     d_flag_.reserve(1);
@@ -749,7 +925,15 @@ void Builder::run(h2_handle_s* h) {
     const double tn1 = now_s();
     tau_test_ = tol_ * norm_ / (10.0 * std::sqrt(2.0 / M_PI));
     tau_basis_ = 2.0 * tol_ * norm_ / std::sqrt((double)nleaf);
-    for (int l = 1; l <= L_; ++l) peel_level(l);
+    if (hybrid) global_pass();
+    for (int l = 1; l <= L_; ++l) {
+        if (covered_) {
+            kb_[l].assign(1 << (l - 1), 0);
+            range_passed_[l] = 2;   // not sampled: the global piece met the threshold
+            continue;
+        }
+        peel_level(l);
+    }
     leaf_pass();
     const double tp = now_s();
     assemble(h);

@@ -88,6 +88,7 @@ h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
     require(o.b_inc >= 1 && o.b_inc <= 16, "h2_build: b_inc must be in 1..16");
     require(o.q_test >= 1 && o.q_test <= 16, "h2_build: q_test must be in 1..16");
     require(o.q_level_stride >= 0, "h2_build: q_level_stride must be >= 0");
+    require(o.global_rank >= 0, "h2_build: global_rank must be >= 0");
     require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
     require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
     return o;
@@ -115,6 +116,7 @@ int h2_build_opts_default(h2_build_opts* o) {
     o->q_level = nullptr;
     o->q_level_stride = 0;
     o->q_test = 8;
+    o->global_rank = 0;
     return H2_OK;
 }
 

@@ -241,6 +241,9 @@ enum { BLK_COPY = 0, BLK_IDENTITY = 1, BLK_SYMMETRIZE = 2 };
 // COPY: dst = src; IDENTITY: dst = I (src unused); SYMMETRIZE: dst = (src + src^T)/2 (square)
 void block_op(int kind, int count, const BlkDesc* d_desc, const double* src, double* dst, cudaStream_t s);
 uint64_t rng_key(uint64_t seed, int stream_id, int level);
+// C (n x n, lower, ld n) with C C^T = A for a symmetric positive semidefinite A (ld n, lower
+// triangle used and overwritten); pivots at rounding level leave their column of C zero.
+void psd_cholesky(double* A, int n, double* C, cudaStream_t s);
 int eig_max_order();
 
 }  // namespace h2

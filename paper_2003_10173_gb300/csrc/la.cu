@@ -571,4 +571,52 @@ void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, int max
 
 int eig_max_order() { return EIG_MAXN; }
 
+namespace {
+
+constexpr int CHOL_NT = 1024;
+
+// Right-looking Cholesky of the symmetric positive semidefinite n x n matrix A (column-major,
+// lower triangle used and overwritten) into the lower-triangular C (zero above the diagonal).
+// A pivot at or below n 2^-52 max(diag A) is rounding noise of a zero eigenvalue: its column
+// of C stays zero and the elimination continues.  One CTA; every branch is uniform.
+__global__ void __launch_bounds__(CHOL_NT) psd_cholesky_kernel(double* __restrict__ A, int n, double* __restrict__ C) {
+    __shared__ double red[CHOL_NT / 32];
+    __shared__ double s_drop;
+    const int tid = threadIdx.x;
+    double mx = 0.0;
+    for (int i = tid; i < n; i += CHOL_NT) mx = fmax(mx, A[i + (int64_t)i * n]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    for (int64_t e = tid; e < (int64_t)n * n; e += CHOL_NT) C[e] = 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < CHOL_NT / 32; ++w) m = fmax(m, red[w]);
+        s_drop = (double)n * 0x1p-52 * m;
+    }
+    __syncthreads();
+    const double drop = s_drop;
+    for (int j = 0; j < n; ++j) {
+        const double d = A[j + (int64_t)j * n];
+        if (!(d > drop)) continue;   // the same value in every thread: uniform
+        const double cjj = sqrt(d);
+        for (int i = j + tid; i < n; i += CHOL_NT) C[i + (int64_t)j * n] = (i == j) ? cjj : A[i + (int64_t)j * n] / cjj;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int64_t e = tid; e < (int64_t)m * m; e += CHOL_NT) {
+            const int i = j + 1 + (int)(e % m), k = j + 1 + (int)(e / m);
+            if (k <= i) A[i + (int64_t)k * n] -= C[i + (int64_t)j * n] * C[k + (int64_t)j * n];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void psd_cholesky(double* A, int n, double* C, cudaStream_t s) {
+    if (n <= 0) return;
+    psd_cholesky_kernel<<<1, CHOL_NT, 0, s>>>(A, n, C);
+    after_launch("psd_cholesky");
+}
+
 }  // namespace h2

@@ -92,7 +92,7 @@ def test_argument_validation(h2):
     L.h2_tree_free(None)
     o = h2.default_opts()
     assert (o.kmax, o.q0, o.b_inc, o.q_max, o.adaptive) == (32, 32, 16, 256, 1)
-    assert (o.q_level, o.q_level_stride, o.q_test) == (None, 0, 8)
+    assert (o.q_level, o.q_level_stride, o.q_test, o.global_rank) == (None, 0, 8, 0)
 
 
 @pytest.mark.parametrize("n,leaf,adm", [(4, 4, ADM_WEAK), (37, 16, ADM_STRONG), (64, 64, ADM_STRONG)])
