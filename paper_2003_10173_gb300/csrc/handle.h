@@ -97,6 +97,10 @@ struct TcItem {
     int k;             // MMA K extent (padded to 16)
     int64_t b_off;     // byte offset of the B tile in the tile pool of the precision
 };
+struct TcGroup {       // consecutive outputs computed by one CTA, side by side in tensor memory
+    int obeg, oend;    // output range
+    int ibeg, iend;    // their items (split TF32: the tripled list has its own groups)
+};
 struct TcTileSrc {     // how a B tile is made from the FP64 factors
     int64_t m_off, dst;
     int ldm, trans, rows, cols, n, k;
@@ -104,6 +108,9 @@ struct TcTileSrc {     // how a B tile is made from the FP64 factors
 struct TcStage {
     std::vector<TcOut> outs;
     std::vector<TcItem> items;     // b_off holds the tile index until packing
+    std::vector<TcGroup> groups;
+    DevBuf<TcGroup> d_groups, d_groups32x3;
+    int tmem_cols = 32;            // tensor-memory columns per CTA (power of two >= the widest group)
     DevBuf<TcOut> d_outs, d_outs32x3;
     DevBuf<TcItem> d_items16, d_items32, d_items32x3;   // split TF32: three items per product
 };

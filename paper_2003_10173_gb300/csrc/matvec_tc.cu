@@ -100,6 +100,9 @@ struct TcTraits<4> {   // TF32 operands, kind::tf32, K = 8 per MMA
 // The accumulator is written transposed: to Y through the tree permutation (leaf outputs) or
 // to the coefficient workspace (upsweep / coupling outputs).
 constexpr int TC_NMAX = 64, TC_KMAX = 64;
+constexpr int TC_GCOLS = 128;   // tensor-memory columns of a CTA: its outputs side by side (4 CTAs per SM)
+constexpr int TC_GMAX = 8;      // outputs per CTA
+constexpr int TC_GROUP_ITEMS = 84;   // items per CTA group (x3 for split TF32 <= TC_ITEM_CACHE)
 
 template <int EB>
 struct TcCfg {
@@ -120,6 +123,8 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// One output per CTA (the near field + leaf expansion: outputs are rows of Y through the
+// permutation, transposed through shared memory).
 template <int EB>
 __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     const TcOut* __restrict__ outs, const TcItem* __restrict__ items, const unsigned char* __restrict__ W,
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
     using Tr = TcTraits<EB>;
     using C = TcCfg<EB>;
     constexpr int S = C::STAGES;
-    constexpr int TMEM_COLS = 64;
+    constexpr int TMEM_COLS = 64;   // one output of at most TC_NMAX columns
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ uint32_t tmem_slot;
@@ -254,6 +259,166 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
         if (o.to_y) Y[perm[o.out_off + i] + (int64_t)(r0 + r) * ldy] = v;
         else ws[o.out_off + i + (int64_t)(r0 + r) * ws_ld] = v;
     }
+}
+
+// Several consecutive coefficient outputs per CTA (leaf upsweep, couplings): one operand ring
+// across all their items, each output accumulating in its own columns of tensor memory, stored
+// to the workspace straight from the tensor-memory loads.
+template <int EB>
+__global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
+    const TcGroup* __restrict__ groups, const TcOut* __restrict__ outs, const TcItem* __restrict__ items,
+    const unsigned char* __restrict__ W, const unsigned char* __restrict__ opnd, float* __restrict__ ws,
+    int64_t ws_ld, int nrhs, int tmem_cols, int* __restrict__ err) {
+    using Tr = TcTraits<EB>;
+    using C = TcCfg<EB>;
+    constexpr int S = C::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int okflag, prod_issued, cons_done;
+    __shared__ TcItem sitems[TC_ITEM_CACHE];
+    __shared__ TcOut souts[TC_GMAX];
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int rt = blockIdx.x;
+    const int r0 = rt * TC_M;
+    const TcGroup g = groups[blockIdx.y];
+    const int nout = g.oend - g.obeg;   // 1..TC_GMAX (host-checked)
+    const int ibeg = g.ibeg;
+    const int nitem = g.iend - g.ibeg;
+    // the group's outputs and item descriptors, staged once in shared memory (off the producer's
+    // critical path)
+    if (tid < nout) souts[tid] = outs[g.obeg + tid];
+    const bool cached = nitem <= TC_ITEM_CACHE;
+    if (cached)
+        for (int i = tid; i < nitem; i += TC_THREADS) sitems[i] = items[ibeg + i];
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+        }
+        okflag = 1;
+        prod_issued = 0;
+        cons_done = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    auto item_at = [&](int it) -> TcItem { return cached ? sitems[it - ibeg] : items[it]; };
+
+    // warp-specialised pipeline over all items of the group's outputs, in output order: thread 0
+    // copies operands into the stage ring, thread 32 issues the MMAs into the output's columns of
+    // tensor memory; a stage is refilled as soon as the MMAs that read it have completed
+    if (tid == 0) {
+        int issued = 0;
+        bool run = true;
+        for (int j = 0; j < nout && run; ++j) {
+            const TcOut o = souts[j];
+            for (int it = o.beg; it < o.end; ++it) {
+                const int st = issued % S;
+                if (issued >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((issued / S) - 1) & 1), err)) {
+                    run = false;
+                    break;
+                }
+                const TcItem m = item_at(it);
+                const uint32_t abytes = (uint32_t)(TC_M * m.k * EB);
+                const uint32_t bbytes = (uint32_t)(o.n * m.k * EB);
+                const uint32_t sa = smem_u32(smem + st * C::STAGE_BYTES);
+                const uint32_t fb = smem_u32(&full[st]);
+                mbar_expect(fb, abytes + bbytes);
+                // block base (rows) x tiles x 128 columns, then this tile
+                const int64_t aoff = ((int64_t)m.a_row * gridDim.x * TC_M + (int64_t)rt * TC_M * m.k) * EB;
+                bulk_g2s(sa, opnd + aoff, abytes, fb);
+                bulk_g2s(sa + C::A_BYTES, W + m.b_off, bbytes, fb);
+                ++issued;
+            }
+        }
+        prod_issued = issued;
+    } else if (tid == 32) {
+        int done = 0, col = 0;
+        bool run = true;
+        for (int j = 0; j < nout && run; ++j) {
+            const TcOut o = souts[j];
+            const uint32_t idesc = (1u << 4) | (Tr::ab_fmt << 7) | (Tr::ab_fmt << 10) |
+                                   ((uint32_t)(o.n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+            const uint32_t d = tmem + (uint32_t)col;
+            col += o.n;
+            for (int it = o.beg; it < o.end; ++it) {
+                const int st = done % S;
+                if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((done / S) & 1), err)) {
+                    run = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int K = item_at(it).k;
+                const uint32_t a0 = smem_u32(smem + st * C::STAGE_BYTES);
+                const uint32_t b0 = a0 + C::A_BYTES;
+                const uint32_t SBO = (uint32_t)(K * EB / 16) * 128;
+                for (int kk = 0; kk < K / Tr::KSTEP; ++kk) {
+                    const uint64_t ad = smem_desc(a0 + kk * 256, 128, SBO);
+                    const uint64_t bd = smem_desc(b0 + kk * 256, 128, SBO);
+                    Tr::mma(d, ad, bd, idesc, (it > o.beg || kk > 0) ? 1u : 0u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&empty[st])));
+                ++done;
+            }
+        }
+        cons_done = done;
+        // every MMA issued completes before the accumulators are read or released
+        if (done > 0 && !mbar_wait(smem_u32(&empty[(done - 1) % S]), (uint32_t)(((done - 1) / S) & 1), err))
+            done = -1;
+        if (done != nitem) okflag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // copies issued for items that were never consumed land before the memory is reused
+        for (int j = cons_done; j < prod_issued; ++j)
+            mbar_wait(smem_u32(&full[j % S]), (uint32_t)((j / S) & 1), err);
+        if (prod_issued != nitem) okflag = 0;
+    }
+    __syncthreads();
+    const bool ok = okflag != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // coefficient outputs: each thread stores its right-hand side's row of every block
+    // (consecutive workspace rows) straight from the tensor-memory loads
+    const int r = warp * 32 + (tid & 31);
+    const bool live = r0 + r < nrhs;
+    int col = 0;
+    for (int j = 0; j < nout && ok; ++j) {
+        const TcOut o = souts[j];
+        const bool any = o.end > o.beg;
+        float* dst = ws + o.out_off + (int64_t)(r0 + r) * ws_ld;
+        for (int c0 = 0; c0 < o.n; c0 += 16) {
+            uint32_t v[16];
+            if (any) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(col + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0u;
+            }
+            if (live)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < o.rows) dst[c0 + q] = __uint_as_float(v[q]);
+        }
+        col += o.n;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 // TF32 rounding (nearest, ties away) as an FP32 bit pattern, and the rounded low part of the rest:
@@ -403,7 +568,8 @@ __global__ void __launch_bounds__(PK_THREADS) tc_pack_coef_kernel(const int4* __
 }
 
 template <int EB>
-void launch_products(const TcStage& st, const TcOut* d_outs, const TcItem* d_items, const unsigned char* W,
+void launch_products(const TcStage& st, const TcGroup* d_groups, const TcOut* d_outs, const TcItem* d_items,
+                     const unsigned char* W,
                      const unsigned char* opnd, const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld,
                      int nrhs, int* err, cudaStream_t s) {
     if (st.outs.empty()) return;
@@ -411,11 +577,18 @@ void launch_products(const TcStage& st, const TcOut* d_outs, const TcItem* d_ite
     static std::once_flag attr;
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(tc_products_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        H2_CUDA(cudaFuncSetAttribute(tc_group_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     });
-    dim3 grid((unsigned)((nrhs + TC_M - 1) / TC_M), (unsigned)st.outs.size());
-    tc_products_kernel<EB><<<grid, TC_THREADS, smem, s>>>(d_outs, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs,
-                                                          err);
-    after_launch("tc_products");
+    const unsigned nrt = (unsigned)((nrhs + TC_M - 1) / TC_M);
+    if (st.outs[0].to_y) {
+        tc_products_kernel<EB><<<dim3(nrt, (unsigned)st.outs.size()), TC_THREADS, smem, s>>>(
+            d_outs, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs, err);
+        after_launch("tc_products");
+    } else {
+        tc_group_kernel<EB><<<dim3(nrt, (unsigned)st.groups.size()), TC_THREADS, smem, s>>>(
+            d_groups, d_outs, d_items, W, opnd, ws, ws_ld, nrhs, st.tmem_cols, err);
+        after_launch("tc_group");
+    }
 }
 
 inline int pad16(int k) { return (k + 15) / 16 * 16; }
@@ -553,10 +726,46 @@ void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
     for (TcStage* st : {&P.leaf_up, &P.couple, &P.near})
         for (auto& o : st->outs)
             if (o.n > TC_NMAX || o.n % 16) fail(H2_ERR_INVALID_ARG, "tensor-core plan: output rows out of range");
+    // CTA groups: consecutive outputs (neighbouring boxes in tree order) side by side in tensor
+    // memory, one operand ring across all their items; coefficient outputs only (the near-field
+    // outputs go through the permutation and keep one CTA each), and at most TC_GROUP_ITEMS items
+    // so that the split-TF32 lists (three items per product) stay in the shared-memory cache
+    for (TcStage* st : {&P.leaf_up, &P.couple, &P.near}) {
+        st->groups.clear();
+        st->tmem_cols = 32;
+        int cols = 0, nit = 0;
+        for (int o = 0; o < (int)st->outs.size(); ++o) {
+            const TcOut& out = st->outs[o];
+            const int n = out.n, ni = out.end - out.beg;
+            if (st->groups.empty() || out.to_y || st->outs[st->groups.back().obeg].to_y || cols + n > TC_GCOLS ||
+                nit + ni > TC_GROUP_ITEMS || st->groups.back().oend - st->groups.back().obeg >= TC_GMAX) {
+                st->groups.push_back(TcGroup{o, o, out.beg, out.beg});
+                cols = 0;
+                nit = 0;
+            }
+            st->groups.back().oend = o + 1;
+            st->groups.back().iend = out.end;
+            cols += n;
+            nit += ni;
+            while (st->tmem_cols < cols) st->tmem_cols *= 2;
+        }
+        if (st->groups.size() > 65535) fail(H2_ERR_INVALID_ARG, "tensor-core plan: more than 65535 output groups");
+        for (const auto& o : st->outs)
+            if (o.to_y != st->outs[0].to_y) fail(H2_ERR_INVALID_ARG, "tensor-core plan: mixed output kinds in a stage");
+    }
     P.w_elems = wpos;
     Stager stg;
     for (TcStage* st : {&P.leaf_up, &P.couple, &P.near}) {
         upload(st->d_outs, st->outs, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+        upload(st->d_groups, st->groups, s, stg);
+        H2_CUDA(cudaStreamSynchronize(s));
+        std::vector<TcGroup> g3 = st->groups;
+        for (auto& g : g3) {
+            g.ibeg *= 3;
+            g.iend *= 3;
+        }
+        upload(st->d_groups32x3, g3, s, stg);
         H2_CUDA(cudaStreamSynchronize(s));
     }
     P.d_err.reserve(1);
@@ -649,14 +858,14 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
     auto run = [&](TcStage& st) {
         if (st.outs.empty()) return;
         if (EB == 2)
-            launch_products<2>(st, st.d_outs.p, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs,
-                               P.d_err.p, s);
+            launch_products<2>(st, st.d_groups.p, st.d_outs.p, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws,
+                               ws_ld, nrhs, P.d_err.p, s);
         else if (split)
-            launch_products<4>(st, st.d_outs32x3.p, st.d_items32x3.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld,
-                               nrhs, P.d_err.p, s);
+            launch_products<4>(st, st.d_groups32x3.p, st.d_outs32x3.p, st.d_items32x3.p, W, P.opnd.p, h->d_perm.p, Y,
+                               ldy, ws, ws_ld, nrhs, P.d_err.p, s);
         else
-            launch_products<4>(st, st.d_outs.p, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws, ws_ld, nrhs,
-                               P.d_err.p, s);
+            launch_products<4>(st, st.d_groups.p, st.d_outs.p, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws,
+                               ws_ld, nrhs, P.d_err.p, s);
     };
     if (nrt > 65535) fail(H2_ERR_INVALID_ARG, "h2_matvec: more than 65535 tiles of 128 right-hand sides");
     auto pack_coef = [&](const std::vector<int4>& bx, const DevBuf<int4>& dbx, const DevBuf<int64_t>& dsrc) {
