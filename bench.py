@@ -392,37 +392,42 @@ def learned_ranks_section(h2, torch, stream) -> dict:
 
 
 def hybrid_section(h2, torch, stream) -> dict:
-    """Hybrid construction (Section 3.3, end) on the 256 x 256 heat Hessian: a global low-rank
-    piece B B^T from an adaptive randomized range finder with budgets 128..512, then H^2 on the
-    residual (skipped when the global range test passes), against the plain construction, all
-    at tol 1e-6: products, operator calls, build seconds and the 2-norm error of each."""
-    p, bb = W.MEDIUM_N256["problem"], W.MEDIUM_N256["build"]
-    gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
-    tree = h2.Tree(W.grid_coords(p.n), bb.leaf, bb.adm, bb.eta)
-    base = dict(kmax=bb.kmax, q0=bb.q0, b_inc=bb.b_inc, q_max=bb.q_max, adaptive=1, seed=bb.seed, stream=stream)
-    out = {"workload": W.MEDIUM_N256["name"], "runs": {}}
-    for budget in (0, 128, 256, 384, 512):
-        opts = h2.default_opts(**base, global_rank=budget)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G = h2.H2.build(gop, tree, bb.tol, opts)
-        torch.cuda.synchronize()
-        bt = time.perf_counter() - t0
-        st = G.stats()
-        key = "plain" if budget == 0 else f"global_{budget}"
-        out["runs"][key] = {
-            "global_budget": budget, "global_rank": st["range_probes"][0], "global_passed": st["range_passed"][0],
-            "samples": st["samples"], "op_calls": st["op_calls"], "build_s": bt, "t_peel": st["t_peel"],
-            "t_assemble": st["t_assemble"], "max_rank": st["max_rank"],
-            "levels_sampled": sum(1 for l in range(1, st["levels"] + 1) if st["range_passed"][l] != 2),
-            "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, p.N, st["norm_est"], stream)}
-        G.close()
-    plain = out["runs"]["plain"]
-    best = min((r for k, r in out["runs"].items() if k != "plain"), key=lambda r: r["samples"])
-    out["best"] = {"global_budget": best["global_budget"], "samples_saved": 1.0 - best["samples"] / plain["samples"],
-                   "build_speedup": plain["build_s"] / best["build_s"]}
-    del gop, tree
-    torch.cuda.empty_cache()
+    """Hybrid construction (Section 3.3, end) on the 256 x 256 and 512 x 512 heat Hessians: a
+    global low-rank piece B B^T from an adaptive randomized range finder with several budgets,
+    then H^2 on the residual (skipped when the global range test passes), against the plain
+    construction, all at tol 1e-6: products, operator calls, build seconds and the 2-norm error
+    of each."""
+    out = {}
+    for cfg, budgets in ((W.MEDIUM_N256, (0, 128, 256, 384, 512)), (W.LARGE_N512, (0, 256, 512, 768))):
+        p, bb = cfg["problem"], cfg["build"]
+        gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+        tree = h2.Tree(W.grid_coords(p.n), bb.leaf, bb.adm, bb.eta)
+        base = dict(kmax=bb.kmax, q0=bb.q0, b_inc=bb.b_inc, q_max=bb.q_max, adaptive=1, seed=bb.seed, stream=stream)
+        res = {"runs": {}}
+        for budget in budgets:
+            opts = h2.default_opts(**base, global_rank=budget)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = h2.H2.build(gop, tree, bb.tol, opts)
+            torch.cuda.synchronize()
+            bt = time.perf_counter() - t0
+            st = G.stats()
+            key = "plain" if budget == 0 else f"global_{budget}"
+            res["runs"][key] = {
+                "global_budget": budget, "global_rank": st["range_probes"][0], "global_passed": st["range_passed"][0],
+                "samples": st["samples"], "op_calls": st["op_calls"], "build_s": bt, "t_peel": st["t_peel"],
+                "t_assemble": st["t_assemble"], "max_rank": st["max_rank"],
+                "levels_sampled": sum(1 for l in range(1, st["levels"] + 1) if st["range_passed"][l] != 2),
+                "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, p.N, st["norm_est"], stream)}
+            G.close()
+        plain = res["runs"]["plain"]
+        best = min((r for k, r in res["runs"].items() if k != "plain"), key=lambda r: r["samples"])
+        res["best"] = {"global_budget": best["global_budget"],
+                       "samples_saved": 1.0 - best["samples"] / plain["samples"],
+                       "build_speedup": plain["build_s"] / best["build_s"]}
+        out[cfg["name"]] = res
+        del gop, tree
+        torch.cuda.empty_cache()
     return out
 
 

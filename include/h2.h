@@ -113,8 +113,8 @@ typedef struct {
      * product gives M = Q^T H Q, and B = Q C with C C^T = M (semidefinite Cholesky; H must be
      * symmetric positive semidefinite).  If the range test passes within the budget the
      * residual is not sampled at all (every level reports range_passed = 2).  0 (default):
-     * plain construction.  Requires 0 <= global_rank < n and, when > 0, n <= 147,456 (the
-     * single-panel QR of the whole matrix) and at least one level. */
+     * plain construction.  Requires 0 <= global_rank < n and, when > 0, n <= 14,155,776 (the
+     * two-level tall-skinny QR of the whole matrix); ignored for a single leaf. */
     int global_rank;
 } h2_build_opts;
 

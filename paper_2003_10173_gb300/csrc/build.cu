@@ -33,7 +33,7 @@ namespace {
 constexpr int STREAM_PROBE = 1;
 constexpr int STREAM_POWER = 2;
 constexpr int STREAM_GLOBAL = 5;   // probes of the global low-rank range finder
-constexpr int64_t kGlobalMaxRows = 96 * 1536;   // one TSQR panel of the whole matrix
+constexpr int64_t kGlobalMaxRows = (int64_t)96 * 96 * 1536;   // one two-level TSQR panel of the whole matrix
 constexpr int PANEL = 16;
 
 double now_s() {
@@ -889,7 +889,7 @@ void Builder::run(h2_handle_s* h) {
     const bool hybrid = o_.global_rank > 0 && L_ >= 1;
     if (hybrid) {
         if (o_.global_rank >= N_) fail(H2_ERR_INVALID_ARG, "h2_build: global_rank must be below n");
-        if (N_ > kGlobalMaxRows) fail(H2_ERR_INVALID_ARG, "h2_build: global_rank needs n <= 147,456");
+        if (N_ > kGlobalMaxRows) fail(H2_ERR_INVALID_ARG, "h2_build: global_rank needs n <= 14,155,776");
         qcap_[0] = o_.global_rank;
         pc = o_.global_rank;
         cmax_ = std::max({cmax_, std::min(o_.q0, o_.global_rank) + o_.b_inc, o_.global_rank});

@@ -187,10 +187,10 @@ constexpr int kTsqrChunk = 512;      // target rows per chunk
 constexpr int kTsqrMaxChunks = 96;   // chunks per panel (stacked R: <= 1536 x 16)
 constexpr int kTsqrMaxRows = 1536;   // shared-memory rows of one CTA
 struct TsqrWork {
-    DevBuf<TsqrChunk> d_chunks, d_multi;
-    DevBuf<int4> d_roots;
-    DevBuf<double> Rbuf, Qs;
-    Stager st_chunks, st_multi, st_roots;
+    DevBuf<TsqrChunk> d_chunks, d_multi, d_multi2;
+    DevBuf<int4> d_roots, d_roots2;
+    DevBuf<double> Rbuf, Qs, R2, Qs2;
+    Stager st_chunks, st_multi, st_roots, st_multi2, st_roots2;
 };
 void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const int* m, int c, double* Y, int ldy,
                  double* Q, int ldq, TsqrWork& w, cudaStream_t s);

@@ -425,9 +425,11 @@ __global__ void __launch_bounds__(NT) tsqr_chunk_kernel(const TsqrChunk* __restr
     }
 }
 
-// stage 2: the stacked R factors of one panel per CTA -> Qs (nchunk*c x c, leading dimension nchunk*c)
+// stage 2: the stacked R factors of one panel per CTA -> Qs (nchunk*c x c, leading dimension nchunk*c);
+// with roots[].w >= 0 the combined R factor also goes to Rout block w (the next level of the tree)
 __global__ void __launch_bounds__(NT) tsqr_root_kernel(const int4* __restrict__ roots, int c,
-                                                        const double* __restrict__ Rbuf, double* __restrict__ Qs) {
+                                                        const double* __restrict__ Rbuf, double* __restrict__ Qs,
+                                                        double* __restrict__ Rout) {
     extern __shared__ double A[];
     __shared__ double sh[NW * MAXC];
     __shared__ double res[MAXC];
@@ -443,6 +445,11 @@ __global__ void __launch_bounds__(NT) tsqr_root_kernel(const int4* __restrict__ 
     }
     __syncthreads();
     house_qr_smem(A, h, c, tau, sh, res);
+    if (r.w >= 0)
+        for (int e = threadIdx.x; e < c * c; e += NT) {
+            const int i = e % c, k = e / c;
+            Rout[(int64_t)r.w * c * c + i + k * c] = (i <= k) ? A[i + k * h] : 0.0;
+        }
     __syncthreads();
     house_orgqr_smem(A, h, c, tau, sh, res);
     double* out = Qs + (int64_t)r.z * c * c;
@@ -487,31 +494,55 @@ void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const in
                  double* Q, int ldq, TsqrWork& w, cudaStream_t s) {
     if (count <= 0) return;
     if (c < 1 || c > MAXC) fail(H2_ERR_INVALID_ARG, "tsqr: panel width out of range");
-    std::vector<TsqrChunk> chunks, multi;
-    std::vector<int4> roots;
-    int64_t rcount = 0, qscount = 0;
+    // level 1: chunks of at most kTsqrMaxRows rows, one R each; groups of at most kTsqrMaxChunks
+    // chunks combine their stacked R factors in one root.  A panel with more than one group
+    // (taller than kTsqrMaxChunks * kTsqrMaxRows rows) adds level 2: a root over the groups' R
+    // factors, applied to every chunk after its group's factor.
+    std::vector<TsqrChunk> chunks, multi, multi2;
+    std::vector<int4> roots, roots2;
+    int64_t rcount = 0, qscount = 0, r2count = 0, qs2count = 0;
     int max_h = 0, max_root = 0;
     for (int p = 0; p < count; ++p) {
         if (m[p] <= c) fail(H2_ERR_INVALID_ARG, "tsqr: panel must have more rows than columns");
         int nch = std::max(1, std::min(kTsqrMaxChunks, m[p] / kTsqrChunk));
-        if ((m[p] + nch - 1) / nch > kTsqrMaxRows) fail(H2_ERR_INVALID_ARG, "tsqr: panel too tall");
-        const int64_t r0 = rcount, qs0 = qscount;
-        int row = 0;
-        for (int k = 0; k < nch; ++k) {
-            const int h = m[p] / nch + (k < m[p] % nch ? 1 : 0);
-            TsqrChunk d{y_off[p] + row, q_off[p] + row, h, nch > 1 ? (r0 + k) * c * c : -1,
-                        (qs0 * c * c) + (int64_t)k * c, nch * c};
-            chunks.push_back(d);
-            if (nch > 1) multi.push_back(d);
-            max_h = std::max(max_h, h);
-            row += h;
+        if ((m[p] + nch - 1) / nch > kTsqrMaxRows) nch = (m[p] + kTsqrMaxRows - 1) / kTsqrMaxRows;   // two levels
+        const int ngroups = (nch + kTsqrMaxChunks - 1) / kTsqrMaxChunks;
+        if (ngroups > kTsqrMaxChunks) fail(H2_ERR_INVALID_ARG, "tsqr: panel too tall");
+        const int64_t r2base = r2count, qs2base = qs2count;
+        int row = 0, k = 0;
+        for (int gi = 0; gi < ngroups; ++gi) {
+            // chunks spread evenly over the groups (every group of a two-level panel has > 1 chunk)
+            const int nchg = nch / ngroups + (gi < nch % ngroups ? 1 : 0);
+            const int64_t r0 = rcount, qs0 = qscount;
+            for (int kk = 0; kk < nchg; ++kk, ++k) {
+                const int h = m[p] / nch + (k < m[p] % nch ? 1 : 0);
+                TsqrChunk d{y_off[p] + row, q_off[p] + row, h, nch > 1 ? (r0 + kk) * c * c : -1,
+                            (qs0 * c * c) + (int64_t)kk * c, nchg * c};
+                chunks.push_back(d);
+                if (nchg > 1) multi.push_back(d);
+                if (ngroups > 1)
+                    multi2.push_back(TsqrChunk{0, q_off[p] + row, h, -1, qs2base * c * c + (int64_t)gi * c, ngroups * c});
+                max_h = std::max(max_h, h);
+                row += h;
+            }
+            if (nchg > 1) {
+                roots.push_back(make_int4((int)r0, nchg, (int)qs0, ngroups > 1 ? (int)(r2base + gi) : -1));
+                max_root = std::max(max_root, nchg * c);
+            } else if (ngroups > 1) {
+                fail(H2_ERR_INVALID_ARG, "tsqr: single-chunk group in a two-level panel");
+            }
+            if (nchg > 1) {
+                rcount += nchg;
+                qscount += nchg;
+            }
         }
-        if (nch > 1) {
-            roots.push_back(make_int4((int)r0, nch, (int)qs0, 0));
-            rcount += nch;
-            qscount += nch;
-            max_root = std::max(max_root, nch * c);
+        if (ngroups > 1) {
+            roots2.push_back(make_int4((int)r2base, ngroups, (int)qs2base, -1));
+            max_root = std::max(max_root, ngroups * c);
+            r2count += ngroups;
+            qs2count += ngroups;
         }
+        if (max_h > kTsqrMaxRows) fail(H2_ERR_INVALID_ARG, "tsqr: panel too tall");
     }
     upload(w.d_chunks, chunks, s, w.st_chunks);
     w.Rbuf.reserve((size_t)std::max<int64_t>(rcount * c * c, 1));
@@ -526,12 +557,23 @@ void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const in
     tsqr_chunk_kernel<<<(unsigned)chunks.size(), NT, smem1, s>>>(w.d_chunks.p, c, Y, ldy, Q, ldq, w.Rbuf.p);
     after_launch("tsqr_chunk");
     if (!roots.empty()) {
+        if (!roots2.empty()) w.R2.reserve((size_t)(r2count * c * c));
         upload(w.d_roots, roots, s, w.st_roots);
         upload(w.d_multi, multi, s, w.st_multi);
-        tsqr_root_kernel<<<(unsigned)roots.size(), NT, (size_t)max_root * c * sizeof(double), s>>>(w.d_roots.p, c,
-                                                                                                 w.Rbuf.p, w.Qs.p);
+        tsqr_root_kernel<<<(unsigned)roots.size(), NT, (size_t)max_root * c * sizeof(double), s>>>(
+            w.d_roots.p, c, w.Rbuf.p, w.Qs.p, w.R2.p);
         after_launch("tsqr_root");
         tsqr_apply_kernel<<<(unsigned)multi.size(), NT, 0, s>>>(w.d_multi.p, c, Q, ldq, w.Qs.p);
+        after_launch("tsqr_apply");
+    }
+    if (!roots2.empty()) {
+        w.Qs2.reserve((size_t)(qs2count * c * c));
+        upload(w.d_roots2, roots2, s, w.st_roots2);
+        upload(w.d_multi2, multi2, s, w.st_multi2);
+        tsqr_root_kernel<<<(unsigned)roots2.size(), NT, (size_t)max_root * c * sizeof(double), s>>>(
+            w.d_roots2.p, c, w.R2.p, w.Qs2.p, nullptr);
+        after_launch("tsqr_root");
+        tsqr_apply_kernel<<<(unsigned)multi2.size(), NT, 0, s>>>(w.d_multi2.p, c, Q, ldq, w.Qs2.p);
         after_launch("tsqr_apply");
     }
 }

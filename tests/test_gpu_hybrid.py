@@ -107,3 +107,31 @@ def test_hybrid_argument_errors(h2):
         with pytest.raises(h2.H2Error) as ei:
             h2.H2.build(gop, tree, 1e-6, h2.default_opts(global_rank=bad))
         assert ei.value.status == h2.H2_ERR_INVALID_ARG
+
+
+def test_hybrid_tall_global_panel_two_level_qr(h2):
+    """400 x 400 (N = 160,000 rows): the global basis is orthonormalised by the two-level TSQR
+    (more than 96 chunks of 1,536 rows).  The global piece alone must meet the tolerance against
+    the operator with fewer products than the plain construction."""
+    n, m = 400, 4000
+    mask = W.sensor_mask(n * n, m, 33)
+    gop = h2.HeatOperator(n, 0.01, 0.5, 0.01, mask)
+    tree = h2.Tree(W.grid_coords(n), 64, ADM_STRONG, 0.7)
+    base = dict(kmax=32, q0=32, b_inc=16, q_max=256, seed=7)
+    P = h2.H2.build(gop, tree, 1e-6, h2.default_opts(**base))
+    G = h2.H2.build(gop, tree, 1e-6, h2.default_opts(**base, global_rank=384))
+    st, sp = G.stats(), P.stats()
+    assert st["range_passed"][0] == 1 and st["samples"] < sp["samples"]
+    N = n * n
+
+    def op_apply(v):
+        vd = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+        yd = torch.empty_like(vd)
+        gop.apply(vd, yd, 1)
+        torch.cuda.synchronize()
+        return yd.cpu().numpy()
+
+    assert norm2_rel(gpu_apply(h2, G, N), op_apply, N, st["norm_est"]) < 1e-6
+    assert norm2_rel(gpu_apply(h2, G, N), gpu_apply(h2, P, N), N, st["norm_est"]) < 1e-6
+    G.close()
+    P.close()
