@@ -431,6 +431,49 @@ def hybrid_section(h2, torch, stream) -> dict:
     return out
 
 
+def advdiff_section(h2, torch, stream) -> dict:
+    """Second Hessian family (Section 4.3's study on a finite-difference stand-in): source
+    inversion in stationary advection-diffusion on a 128 x 128 grid, v = (x, y), c = 0.5,
+    sigma = 0.01, kappa in {1e-1, 1e-3}, 256 / 1024 / 4096 point observations (nested sets, one
+    adjoint solve per observation on the host: the operator's input data), constructed to
+    1e-4 in the 2-norm.  Products of the H^2 construction against those of a global low-rank
+    approximation (the hybrid's global piece with a budget above n_obs: the adaptive range
+    finder and its projection), with build seconds and the 2-norm error of each."""
+    from workloads import advdiff as AD
+    n, tol, leaf = 128, 1e-4, 64
+    N = n * n
+    out = {"workload": f"advdiff_n{n}", "tol": tol, "runs": {}}
+    tree = h2.Tree(AD.coords(n), leaf, h2.H2_ADM_STRONG, 0.7)
+    for kappa in (1e-1, 1e-3):
+        t0 = time.perf_counter()
+        Zall = AD.hessian_factor(n, kappa, 4096, 11)
+        t_solve = time.perf_counter() - t0
+        for n_obs in (256, 1024, 4096):
+            Zt = torch.from_numpy(np.ascontiguousarray(Zall[:, :n_obs].T)).cuda()
+            gop = h2.LowRankOperator(Zt, 1e4)
+            row = {"n_obs": n_obs, "kappa": kappa, "adjoint_solves_s": t_solve}
+            for key, budget in (("h2", 0), ("global_low_rank", n_obs + 256)):
+                opts = h2.default_opts(kmax=48, q0=32, b_inc=16, q_max=512, adaptive=1, seed=7, stream=stream,
+                                       global_rank=budget)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                G = h2.H2.build(gop, tree, tol, opts)
+                torch.cuda.synchronize()
+                bt = time.perf_counter() - t0
+                st = G.stats()
+                row[key] = {"samples": st["samples"], "op_calls": st["op_calls"], "build_s": bt,
+                            "max_rank": max(st["max_rank"]), "global_rank": st["range_probes"][0],
+                            "global_passed": st["range_passed"][0],
+                            "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, N, st["norm_est"], stream)}
+                G.close()
+            out["runs"][f"kappa{kappa:g}_obs{n_obs}"] = row
+            gop.close()
+            del Zt
+        del Zall
+        torch.cuda.empty_cache()
+    return out
+
+
 def inversion_section(h2, torch, stream) -> dict:
     """Appendix A on the regularised 128 x 128 heat Hessian (N = 16,384, the paper's inversion size):
     A = H~ + beta I with H~ the H^2 approximation (tol 1e-6, leaf 64, strong 0.7) and beta =
@@ -558,6 +601,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-inversion", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true")
+    ap.add_argument("--no-advdiff", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
     ap.add_argument("--precision-n", type=int, default=512, help="grid size of the precision section")
@@ -735,6 +779,10 @@ def main():
     if rank == 0 and not args.no_hybrid:
         hybrid = hybrid_section(h2, torch, stream)
 
+    advdiff = None
+    if rank == 0 and not args.no_advdiff:
+        advdiff = advdiff_section(h2, torch, stream)
+
     inversion = None
     if rank == 0 and not args.no_inversion:
         inversion = inversion_section(h2, torch, stream)
@@ -769,6 +817,8 @@ def main():
             line["learned_ranks"] = learned
         if hybrid is not None:
             line["hybrid"] = hybrid
+        if advdiff is not None:
+            line["advdiff"] = advdiff
         if inversion is not None:
             line["inversion"] = inversion
         if cpu is not None:

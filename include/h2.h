@@ -486,6 +486,16 @@ int h2_dense_op_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64
                       int64_t ldy, h2_stream_t stream);
 void h2_dense_op_destroy(void* ctx);
 
+/* Factored symmetric positive semidefinite operator Y = scale Z (Z^T X), Z an n x r device
+ * matrix (leading dimension ldz) that the caller keeps alive while the context is used; the
+ * misfit Hessian of a linear inverse problem with r point observations has this form with
+ * Z = A^-T O^T (one adjoint solve per observation) and scale = 1 / sigma^2 (Section 4.3's source
+ * inversion).  Workspace r x nrhs is owned by the context.  Errors: INVALID_ARG, CUDA, OOM. */
+int h2_lowrank_op_create(const double* Z_device, int64_t n, int64_t r, int64_t ldz, double scale, void** ctx_out);
+int h2_lowrank_op_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y,
+                        int64_t ldy, h2_stream_t stream);
+void h2_lowrank_op_destroy(void* ctx);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 
 const char* h2_error_string(int status);

@@ -10,7 +10,7 @@ Hessian-vector products), with numpy library primitives (QR, SVD, matmul)
 as steps.
 """
 from .h2 import H2Matrix, assemble, expand_dense, frobenius_norm, matvec, power_norm, storage_entries
-from .heat import DenseOperator, HeatHessian
+from .heat import DenseOperator, HeatHessian, LowRankOperator
 from .peel import PeelResult, TreeOperator, apply_pieces, global_lowrank, norm2_estimate, peel, psd_cholesky
 from .tree import ADM_STRONG, ADM_WEAK, ClusterTree, Partition
 

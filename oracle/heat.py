@@ -109,3 +109,24 @@ class DenseOperator:
         return self.A @ X
 
     __call__ = apply
+
+
+class LowRankOperator:
+    """Hessian-vector products scale Z (Z^T X) of a misfit Hessian given in factored form
+    (Z = A^-T O^T, scale = 1 / sigma^2: the source-inversion Hessian of Section 4.3)."""
+
+    def __init__(self, Z: np.ndarray, scale: float = 1.0):
+        self.Z = np.asarray(Z, dtype=np.float64)
+        self.scale = float(scale)
+        self.N = self.Z.shape[0]
+        self.matvecs = 0
+
+    def apply(self, X: np.ndarray) -> np.ndarray:
+        X = np.asarray(X, dtype=np.float64)
+        self.matvecs += 1 if X.ndim == 1 else X.shape[1]
+        return self.scale * (self.Z @ (self.Z.T @ X))
+
+    def dense(self) -> np.ndarray:
+        return self.scale * (self.Z @ self.Z.T)
+
+    __call__ = apply

@@ -218,7 +218,7 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
     tau = tol * res.norm_est
     res.tau = tau
     thr = tau / (10.0 * math.sqrt(2.0 / math.pi))
-    if global_rank > 0:
+    if global_rank > 0 and tree.L >= 1:   # a single leaf is one dense block: nothing to split off
         res.pieces[0] = global_lowrank(opt, N, thr, q0, b_inc, global_rank, adaptive, seed, res)
 
     covered = global_rank > 0 and res.global_passed == 1

@@ -157,6 +157,9 @@ _SIGS = {
     "h2_dense_op_create": (_I, [_P, _I64, _I64, ctypes.POINTER(_P)]),
     "h2_dense_op_apply": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P]),
     "h2_dense_op_destroy": (None, [_P]),
+    "h2_lowrank_op_create": (_I, [_P, _I64, _I64, _I64, ctypes.c_double, ctypes.POINTER(_P)]),
+    "h2_lowrank_op_apply": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P]),
+    "h2_lowrank_op_destroy": (None, [_P]),
     "h2_error_string": (ctypes.c_char_p, [_I]),
     "h2_last_error": (ctypes.c_char_p, []),
     "h2_launch_count": (_I64, []),
@@ -311,6 +314,35 @@ class HeatOperator:
     def close(self):
         if self.ctx:
             lib().h2_heat2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LowRankOperator:
+    """Y = scale Z (Z^T X) with a caller-owned FP64 device matrix Z (n x r, column-major: a torch
+    tensor of shape (r, n); kept alive by this object)."""
+
+    def __init__(self, Zt, scale: float = 1.0):
+        self.Z = Zt
+        r, n = Zt.shape
+        h = ctypes.c_void_p()
+        _check(lib().h2_lowrank_op_create(_ptr(Zt), n, r, n, float(scale), ctypes.byref(h)))
+        self.ctx = h
+        self.N = n
+        self.fn = ctypes.cast(lib().h2_lowrank_op_apply, ctypes.c_void_p)
+
+    def apply(self, X, Y, nrhs: int, stream=None, ldx: int | None = None, ldy: int | None = None):
+        _check(lib().h2_lowrank_op_apply(self.ctx, self.N, nrhs, _ptr(X), ldx or self.N, _ptr(Y), ldy or self.N,
+                                         _stream_ptr(stream)))
+
+    def close(self):
+        if self.ctx:
+            lib().h2_lowrank_op_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -87,6 +87,16 @@ struct DenseOp {
     GemmBatch gb;
 };
 
+// Factored symmetric operator Y = scale Z (Z^T X): a misfit Hessian A^-T O^T O A^-1 / sigma^2
+// given Z = A^-T O^T (one adjoint solve per observation).
+struct LowRankOp {
+    const double* Z = nullptr;
+    int64_t n = 0, r = 0, ldz = 0;
+    double scale = 1.0;
+    DevBuf<double> T;
+    GemmBatch gb;
+};
+
 }  // namespace
 
 }  // namespace h2
@@ -217,6 +227,50 @@ void h2_dense_op_destroy(void* ctx) {
     if (ctx) {
         cudaDeviceSynchronize();
         delete static_cast<DenseOp*>(ctx);
+    }
+}
+
+int h2_lowrank_op_create(const double* Z, int64_t n, int64_t r, int64_t ldz, double scale, void** ctx_out) {
+    if (!ctx_out) return H2_ERR_INVALID_ARG;
+    *ctx_out = nullptr;
+    if (!Z || n < 1 || r < 1 || ldz < n || n >= (1 << 22) || r >= (1 << 22) || !std::isfinite(scale))
+        return H2_ERR_INVALID_ARG;
+    auto* D = new (std::nothrow) LowRankOp();
+    if (!D) return H2_ERR_OOM;
+    D->Z = Z;
+    D->n = n;
+    D->r = r;
+    D->ldz = ldz;
+    D->scale = scale;
+    *ctx_out = D;
+    return H2_OK;
+}
+
+int h2_lowrank_op_apply(void* ctx, int64_t n, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                        h2_stream_t stream) {
+    auto* D = static_cast<LowRankOp*>(ctx);
+    if (!D || n != D->n || nrhs < 0 || ldx < n || ldy < n) return H2_ERR_INVALID_ARG;
+    if (nrhs == 0) return H2_OK;
+    if (!X || !Y) return H2_ERR_INVALID_ARG;
+    try {
+        const cudaStream_t s = (cudaStream_t)stream;
+        D->T.reserve((size_t)D->r * nrhs);
+        D->gb.add(D->Z, (int)D->ldz, 1, X, (int)ldx, 0, D->T.p, (int)D->r, (int)D->r, (int)nrhs, (int)n, 1.0, 0.0);
+        D->gb.run(s);
+        D->gb.add(D->Z, (int)D->ldz, 0, D->T.p, (int)D->r, 0, Y, (int)ldy, (int)n, (int)nrhs, (int)D->r, D->scale, 0.0);
+        D->gb.run(s);
+        return H2_OK;
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        return H2_ERR_CUDA;
+    }
+}
+
+void h2_lowrank_op_destroy(void* ctx) {
+    if (ctx) {
+        cudaDeviceSynchronize();
+        delete static_cast<LowRankOp*>(ctx);
     }
 }
 

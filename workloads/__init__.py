@@ -4,7 +4,9 @@ This module holds data only: grid coordinates, sensor sets, right-hand sides
 and the parameter table of the synthetic heat-equation Hessians.  It contains
 none of the method's arithmetic (no operator, no tree, no sampling), so that
 the oracle and the CUDA path can both consume the same inputs without sharing
-any computational code.
+any computational code.  `workloads.advdiff` generates the second family's
+input data (the factor of an advection-diffusion misfit Hessian, from a sparse
+solve of its PDE): the operator's data, again none of the hierarchical method.
 
 The workload stands in for the PDE-constrained Hessians of the paper
 (Section 4): a 2-D initial-condition inversion for the heat equation on the
