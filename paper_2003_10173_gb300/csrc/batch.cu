@@ -173,7 +173,7 @@ void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* co
         for (int k = 0; k < kSide; ++k) H2_CUDA(cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
         for (size_t i = 0; i < b->hs.size(); ++i) {
             h2_handle_s* h = b->hs[i];
-            tc_phase(h, mode, ph, X[i], ldx[i], (float*)Y[i], ldy[i], nrhs, h->ws.f32.p, h->plan.ws_rows,
+            tc_phase(h, mode, ph, X[i], ldx[i], (float*)Y[i], ldy[i], nrhs, h->ws.f32.p, h->plan.ws_rows, 0,
                      b->side[i % kSide]);
         }
         for (int k = 0; k < kSide; ++k) {

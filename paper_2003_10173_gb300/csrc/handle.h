@@ -214,11 +214,13 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
                         int mode, cudaStream_t s);
 bool tc_supported(const h2_handle_s* h);
 void tc_reserve(h2_handle_s* h, int mode, int nrhs);
+// ws_rmaj: the coefficient workspace is right-hand-side-major (ws[row * ws_ld + rhs]) instead of
+// coefficient-major (ws[row + rhs * ws_ld]).
 void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs,
-              float* ws, int64_t ws_ld, cudaStream_t s);
+              float* ws, int64_t ws_ld, int ws_rmaj, cudaStream_t s);
 void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s);
 void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
-               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
+               int64_t ws_ld, int ws_rmaj, cudaStream_t s, const std::function<void(int)>& sweeps,
                const std::function<void(int, std::function<void()>)>& timed);
 int tc_device_error(h2_handle_s* h);
 }  // namespace h2

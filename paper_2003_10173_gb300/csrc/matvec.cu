@@ -194,6 +194,82 @@ __global__ void __launch_bounds__(TR_RC) mv_transfer_kernel(const MvOut* __restr
     }
 }
 
+// The same transfer stages on a right-hand-side-major workspace (ws[row * ld + rhs], the
+// tensor-core path's layout), for outputs with at most two items (a parent's two children in the
+// upsweep, the parent in the downsweep): the item matrices go to shared memory once; each thread
+// keeps its right-hand side's output column in registers and reads its inputs straight from
+// global memory (consecutive threads, consecutive addresses); many resident warps hide their
+// latency.  When accumulating, old output values are loaded eight at a time before their stores.
+template <class TS, int KB>
+__global__ void __launch_bounds__(TR_RC) mv_transfer_rm_kernel(const MvOut* __restrict__ outs,
+                                                               const MvItem* __restrict__ items,
+                                                               const TS* __restrict__ fac, float* __restrict__ ws,
+                                                               int64_t ld, int nrhs, int accumulate) {
+    __shared__ __align__(16) float Ms[2][KB * KB];   // item matrices, [col j][row i], zero beyond the rows
+    const MvOut o = outs[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int r = blockIdx.y * TR_RC + tid;
+    const bool live = r < nrhs;
+    const int rows = o.rows;
+    const int nit = o.end - o.beg;   // 1 or 2 (host-checked)
+    float acc[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = 0.f;
+    for (int q = 0; q < nit; ++q) {
+        const MvItem m = items[o.beg + q];
+        const bool tr = (m.trans & 1) != 0;
+        const TS* M = fac + m.m_off;
+        for (int e = tid; e < KB * m.cols; e += TR_RC) {
+            int i, j;
+            if (!tr) { i = e % KB; j = e / KB; }
+            else     { j = e % m.cols; i = e / m.cols; }
+            float v = 0.f;
+            if (i < rows) v = cvt<float>(tr ? M[j + (int64_t)i * m.ldm] : M[i + (int64_t)j * m.ldm]);
+            Ms[q][j * KB + i] = v;
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    for (int q = 0; q < nit; ++q) {
+        const MvItem m = items[o.beg + q];
+        const float* Mq = Ms[q];
+        const float* x = ws + m.in_off * ld + r;
+#pragma unroll 1
+        for (int j = 0; j < m.cols; ++j) {
+            const float xv = x[(int64_t)j * ld];
+            const float4* mj = reinterpret_cast<const float4*>(Mq + j * KB);
+#pragma unroll
+            for (int i4 = 0; i4 < KB / 4; ++i4) {
+                const float4 w = mj[i4];
+                acc[4 * i4 + 0] = fmaf(w.x, xv, acc[4 * i4 + 0]);
+                acc[4 * i4 + 1] = fmaf(w.y, xv, acc[4 * i4 + 1]);
+                acc[4 * i4 + 2] = fmaf(w.z, xv, acc[4 * i4 + 2]);
+                acc[4 * i4 + 3] = fmaf(w.w, xv, acc[4 * i4 + 3]);
+            }
+        }
+    }
+    float* y = ws + o.out_off * ld + r;
+#pragma unroll
+    for (int i0 = 0; i0 < KB; i0 += 8) {
+        if (i0 >= rows) break;
+        // eight old values in flight together, then their stores
+        float old[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) old[u] = (accumulate && i0 + u < rows) ? y[(int64_t)(i0 + u) * ld] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + u < rows) y[(int64_t)(i0 + u) * ld] = acc[i0 + u] + old[u];
+    }
+}
+
+template <class TS, int KB>
+void launch_transfer_rm(const MvStage& st, const TS* fac, float* ws, int64_t ld, int nrhs, cudaStream_t s) {
+    dim3 grid((unsigned)st.outs.size(), (unsigned)((nrhs + TR_RC - 1) / TR_RC));
+    mv_transfer_rm_kernel<TS, KB><<<grid, TR_RC, 0, s>>>(st.d_outs.p, st.d_items.p, fac, ws, ld, nrhs,
+                                                         st.accumulate);
+    after_launch("mv_transfer_rm");
+}
+
 template <class TS, class TA, int KB>
 void launch_transfer(const MvStage& st, const TS* fac, TA* ws, int64_t ws_ld, int nrhs, cudaStream_t s) {
     const size_t smem = (size_t)(KB * KB + TR_RC * (KB + 1)) * sizeof(TA);
@@ -591,15 +667,30 @@ void run_tc(h2_handle_s* h, int mode, const TS* fac, float* ws, const TX* X, int
         H2_CUDA(cudaEventRecord(b, s));
         h->ev_used.push_back({kind, {a, b}});
     };
+    // right-hand-side-major coefficient workspace (ws[row * nrhs + rhs]) when the sweeps' blocks fit
+    // the register kernel, else the coefficient-major layout of the SIMT stage kernels
+    int kb = 0;
+    for (const MvStage& st : P.stages)
+        if (st.kind == H2_STAGE_UP || st.kind == H2_STAGE_DOWN) kb = std::max({kb, st.max_rows, st.max_cols});
+    bool rmaj = kb <= 64 && (nrhs + TR_RC - 1) / TR_RC <= 65535;
+    for (const MvStage& st : P.stages)
+        if (st.kind == H2_STAGE_UP || st.kind == H2_STAGE_DOWN)
+            for (const MvOut& o : st.outs) rmaj = rmaj && o.end - o.beg <= 2;
+    const int64_t ws_ld = rmaj ? (int64_t)nrhs : P.ws_rows;
     std::function<void(int)> sweeps = [&](int down) {
         for (const MvStage& st : P.stages) {
-            if (st.kind != (down ? H2_STAGE_DOWN : H2_STAGE_UP)) continue;
+            if (st.kind != (down ? H2_STAGE_DOWN : H2_STAGE_UP) || st.outs.empty()) continue;
             timed(st.kind, [&] {
-                launch_stage<TS, TX, float, float>(st, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+                if (!rmaj)
+                    launch_stage<TS, TX, float, float>(st, fac, ws, P.ws_rows, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+                else if (kb <= 32)
+                    launch_transfer_rm<TS, 32>(st, fac, ws, ws_ld, nrhs, s);
+                else
+                    launch_transfer_rm<TS, 64>(st, fac, ws, ws_ld, nrhs, s);
             });
         }
     };
-    tc_matvec(h, mode, X, ldx, Y, ldy, nrhs, ws, P.ws_rows, s, sweeps, timed);
+    tc_matvec(h, mode, X, ldx, Y, ldy, nrhs, ws, ws_ld, rmaj ? 1 : 0, s, sweeps, timed);
 }
 
 }  // namespace

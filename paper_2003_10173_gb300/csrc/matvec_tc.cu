@@ -30,7 +30,6 @@ namespace h2 {
 namespace {
 
 constexpr int TC_M = 128;      // right-hand sides per CTA (MMA M)
-constexpr int TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;   // about one second
 constexpr int TC_ITEM_CACHE = 256;                   // item descriptors staged in shared memory
@@ -268,7 +267,7 @@ template <int EB>
 __global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
     const TcGroup* __restrict__ groups, const TcOut* __restrict__ outs, const TcItem* __restrict__ items,
     const unsigned char* __restrict__ W, const unsigned char* __restrict__ opnd, float* __restrict__ ws,
-    int64_t ws_ld, int nrhs, int tmem_cols, int* __restrict__ err) {
+    int64_t ws_ld, int ws_rmaj, int nrhs, int tmem_cols, int* __restrict__ err) {
     using Tr = TcTraits<EB>;
     using C = TcCfg<EB>;
     constexpr int S = C::STAGES;
@@ -387,15 +386,17 @@ __global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
     __syncthreads();
     const bool ok = okflag != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // coefficient outputs: each thread stores its right-hand side's row of every block
-    // (consecutive workspace rows) straight from the tensor-memory loads
+    // coefficient outputs: each thread stores its right-hand side's entries of every block
+    // straight from the tensor-memory loads (right-hand-side-major workspace: consecutive
+    // threads write consecutive addresses; coefficient-major: each thread a contiguous run)
     const int r = warp * 32 + (tid & 31);
     const bool live = r0 + r < nrhs;
+    const int64_t rstep = ws_rmaj ? ws_ld : 1;
     int col = 0;
     for (int j = 0; j < nout && ok; ++j) {
         const TcOut o = souts[j];
         const bool any = o.end > o.beg;
-        float* dst = ws + o.out_off + (int64_t)(r0 + r) * ws_ld;
+        float* dst = ws_rmaj ? ws + o.out_off * ws_ld + (r0 + r) : ws + o.out_off + (int64_t)(r0 + r) * ws_ld;
         for (int c0 = 0; c0 < o.n; c0 += 16) {
             uint32_t v[16];
             if (any) {
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
             if (live)
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    if (c0 + q < o.rows) dst[c0 + q] = __uint_as_float(v[q]);
+                    if (c0 + q < o.rows) dst[(int64_t)(c0 + q) * rstep] = __uint_as_float(v[q]);
         }
         col += o.n;
     }
@@ -544,8 +545,9 @@ __global__ void __launch_bounds__(PK_THREADS) tc_pack_x_kernel(const TX* __restr
 template <int EB>
 __global__ void __launch_bounds__(PK_THREADS) tc_pack_coef_kernel(const int4* __restrict__ boxes,
                                                                   const float* __restrict__ ws, int64_t ws_ld,
-                                                                  const int64_t* __restrict__ src_row, int nrhs,
-                                                                  unsigned char* __restrict__ opnd, int64_t lo_off) {
+                                                                  int ws_rmaj, const int64_t* __restrict__ src_row,
+                                                                  int nrhs, unsigned char* __restrict__ opnd,
+                                                                  int64_t lo_off) {
     __shared__ __align__(16) float tile[TC_M][PK_KS + PK_PAD];
     const int b = blockIdx.x, rt = blockIdx.y, nrt = gridDim.y;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -556,10 +558,19 @@ __global__ void __launch_bounds__(PK_THREADS) tc_pack_coef_kernel(const int4* __
     unsigned char* dst = opnd + ((int64_t)d.x * nrt * TC_M + (int64_t)rt * TC_M * kp) * EB;
     for (int ks0 = 0; ks0 < kp; ks0 += PK_KS) {
         const int w = min(PK_KS, kp - ks0);
-        for (int i = tx; i < w; i += 32) {
-            const bool valid = ks0 + i < d.y;
-            for (int rr = ty; rr < TC_M; rr += PK_THREADS / 32)
-                tile[rr][i] = (valid && r0 + rr < nrhs) ? ws[s0 + ks0 + i + (int64_t)(r0 + rr) * ws_ld] : 0.f;
+        if (ws_rmaj) {
+            // right-hand-side-major workspace: lanes run along the right-hand sides
+            for (int i = ty; i < w; i += PK_THREADS / 32) {
+                const bool valid = ks0 + i < d.y;
+                const float* src = ws + (s0 + ks0 + i) * ws_ld + r0;
+                for (int rr = tx; rr < TC_M; rr += 32) tile[rr][i] = (valid && r0 + rr < nrhs) ? src[rr] : 0.f;
+            }
+        } else {
+            for (int i = tx; i < w; i += 32) {
+                const bool valid = ks0 + i < d.y;
+                for (int rr = ty; rr < TC_M; rr += PK_THREADS / 32)
+                    tile[rr][i] = (valid && r0 + rr < nrhs) ? ws[s0 + ks0 + i + (int64_t)(r0 + rr) * ws_ld] : 0.f;
+            }
         }
         __syncthreads();
         pack_store_slice<EB>(tile, kp, ks0, w, dst, lo_off);
@@ -571,7 +582,7 @@ template <int EB>
 void launch_products(const TcStage& st, const TcGroup* d_groups, const TcOut* d_outs, const TcItem* d_items,
                      const unsigned char* W,
                      const unsigned char* opnd, const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld,
-                     int nrhs, int* err, cudaStream_t s) {
+                     int ws_rmaj, int nrhs, int* err, cudaStream_t s) {
     if (st.outs.empty()) return;
     const size_t smem = std::max((size_t)TcCfg<EB>::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
     static std::once_flag attr;
@@ -586,7 +597,7 @@ void launch_products(const TcStage& st, const TcGroup* d_groups, const TcOut* d_
         after_launch("tc_products");
     } else {
         tc_group_kernel<EB><<<dim3(nrt, (unsigned)st.groups.size()), TC_THREADS, smem, s>>>(
-            d_groups, d_outs, d_items, W, opnd, ws, ws_ld, nrhs, st.tmem_cols, err);
+            d_groups, d_outs, d_items, W, opnd, ws, ws_ld, ws_rmaj, nrhs, st.tmem_cols, err);
         after_launch("tc_group");
     }
 }
@@ -845,7 +856,7 @@ void tc_reserve(h2_handle_s* h, int mode, int nrhs) {
 // xh and computes the couplings into yh, 2 packs yh and computes Y = U yh + near field.  The
 // transfer sweeps between the phases run on the SIMT path.
 void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs,
-              float* ws, int64_t ws_ld, cudaStream_t s) {
+              float* ws, int64_t ws_ld, int ws_rmaj, cudaStream_t s) {
     TcPlan& P = h->tc;
     const int EB = (mode == H2_BF16) ? 2 : 4;
     const bool split = mode == H2_TF32X3;
@@ -859,22 +870,23 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
         if (st.outs.empty()) return;
         if (EB == 2)
             launch_products<2>(st, st.d_groups.p, st.d_outs.p, st.d_items16.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws,
-                               ws_ld, nrhs, P.d_err.p, s);
+                               ws_ld, ws_rmaj, nrhs, P.d_err.p, s);
         else if (split)
             launch_products<4>(st, st.d_groups32x3.p, st.d_outs32x3.p, st.d_items32x3.p, W, P.opnd.p, h->d_perm.p, Y,
-                               ldy, ws, ws_ld, nrhs, P.d_err.p, s);
+                               ldy, ws, ws_ld, ws_rmaj, nrhs, P.d_err.p, s);
         else
             launch_products<4>(st, st.d_groups.p, st.d_outs.p, st.d_items32.p, W, P.opnd.p, h->d_perm.p, Y, ldy, ws,
-                               ws_ld, nrhs, P.d_err.p, s);
+                               ws_ld, ws_rmaj, nrhs, P.d_err.p, s);
     };
     if (nrt > 65535) fail(H2_ERR_INVALID_ARG, "h2_matvec: more than 65535 tiles of 128 right-hand sides");
     auto pack_coef = [&](const std::vector<int4>& bx, const DevBuf<int4>& dbx, const DevBuf<int64_t>& dsrc) {
         if (bx.empty()) return;
         const dim3 g((unsigned)bx.size(), (unsigned)nrt);
         if (EB == 2)
-            tc_pack_coef_kernel<2><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, P.opnd.p, 0);
+            tc_pack_coef_kernel<2><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, ws_rmaj, dsrc.p, nrhs, P.opnd.p, 0);
         else
-            tc_pack_coef_kernel<4><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, dsrc.p, nrhs, P.opnd.p, lo_off);
+            tc_pack_coef_kernel<4><<<g, PK_THREADS, 0, s>>>(dbx.p, ws, ws_ld, ws_rmaj, dsrc.p, nrhs, P.opnd.p,
+                                                            lo_off);
         after_launch("tc_pack_coef");
     };
     P.cur_eb = EB;
@@ -899,13 +911,13 @@ void tc_phase(h2_handle_s* h, int mode, int phase, const void* X, int64_t ldx, f
 }
 
 void tc_matvec(h2_handle_s* h, int mode, const void* X, int64_t ldx, float* Y, int64_t ldy, int nrhs, float* ws,
-               int64_t ws_ld, cudaStream_t s, const std::function<void(int)>& sweeps,
+               int64_t ws_ld, int ws_rmaj, cudaStream_t s, const std::function<void(int)>& sweeps,
                const std::function<void(int, std::function<void()>)>& timed) {
-    timed(H2_STAGE_LEAF_UP, [&] { tc_phase(h, mode, 0, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
+    timed(H2_STAGE_LEAF_UP, [&] { tc_phase(h, mode, 0, X, ldx, Y, ldy, nrhs, ws, ws_ld, ws_rmaj, s); });
     sweeps(0);   // transfer upsweep (SIMT)
-    timed(H2_STAGE_COUPLE, [&] { tc_phase(h, mode, 1, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
+    timed(H2_STAGE_COUPLE, [&] { tc_phase(h, mode, 1, X, ldx, Y, ldy, nrhs, ws, ws_ld, ws_rmaj, s); });
     sweeps(1);   // transfer downsweep (SIMT)
-    timed(H2_STAGE_NEAR, [&] { tc_phase(h, mode, 2, X, ldx, Y, ldy, nrhs, ws, ws_ld, s); });
+    timed(H2_STAGE_NEAR, [&] { tc_phase(h, mode, 2, X, ldx, Y, ldy, nrhs, ws, ws_ld, ws_rmaj, s); });
 }
 
 int tc_device_error(h2_handle_s* h) {
