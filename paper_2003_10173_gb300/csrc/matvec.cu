@@ -234,17 +234,24 @@ __global__ void __launch_bounds__(TR_RC) mv_transfer_rm_kernel(const MvOut* __re
         const MvItem m = items[o.beg + q];
         const float* Mq = Ms[q];
         const float* x = ws + m.in_off * ld + r;
+        // four input entries in flight per step
 #pragma unroll 1
-        for (int j = 0; j < m.cols; ++j) {
-            const float xv = x[(int64_t)j * ld];
-            const float4* mj = reinterpret_cast<const float4*>(Mq + j * KB);
+        for (int j0 = 0; j0 < m.cols; j0 += 4) {
+            float xv[4];
 #pragma unroll
-            for (int i4 = 0; i4 < KB / 4; ++i4) {
-                const float4 w = mj[i4];
-                acc[4 * i4 + 0] = fmaf(w.x, xv, acc[4 * i4 + 0]);
-                acc[4 * i4 + 1] = fmaf(w.y, xv, acc[4 * i4 + 1]);
-                acc[4 * i4 + 2] = fmaf(w.z, xv, acc[4 * i4 + 2]);
-                acc[4 * i4 + 3] = fmaf(w.w, xv, acc[4 * i4 + 3]);
+            for (int u = 0; u < 4; ++u) xv[u] = (j0 + u < m.cols) ? x[(int64_t)(j0 + u) * ld] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (j0 + u >= m.cols) break;
+                const float4* mj = reinterpret_cast<const float4*>(Mq + (j0 + u) * KB);
+#pragma unroll
+                for (int i4 = 0; i4 < KB / 4; ++i4) {
+                    const float4 w = mj[i4];
+                    acc[4 * i4 + 0] = fmaf(w.x, xv[u], acc[4 * i4 + 0]);
+                    acc[4 * i4 + 1] = fmaf(w.y, xv[u], acc[4 * i4 + 1]);
+                    acc[4 * i4 + 2] = fmaf(w.z, xv[u], acc[4 * i4 + 2]);
+                    acc[4 * i4 + 3] = fmaf(w.w, xv[u], acc[4 * i4 + 3]);
+                }
             }
         }
     }
