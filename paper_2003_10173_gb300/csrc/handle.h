@@ -111,6 +111,7 @@ struct TcStage {
     std::vector<TcGroup> groups;
     DevBuf<TcGroup> d_groups, d_groups32x3;
     int tmem_cols = 32;            // tensor-memory columns per CTA (power of two >= the widest group)
+    int kmax_item = 0, nmax_out = 0;   // largest item K and output N (choose the operand ring's tiles)
     DevBuf<TcOut> d_outs, d_outs32x3;
     DevBuf<TcItem> d_items16, d_items32, d_items32x3;   // split TF32: three items per product
 };

@@ -103,13 +103,22 @@ constexpr int TC_GCOLS = 128;   // tensor-memory columns of a CTA: its outputs s
 constexpr int TC_GMAX = 8;      // outputs per CTA
 constexpr int TC_GROUP_ITEMS = 84;   // items per CTA group (x3 for split TF32 <= TC_ITEM_CACHE)
 
-template <int EB>
+// Operand ring: S stages, each an A tile (128 x KM) and a B tile (NM x KM).  64 x 64 tiles in two
+// stages for the leaf upsweep and the near field; items of at most 48 x 48 (the couplings) in
+// three stages of the same total size, so that more copies are in flight per CTA.
+template <int EB, int KM = TC_KMAX, int NM = TC_NMAX, int S = 2>
 struct TcCfg {
-    static constexpr int STAGES = 2;
-    static constexpr int A_BYTES = TC_M * TC_KMAX * EB;
-    static constexpr int B_BYTES = TC_NMAX * TC_KMAX * EB;
+    static constexpr int STAGES = S;
+    static constexpr int KMAX = KM, NMAX = NM;
+    static constexpr int A_BYTES = TC_M * KM * EB;
+    static constexpr int B_BYTES = NM * KM * EB;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES;
+    // item descriptors cached in shared memory by the grouped kernel: a group holds at most
+    // TC_GROUP_ITEMS items, three times that in split TF32; the smaller BF16 cache keeps four
+    // three-stage CTAs per SM
+    static constexpr int CACHE = (EB == 2) ? 96 : 256;
+    static_assert(STAGE_BYTES % 128 == 0, "stages must stay 128-byte aligned");
 };
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -263,19 +272,18 @@ __global__ void __launch_bounds__(TC_THREADS) tc_products_kernel(
 // Several consecutive coefficient outputs per CTA (leaf upsweep, couplings): one operand ring
 // across all their items, each output accumulating in its own columns of tensor memory, stored
 // to the workspace straight from the tensor-memory loads.
-template <int EB>
+template <int EB, class C>
 __global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
     const TcGroup* __restrict__ groups, const TcOut* __restrict__ outs, const TcItem* __restrict__ items,
     const unsigned char* __restrict__ W, const unsigned char* __restrict__ opnd, float* __restrict__ ws,
     int64_t ws_ld, int ws_rmaj, int nrhs, int tmem_cols, int* __restrict__ err) {
     using Tr = TcTraits<EB>;
-    using C = TcCfg<EB>;
     constexpr int S = C::STAGES;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ uint32_t tmem_slot;
     __shared__ int okflag, prod_issued, cons_done;
-    __shared__ TcItem sitems[TC_ITEM_CACHE];
+    __shared__ TcItem sitems[C::CACHE];
     __shared__ TcOut souts[TC_GMAX];
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -288,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_group_kernel(
     // the group's outputs and item descriptors, staged once in shared memory (off the producer's
     // critical path)
     if (tid < nout) souts[tid] = outs[g.obeg + tid];
-    const bool cached = nitem <= TC_ITEM_CACHE;
+    const bool cached = nitem <= C::CACHE;
     if (cached)
         for (int i = tid; i < nitem; i += TC_THREADS) sitems[i] = items[ibeg + i];
     if (tid == 0) {
@@ -584,19 +592,28 @@ void launch_products(const TcStage& st, const TcGroup* d_groups, const TcOut* d_
                      const unsigned char* opnd, const int32_t* perm, float* Y, int64_t ldy, float* ws, int64_t ws_ld,
                      int ws_rmaj, int nrhs, int* err, cudaStream_t s) {
     if (st.outs.empty()) return;
-    const size_t smem = std::max((size_t)TcCfg<EB>::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
+    using Big = TcCfg<EB>;
+    using Small = TcCfg<EB, 48, 48, 3>;
+    const size_t smem = std::max((size_t)Big::SMEM, (size_t)TC_M * (TC_NMAX + 1) * sizeof(float));
     static std::once_flag attr;
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(tc_products_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        H2_CUDA(cudaFuncSetAttribute(tc_group_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        H2_CUDA(cudaFuncSetAttribute(tc_group_kernel<EB, Big>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Big::SMEM));
+        H2_CUDA(cudaFuncSetAttribute(tc_group_kernel<EB, Small>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Small::SMEM));
     });
     const unsigned nrt = (unsigned)((nrhs + TC_M - 1) / TC_M);
     if (st.outs[0].to_y) {
         tc_products_kernel<EB><<<dim3(nrt, (unsigned)st.outs.size()), TC_THREADS, smem, s>>>(
             d_outs, d_items, W, opnd, perm, Y, ldy, ws, ws_ld, nrhs, err);
         after_launch("tc_products");
+    } else if (st.kmax_item <= Small::KMAX && st.nmax_out <= Small::NMAX) {
+        tc_group_kernel<EB, Small><<<dim3(nrt, (unsigned)st.groups.size()), TC_THREADS, Small::SMEM, s>>>(
+            d_groups, d_outs, d_items, W, opnd, ws, ws_ld, ws_rmaj, nrhs, st.tmem_cols, err);
+        after_launch("tc_group");
     } else {
-        tc_group_kernel<EB><<<dim3(nrt, (unsigned)st.groups.size()), TC_THREADS, smem, s>>>(
+        tc_group_kernel<EB, Big><<<dim3(nrt, (unsigned)st.groups.size()), TC_THREADS, Big::SMEM, s>>>(
             d_groups, d_outs, d_items, W, opnd, ws, ws_ld, ws_rmaj, nrhs, st.tmem_cols, err);
         after_launch("tc_group");
     }
@@ -737,6 +754,12 @@ void tc_prepare(h2_handle_s* h, int want_bf16, int want_tf32, cudaStream_t s) {
     for (TcStage* st : {&P.leaf_up, &P.couple, &P.near})
         for (auto& o : st->outs)
             if (o.n > TC_NMAX || o.n % 16) fail(H2_ERR_INVALID_ARG, "tensor-core plan: output rows out of range");
+    for (TcStage* st : {&P.leaf_up, &P.couple, &P.near}) {
+        st->kmax_item = 0;
+        st->nmax_out = 0;
+        for (const auto& it : st->items) st->kmax_item = std::max(st->kmax_item, it.k);
+        for (const auto& o : st->outs) st->nmax_out = std::max(st->nmax_out, o.n);
+    }
     // CTA groups: consecutive outputs (neighbouring boxes in tree order) side by side in tensor
     // memory, one operand ring across all their items; coefficient outputs only (the near-field
     // outputs go through the permutation and keep one CTA each), and at most TC_GROUP_ITEMS items
