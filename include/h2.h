@@ -503,6 +503,13 @@ const char* h2_error_string(int status);
 const char* h2_last_error(void);
 /* Number of kernels the library has launched in this process. */
 int64_t h2_launch_count(void);
+/* Device bytes the library currently holds (all handles, trees, workspaces and cached blocks of
+ * running constructions).  No CUDA call. */
+int64_t h2_device_bytes(void);
+/* Cap on the library's device bytes (<= 0 removes it): an allocation that would go above it
+ * fails with H2_ERR_OOM as if the device were full, for testing allocation-failure paths.
+ * Affects all threads; returns H2_OK. */
+int h2_set_device_limit(int64_t bytes);
 /* Library version string. */
 const char* h2_version(void);
 

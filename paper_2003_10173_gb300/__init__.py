@@ -163,6 +163,8 @@ _SIGS = {
     "h2_error_string": (ctypes.c_char_p, [_I]),
     "h2_last_error": (ctypes.c_char_p, []),
     "h2_launch_count": (_I64, []),
+    "h2_device_bytes": (_I64, []),
+    "h2_set_device_limit": (_I, [_I64]),
     "h2_version": (ctypes.c_char_p, []),
 }
 
@@ -648,6 +650,16 @@ def rank_targets(stats: dict):
 
 def launch_count() -> int:
     return int(lib().h2_launch_count())
+
+
+def device_bytes() -> int:
+    """Device bytes the library currently holds."""
+    return int(lib().h2_device_bytes())
+
+
+def set_device_limit(nbytes: int) -> None:
+    """Cap the library's device bytes (<= 0 removes the cap); allocations above it fail with OOM."""
+    _check(lib().h2_set_device_limit(int(nbytes)))
 
 
 def version() -> str:

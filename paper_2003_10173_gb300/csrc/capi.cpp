@@ -645,6 +645,13 @@ const char* h2_last_error(void) { return g_last_error.c_str(); }
 
 int64_t h2_launch_count(void) { return h2::g_launches.load(); }
 
+int64_t h2_device_bytes(void) { return h2::dev_live_bytes(); }
+
+int h2_set_device_limit(int64_t bytes) {
+    h2::dev_alloc_limit(bytes);
+    return H2_OK;
+}
+
 const char* h2_version(void) { return "h2hess 0.1 (sm_103a)"; }
 
 }  // extern "C"

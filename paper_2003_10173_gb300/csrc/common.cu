@@ -1,6 +1,7 @@
 // Error handling, launch accounting and memory helpers.
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <unordered_map>
 
 #include "common.h"
@@ -62,14 +63,39 @@ size_t size_class(size_t b) {
     return (b + g - 1) / g * g;
 }
 
+// Accounting of the library's device blocks (all threads): live bytes, and an optional cap that
+// turns any allocation above it into H2_ERR_OOM (allocation-failure tests without exhausting the
+// device).
+std::mutex g_dev_mu;
+std::unordered_map<void*, size_t> g_dev_sizes;
+int64_t g_dev_live = 0, g_dev_limit = 0;
+
 void* raw_dev_alloc(size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_dev_limit > 0 && g_dev_live + (int64_t)bytes > g_dev_limit)
+        fail(H2_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes above the library's limit of " +
+                             std::to_string(g_dev_limit) + " bytes");
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(H2_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
     }
+    g_dev_sizes[p] = bytes;
+    g_dev_live += (int64_t)bytes;
     return p;
+}
+
+void raw_dev_free(void* p) {
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        auto it = g_dev_sizes.find(p);
+        if (it != g_dev_sizes.end()) {
+            g_dev_live -= (int64_t)it->second;
+            g_dev_sizes.erase(it);
+        }
+    }
+    cudaFree(p);
 }
 
 void* raw_host_alloc(size_t bytes) {
@@ -117,7 +143,7 @@ void* dev_alloc_bytes(size_t bytes) {
 void dev_free(void* p) {
     if (!p) return;
     if (t_cache && cached_free(p, t_cache->dev_kept, t_cache->dev_live, kDevKeepMax)) return;
-    cudaFree(p);
+    raw_dev_free(p);
 }
 
 void* host_alloc_bytes(size_t bytes) {
@@ -129,6 +155,16 @@ void host_free(void* p) {
     if (!p) return;
     if (t_cache && cached_free(p, t_cache->host_kept, t_cache->host_live, kHostKeepMax)) return;
     cudaFreeHost(p);
+}
+
+void dev_alloc_limit(int64_t bytes) {
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    g_dev_limit = bytes > 0 ? bytes : 0;
+}
+
+int64_t dev_live_bytes() {
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    return g_dev_live;
 }
 
 AllocScope::AllocScope(cudaStream_t s) {
@@ -143,7 +179,7 @@ AllocScope::~AllocScope() {
     ThreadCache* c = t_cache;
     t_cache = nullptr;
     cudaStreamSynchronize(c->s);
-    for (auto& b : c->dev_kept.blocks) cudaFree(b.second);
+    for (auto& b : c->dev_kept.blocks) raw_dev_free(b.second);
     for (auto& b : c->host_kept.blocks) cudaFreeHost(b.second);
     delete c;
 }

@@ -52,6 +52,10 @@ void* dev_alloc_bytes(size_t bytes);
 void dev_free(void* p);
 void* host_alloc_bytes(size_t bytes);
 void host_free(void* p);
+// Device bytes the library holds (kept scope blocks included), and an optional cap (<= 0: none)
+// above which allocations fail with H2_ERR_OOM.
+int64_t dev_live_bytes();
+void dev_alloc_limit(int64_t bytes);
 
 // While an AllocScope is alive on a thread, the blocks that this thread allocated inside
 // the scope and then frees are kept on per-thread free lists and handed out again to the

@@ -378,3 +378,29 @@ def test_repeated_matvec_graph_replay(h2, mode, nrhs):
         else:
             tol = 1e-13 if mode == 0 else 1e-6   # atomics in the small-nrhs scatter
             assert float((R.double() - Y.double()).norm() / R.double().norm()) < tol
+
+
+def test_allocation_failure_is_reported_without_leaks(h2):
+    """A cap on the library's device memory makes a construction fail with H2_ERR_OOM part-way;
+    every block it allocated is returned, and the next construction succeeds."""
+    n = 64
+    mask, op = _heat_problem(n, 256, 4)
+    gop = h2.HeatOperator(n, 0.01, 0.5, 0.01, mask)
+    tree = h2.Tree(W.grid_coords(n), 64, ADM_STRONG, 0.7)
+    # one full build first: the operator keeps its own workspaces (sized by the widest product)
+    h2.H2.build(gop, tree, 1e-6, h2.default_opts()).close()
+    torch.cuda.synchronize()
+    before = h2.device_bytes()
+    for extra in (1 << 16, 1 << 20, 8 << 20):
+        h2.set_device_limit(before + extra)
+        try:
+            with pytest.raises(h2.H2Error) as e:
+                h2.H2.build(gop, tree, 1e-6, h2.default_opts(global_rank=128 if extra == (8 << 20) else 0))
+            assert e.value.status == h2.H2_ERR_OOM
+        finally:
+            h2.set_device_limit(0)
+        assert h2.device_bytes() == before
+    G = h2.H2.build(gop, tree, 1e-6, h2.default_opts())
+    assert G.stats()["samples"] > 0
+    G.close()
+    assert h2.device_bytes() == before
