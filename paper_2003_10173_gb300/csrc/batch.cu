@@ -84,7 +84,9 @@ struct h2_batch_s {
 
 namespace h2 {
 
-// defined in matvec.cu (the batched stage kernel lives next to the stage body)
+// defined in matvec.cu (the batched stage kernels live next to the stage bodies)
+void launch_batch_transfer_rm(int mode, int kb, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
+                              const BatchBase* bases, int nrhs, cudaStream_t s);
 void launch_batch_stage(int mode, int rt, int out_y, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
                         const BatchBase* bases, int nrhs, cudaStream_t s);
 
@@ -166,6 +168,19 @@ void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* co
         }
         H2_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
     }
+    // right-hand-side-major workspaces when every merged transfer output has at most two items of
+    // at most 64 x 64 (the register sweep kernel), else the coefficient-major SIMT sweeps
+    int kb = 0;
+    bool rmaj = (nrhs + 127) / 128 <= 65535;
+    for (const BStage& m : b->stages) {
+        if (m.kind != H2_STAGE_UP && m.kind != H2_STAGE_DOWN) continue;
+        for (const MvOut& o : m.outs) {
+            rmaj = rmaj && o.end - o.beg <= 2;
+            kb = std::max(kb, o.rows);
+        }
+        for (const MvItem& it : m.items) kb = std::max({kb, it.rows, it.cols});
+    }
+    rmaj = rmaj && kb <= 64;
     // the handles' phase launches are independent (own operand buffers and workspaces): spread
     // them over the side streams so that the small grids of different Hessians run together
     auto phase = [&](int ph) {
@@ -173,8 +188,8 @@ void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* co
         for (int k = 0; k < kSide; ++k) H2_CUDA(cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
         for (size_t i = 0; i < b->hs.size(); ++i) {
             h2_handle_s* h = b->hs[i];
-            tc_phase(h, mode, ph, X[i], ldx[i], (float*)Y[i], ldy[i], nrhs, h->ws.f32.p, h->plan.ws_rows, 0,
-                     b->side[i % kSide]);
+            tc_phase(h, mode, ph, X[i], ldx[i], (float*)Y[i], ldy[i], nrhs, h->ws.f32.p,
+                     rmaj ? (int64_t)nrhs : h->plan.ws_rows, rmaj ? 1 : 0, b->side[i % kSide]);
         }
         for (int k = 0; k < kSide; ++k) {
             H2_CUDA(cudaEventRecord(b->side_ev[k], b->side[k]));
@@ -184,8 +199,12 @@ void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* co
     auto sweeps = [&](int kind) {
         for (BStage& m : b->stages) {
             if (m.outs.empty() || m.kind != kind) continue;
-            launch_batch_stage(md, rt, m.out_y, m.accumulate, m.d_outs.p, (int)m.outs.size(), m.d_items.p,
-                               b->d_bases.p, nrhs, s);
+            if (rmaj)
+                launch_batch_transfer_rm(md, kb, m.accumulate, m.d_outs.p, (int)m.outs.size(), m.d_items.p,
+                                         b->d_bases.p, nrhs, s);
+            else
+                launch_batch_stage(md, rt, m.out_y, m.accumulate, m.d_outs.p, (int)m.outs.size(), m.d_items.p,
+                                   b->d_bases.p, nrhs, s);
         }
     };
     phase(0);

@@ -201,12 +201,10 @@ __global__ void __launch_bounds__(TR_RC) mv_transfer_kernel(const MvOut* __restr
 // global memory (consecutive threads, consecutive addresses); many resident warps hide their
 // latency.  When accumulating, old output values are loaded eight at a time before their stores.
 template <class TS, int KB>
-__global__ void __launch_bounds__(TR_RC) mv_transfer_rm_kernel(const MvOut* __restrict__ outs,
-                                                               const MvItem* __restrict__ items,
-                                                               const TS* __restrict__ fac, float* __restrict__ ws,
-                                                               int64_t ld, int nrhs, int accumulate) {
+__device__ __forceinline__ void transfer_rm_body(const MvOut& o, const MvItem* __restrict__ items,
+                                                 const TS* __restrict__ fac, float* __restrict__ ws, int64_t ld,
+                                                 int nrhs, int accumulate) {
     __shared__ __align__(16) float Ms[2][KB * KB];   // item matrices, [col j][row i], zero beyond the rows
-    const MvOut o = outs[blockIdx.x];
     const int tid = threadIdx.x;
     const int r = blockIdx.y * TR_RC + tid;
     const bool live = r < nrhs;
@@ -267,6 +265,27 @@ __global__ void __launch_bounds__(TR_RC) mv_transfer_rm_kernel(const MvOut* __re
         for (int u = 0; u < 8; ++u)
             if (i0 + u < rows) y[(int64_t)(i0 + u) * ld] = acc[i0 + u] + old[u];
     }
+}
+
+template <class TS, int KB>
+__global__ void __launch_bounds__(TR_RC) mv_transfer_rm_kernel(const MvOut* __restrict__ outs,
+                                                               const MvItem* __restrict__ items,
+                                                               const TS* __restrict__ fac, float* __restrict__ ws,
+                                                               int64_t ld, int nrhs, int accumulate) {
+    transfer_rm_body<TS, KB>(outs[blockIdx.x], items, fac, ws, ld, nrhs, accumulate);
+}
+
+// The merged sweep stage of a batch on the handles' right-hand-side-major workspaces (leading
+// dimension nrhs for every handle): output o belongs to handle o.h.
+template <class TS, int KB>
+__global__ void __launch_bounds__(TR_RC) mv_batch_transfer_rm_kernel(const MvOut* __restrict__ outs,
+                                                                     const MvItem* __restrict__ items,
+                                                                     const BatchBase* __restrict__ bases, int nrhs,
+                                                                     int accumulate) {
+    const MvOut o = outs[blockIdx.x];
+    const BatchBase B = bases[o.h];
+    transfer_rm_body<TS, KB>(o, items, static_cast<const TS*>(B.fac), static_cast<float*>(B.ws), (int64_t)nrhs, nrhs,
+                             accumulate);
 }
 
 template <class TS, int KB>
@@ -767,6 +786,20 @@ void launch_batch_rt(int rt, int out_y, int accumulate, const MvOut* outs, int n
 }
 
 }  // namespace
+
+void launch_batch_transfer_rm(int mode, int kb, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
+                              const BatchBase* bases, int nrhs, cudaStream_t s) {
+    if (nouts <= 0) return;
+    const dim3 grid((unsigned)nouts, (unsigned)((nrhs + TR_RC - 1) / TR_RC));
+    if (mode == H2_BF16) {
+        if (kb <= 32) mv_batch_transfer_rm_kernel<__nv_bfloat16, 32><<<grid, TR_RC, 0, s>>>(outs, items, bases, nrhs, accumulate);
+        else mv_batch_transfer_rm_kernel<__nv_bfloat16, 64><<<grid, TR_RC, 0, s>>>(outs, items, bases, nrhs, accumulate);
+    } else {
+        if (kb <= 32) mv_batch_transfer_rm_kernel<float, 32><<<grid, TR_RC, 0, s>>>(outs, items, bases, nrhs, accumulate);
+        else mv_batch_transfer_rm_kernel<float, 64><<<grid, TR_RC, 0, s>>>(outs, items, bases, nrhs, accumulate);
+    }
+    after_launch("mv_batch_transfer_rm");
+}
 
 void launch_batch_stage(int mode, int rt, int out_y, int accumulate, const MvOut* outs, int nouts, const MvItem* items,
                         const BatchBase* bases, int nrhs, cudaStream_t s) {
