@@ -96,8 +96,10 @@ struct TcTraits<4> {   // TF32 operands, kind::tf32, K = 8 per MMA
 //   A_item = rows [a_row, a_row + K) of the padded operand buffer (K-major: rows are contiguous
 //            per right-hand side), and
 //   B_item = a pre-laid-out N_o x K tile of the tile pool.
-// The accumulator is written transposed: to Y through the tree permutation (leaf outputs) or
-// to the coefficient workspace (upsweep / coupling outputs).
+// Two kernels run these lists: tc_products_kernel (one output per CTA; the near field + leaf
+// expansion, written to Y through the tree permutation via a shared-memory transpose) and
+// tc_group_kernel (several coefficient outputs per CTA; the leaf upsweep and the couplings,
+// stored to the coefficient workspace straight from tensor memory).
 constexpr int TC_NMAX = 64, TC_KMAX = 64;
 constexpr int TC_GCOLS = 128;   // tensor-memory columns of a CTA: its outputs side by side (4 CTAs per SM)
 constexpr int TC_GMAX = 8;      // outputs per CTA
