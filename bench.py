@@ -208,7 +208,8 @@ def precision_section(h2, torch, stream, bf16_peak: float, n: int = 512) -> dict
 def batching_section(h2, torch, stream) -> dict:
     """64 heat Hessians of uneven sizes (n ~ U{64..256}, kappa ~ U[0.002, 0.05], 5-20 % sensors):
     batched FP64 construction and the merged, autotuned, graph-captured FP32 matvec with
-    nrhs = 64, against the plain FP64 form (one h2_build and one FP64 h2_matvec per Hessian)."""
+    nrhs = 64, against the plain FP64 form (one h2_build and one FP64 h2_matvec per Hessian);
+    the batched tensor-core forms in TF32 and split TF32 (FP32-grade) beside it."""
     probs = W.batch_problems(64)
     b = CFG["build"]
     nrhs = 64
@@ -262,6 +263,17 @@ def batching_section(h2, torch, stream) -> dict:
     torch.cuda.synchronize()
     t_tc = e0.elapsed_time(e1) / reps
     err_tc = max(float((yt.double() - y64).norm() / y64.norm()) for yt, y64 in zip(YT, Y64))
+    # split TF32 on tensor cores: FP32-grade accuracy (the alternative to the FP32 SIMT form)
+    Y3 = [torch.empty_like(x) for x in X32]
+    B.matvec(X32, Y3, nrhs, h2.H2_TF32X3, stream=stream)     # capture
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        B.matvec(X32, Y3, nrhs, h2.H2_TF32X3, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_x3 = e0.elapsed_time(e1) / reps
+    err_x3 = max(float((y3.double() - y64).norm() / y64.norm()) for y3, y64 in zip(Y3, Y64))
     by32 = sum(matvec_bytes(G.stats(), p.N, nrhs, 4) for G, p in zip(Gs, probs))
     by64 = sum(matvec_bytes(G.stats(), p.N, nrhs, 8) for G, p in zip(plain, probs))
     hbm = peaks()[0]
@@ -274,6 +286,7 @@ def batching_section(h2, torch, stream) -> dict:
            "matvec_batched_tf32_tc_ms": t_tc, "matvec_batched_tf32_tc_GBps": by32 / (t_tc / 1e3) / 1e9,
            "matvec_batched_tf32_tc_frac_of_hbm": by32 / (t_tc / 1e3) / 1e9 / hbm,
            "matvec_tf32_tc_speedup_vs_plain_fp64": t_pmv / t_tc, "rel_err_tf32_vs_fp64_max": err_tc,
+           "matvec_batched_tf32x3_tc_ms": t_x3, "rel_err_tf32x3_vs_fp64_max": err_x3,
            "samples_total": sum(G.stats()["samples"] for G in Gs)}
     B.close()
     for G in Gs + plain:
