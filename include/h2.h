@@ -392,8 +392,8 @@ int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* bu
 /*
  * A 3-layer perceptron that predicts, per tree level, the probe count the adaptive range
  * finder settles on, so that peeling can start there (Section 3.3: the per-level sample
- * count C_l k is the quantity being tuned; adaptive growth stays the fallback and the judge
- * of the error).  Not a construct of the paper: a learned replacement for its hand-tuned
+ * count C_l k is the quantity being tuned; adaptive growth stays the fallback and decides
+ * the error).  Not a construct of the paper: a learned replacement for its hand-tuned
  * sampling parameters.
  *   x (H2_RM_FEATURES) -> gelu(W1 x + b1) -> gelu(W2 h1 + b2) -> y = W3 h2 + b3, width 64,
  *   gelu(u) = u/2 (1 + tanh(sqrt(2/pi) (u + 0.044715 u^3))); target y = log2(1 + need).

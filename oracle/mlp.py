@@ -7,7 +7,7 @@ The paper notes that the number of Hessian-vector products per level is C_l k
 and that tuning the sampling to the structure of the Hessian pays (Section 3.3);
 the learned part predicts, from level, box geometry and operator parameters,
 the probe count that adaptive peeling would choose, so that peeling can start
-there (adaptive growth remains the fallback and the judge of the error).
+there (adaptive growth remains the fallback and decides the error).
 
 Model: x (F = 8 features) -> z1 = W1 x + b1 -> h1 = gelu(z1) -> z2 = W2 h1 + b2
 -> h2 = gelu(z2) -> y = W3 h2 + b3, width 64, gelu in its tanh form
