@@ -26,12 +26,23 @@ def basis_threshold(tol: float, norm_est: float, n_leaves: int) -> float:
 
 
 def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None,
-          q_level=None, q_test=8, global_rank=0):
-    """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result)."""
+          q_level=None, q_test=8, global_rank=0, ranks=None, q_exact=None):
+    """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result).
+    ranks, q_exact: optional basis ranks and range-probe counts to replay (see assemble, peel)."""
     tree = ClusterTree(coords, leaf)
     part = Partition(tree, adm, eta)
     res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est, q_level=q_level,
-               q_test=q_test, global_rank=global_rank)
+               q_test=q_test, global_rank=global_rank, q_exact=q_exact)
     res.tau_basis = basis_threshold(tol, res.norm_est, 1 << tree.L)
-    h = assemble(tree, part, res, res.tau_basis, kmax)
+    h = assemble(tree, part, res, res.tau_basis, kmax, ranks=ranks)
     return h, res
+
+
+def replay_build(op, coords, leaf, adm, eta, tol, kmax, seed, norm_est, range_probes, ranks):
+    """Rank replay: the construction with every decision of another run given as data.
+    range_probes[l] > 0 is the number of range-pass probes of level l (0: identity range, no
+    range pass); norm_est the 2-norm estimate used; ranks[l][b] the basis rank of box b of
+    level l.  The peeling then runs with exactly these probe counts (no adaptive test) and
+    the truncations keep exactly these ranks; everything else is the ordinary method."""
+    return build(op, coords, leaf, adm, eta, tol, kmax, 1, 1, 1 << 30, False, seed, norm_est=norm_est,
+                 ranks=ranks, q_exact=[int(q) for q in range_probes])

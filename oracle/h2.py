@@ -57,10 +57,18 @@ class H2Matrix:
         return [(int(t), int(s)) for t, s in self.part.near if t >= s]
 
 
-def _truncate(W: np.ndarray, tau: float, kmax: int):
+def _truncate(W: np.ndarray, tau: float, kmax: int, k_given=None):
+    """Leading left singular vectors of W with singular value > tau (at most kmax).  With
+    k_given (rank replay) exactly that many are kept, whatever the threshold says."""
     if W.size == 0 or W.shape[1] == 0:
+        if k_given:
+            raise ValueError("rank replay asks for vectors of an empty block row")
         return np.zeros((W.shape[0], 0)), np.zeros(0), False
     U, s, _ = np.linalg.svd(W, full_matrices=False)
+    if k_given is not None:
+        if k_given > U.shape[1]:
+            raise ValueError("rank replay asks for more vectors than the block row has")
+        return U[:, :k_given], s, False
     k = int(np.sum(s > tau))
     cap = k > kmax
     k = min(k, kmax)
@@ -90,8 +98,13 @@ def block_row_weights(tree: ClusterTree, part: Partition, pieces):
     return R
 
 
-def assemble(tree: ClusterTree, part: Partition, peel_res, tau: float, kmax: int) -> H2Matrix:
-    """Destination assembly, nested bases, couplings and dense blocks from the pieces."""
+def assemble(tree: ClusterTree, part: Partition, peel_res, tau: float, kmax: int, ranks=None) -> H2Matrix:
+    """Destination assembly, nested bases, couplings and dense blocks from the pieces.
+
+    ranks (rank replay, optional): per level l a sequence of the basis rank of every box of
+    that level; the truncations keep exactly these ranks instead of deciding by tau.  The
+    ranks of another implementation can be replayed this way, so that two constructions
+    that agree on every rank decision can be compared to rounding error."""
     L = tree.L
     P = peel_res.pieces
     h = H2Matrix(tree, part)
@@ -102,7 +115,7 @@ def assemble(tree: ClusterTree, part: Partition, peel_res, tau: float, kmax: int
         rows = tree.rows(L, t)
         cols = [P[lp][rows] @ Rl.T for lp, Rl in R[L][t].items()]
         W = np.hstack(cols) if cols else np.zeros((rows.stop - rows.start, 0))
-        U, s, cap = _truncate(W, tau, kmax)
+        U, s, cap = _truncate(W, tau, kmax, None if ranks is None else int(ranks[L][t]))
         h.cap_hit |= cap
         h.sv[(L, t)] = s
         h.U[t] = U
@@ -123,7 +136,7 @@ def assemble(tree: ClusterTree, part: Partition, peel_res, tau: float, kmax: int
                 W = np.vstack([np.hstack(top), np.hstack(bot)])
             else:
                 W = np.zeros((k1 + k2, 0))
-            Uh, s, cap = _truncate(W, tau, kmax)
+            Uh, s, cap = _truncate(W, tau, kmax, None if ranks is None else int(ranks[l][t]))
             h.cap_hit |= cap
             h.sv[(l, t)] = s
             h.E[(l + 1, c1)] = Uh[:k1]

@@ -119,6 +119,21 @@ def apply_pieces(pieces, levels, tree: ClusterTree, Om: np.ndarray) -> np.ndarra
     return out
 
 
+def range_basis(Y: np.ndarray) -> np.ndarray:
+    """Orthonormal column basis of a sample block (Section 3.3: "a QR factorization of
+    (A Omega)_1 gives the orthogonal columns basis U").  Reading: the basis is the Q factor of
+    the thin QR with a non-negative diagonal of R, the unique one when Y has full column rank,
+    so that the basis -- not only its span -- is fixed by the samples (the projection pass
+    applies all blocks' bases at once, and the coarse levels' residual couples them); once
+    the samples have at least as many columns as rows, the range is all of R^m and U = I."""
+    m, q = Y.shape
+    if q >= m:
+        return np.eye(m)
+    Q, R = np.linalg.qr(Y)
+    sgn = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return Q * sgn
+
+
 def psd_cholesky(M: np.ndarray) -> np.ndarray:
     """Lower-triangular C with C C^T = M for a symmetric positive semidefinite M (right-looking
     Cholesky).  A pivot at or below n * 2^-52 * max(diag M) is rounding noise of a zero
@@ -203,11 +218,14 @@ class PeelResult:
 
 def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, adaptive: bool,
          seed: int, norm_est: float | None = None, q_level=None, q_test: int = 8,
-         global_rank: int = 0) -> PeelResult:
+         global_rank: int = 0, q_exact=None) -> PeelResult:
     """Construct the sibling pieces and the leaf diagonal blocks from products with op.
 
     q_level: optional sequence indexed by level (entries <= 0 mean q0) of start counts.
-    global_rank: budget of the global low-rank piece (0: none)."""
+    global_rank: budget of the global low-rank piece (0: none).
+    q_exact (replay of another run's decisions): sequence indexed by level; level l draws
+    exactly q_exact[l] range probes without any test, and takes the identity range when
+    q_exact[l] == 0.  Overrides q0, q_level and adaptive."""
     N = tree.N
     opt = TreeOperator(op, tree)
     res = PeelResult()
@@ -241,9 +259,12 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
         predicted = q_level is not None and l < len(q_level) and q_level[l] > 0
         if predicted:
             ql = int(q_level[l])
+        if q_exact is not None:
+            ql = int(q_exact[l])
+            adaptive = False
         res.range_calls[l] = 0
         res.passed[l] = 0
-        if ql >= mb:
+        if (ql >= mb and q_exact is None) or (q_exact is not None and ql == 0):
             # the range of H[b, a] is all of R^|b|
             for b in B:
                 Qs.append(np.eye(b.stop - b.start))
@@ -268,7 +289,7 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
             pending = Y[:, q:] if c1 else None
             Y = Y[:, :q]
             Ys = [Y[b] for b in B]
-            Qs = [np.linalg.qr(y)[0] for y in Ys]
+            Qs = [range_basis(y) for y in Ys]
             res.need[l] = q
             while adaptive and q < q_max and q < mb:
                 c = min(inc, q_max - q)
@@ -287,7 +308,7 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
                         r = yb - Qs[i] @ (Qs[i].T @ yb)
                         errs.append(float(np.linalg.norm(r, axis=0).max()))
                     Ys[i] = np.hstack([Ys[i], yb])
-                    Qs[i] = np.linalg.qr(Ys[i])[0]
+                    Qs[i] = range_basis(Ys[i])
                 res.test_err[l].append(errs)
                 res.need[l] = q
                 q += c

@@ -10,10 +10,13 @@
 // Recompression into nested bases (Section 3.2): for every box t, the far block
 // row (far blocks of t and of its ancestors restricted to t) is, grouped by the
 // pair level lp of the sampled piece containing each block, sum_lp P_lp[t] C_lp^T.
-// Its Gram matrix sum_lp P_lp[t] M_lp(t) P_lp[t]^T (M_lp = C_lp^T C_lp, built by
-// a downsweep of per-box Gram matrices) is eigen-decomposed at the leaves and, in
-// the coordinates of the children's bases, at every upper level (upsweep), keeping
-// the directions above the truncation threshold.  Couplings S_ts are products of
+// A QR downsweep gives the R factors R_lp(t) of the column sides C_lp(t), so that
+// the block row has the left singular vectors and values of the compact factor
+// W_t = [P_lp[t] R_lp(t)^T]_lp; its truncated SVD (QR of W_t^T, one-sided Jacobi)
+// gives the leaf bases and, in the coordinates of the children's bases, the
+// transfer matrices of every upper level (upsweep), keeping the directions above
+// the truncation threshold.  No Gram matrix is formed, so the singular values are
+// resolved to about eps * sigma_max.  Couplings S_ts are products of
 // the projected pieces, near blocks products of the pieces.
 //
 // The host only orchestrates: every arithmetic step runs in the library's kernels.
@@ -79,7 +82,8 @@ class Builder {
     int L_;
 
     DevBuf<int32_t> d_perm_, d_row_leaf_;
-    DevBuf<double> Om_, Yo_, Yt_, Ot_, Tw_, Cw_;
+    DevBuf<double> Om_, Yo_, Yt_, Ot_, Tw_, Cw_, Ysv_;
+    DevBuf<SignItem> d_sign_;
     DevBuf<double> Pcap_;
     std::vector<int64_t> pcol_;      // capacity column offset per level
     std::vector<int> qcap_, qw_;     // capacity and final piece width per level
@@ -88,6 +92,7 @@ class Builder {
     std::vector<int64_t> ddiag_off_;
     GemmBatch gb_;
     TsqrWork tsqr_;
+    StackWork stk_;
     Stager stg_[4];
     DevBuf<int64_t> d_i64a_, d_i64b_;
     DevBuf<int> d_i32a_, d_i32b_, d_i32c_, d_flag_;
@@ -279,12 +284,17 @@ std::vector<double> Builder::colnorm(int l, const std::vector<int>& pairs, int c
 // Gram-Schmidt with reorthogonalisation (BCGS2; Barlow and Smoktunowicz 2013): project and
 // Householder-QR the panel, then project the orthonormal result once more and QR it again.
 // The second round keeps the new columns orthogonal to Q_b also when the panel is
-// numerically rank deficient (samples of a block whose range is already captured).
+// numerically rank deficient (samples of a block whose range is already captured).  Finally
+// every new column q_j is turned so that q_j^T y_j >= 0 for its sample column y_j: the basis
+// is then the Q factor of the samples' thin QR with a non-negative diagonal of R, fixed by
+// the samples and not by the orthogonalisation method (the projection pass applies all
+// blocks' bases at once, so the basis itself, not only its span, reaches the pieces).
 void Builder::panel(int l, const std::vector<int>& pairs, int c0, int w) {
     if (pairs.empty()) return;
     std::vector<int64_t> yoff, qoff;
     std::vector<int> m;
-    std::vector<BlkDesc> back;
+    std::vector<BlkDesc> back, save;
+    std::vector<SignItem> signs;
     for (int i : pairs) {
         const int64_t st = bstart(l, 2 * i + 1);
         yoff.push_back(st + (int64_t)c0 * N_);
@@ -292,13 +302,19 @@ void Builder::panel(int l, const std::vector<int>& pairs, int c0, int w) {
         m.push_back(bsize(l, 2 * i + 1));
         back.push_back(BlkDesc{st + (int64_t)kb_[l][i] * N_, st + (int64_t)c0 * N_, bsize(l, 2 * i + 1), w, (int)N_,
                                (int)N_});
+        save.push_back(BlkDesc{st + (int64_t)c0 * N_, st, bsize(l, 2 * i + 1), w, (int)N_, (int)N_});
+        for (int j = 0; j < w; ++j)
+            signs.push_back(SignItem{st + (int64_t)(kb_[l][i] + j) * N_, st + (int64_t)j * N_, bsize(l, 2 * i + 1)});
     }
+    Ysv_.reserve((size_t)N_ * PANEL);
+    blocks(BLK_COPY, save, Yt_.p, Ysv_.p);
     for (int round = 0; round < 2; ++round) {
         project(l, pairs, w, c0, 1);
         tsqr_panels((int)pairs.size(), yoff.data(), qoff.data(), m.data(), w, Yt_.p, (int)N_, Pl(l), (int)N_, tsqr_,
                     s_);
         if (round == 0) blocks(BLK_COPY, back, Pl(l), Yt_.p);
     }
+    align_signs((int)signs.size(), dev_list(d_sign_, signs, 3), Pl(l), Ysv_.p, s_);
     for (int i : pairs) kb_[l][i] += w;
 }
 
@@ -594,12 +610,11 @@ void Builder::assemble(h2_handle_s* h) {
         qoff[l] = Q;
         Q += qw_[l];
     }
-    DevBuf<double> Pall, Tall, gram, Gbuf, Utmp, Uhtmp;
+    DevBuf<double> Pall, Tall, Rb, Utmp, Uhtmp;
     std::vector<DevBuf<double>> Pi(L + 1);
     std::vector<std::vector<int64_t>> rowoff(L + 1);
     std::vector<int64_t> Krows(L + 1, 0);
     std::vector<int64_t> utmp_off(1 << L, 0), uhtmp_off(h->koff[L], 0);
-    const double thr = tau_basis_ * tau_basis_;
     DevBuf<int> d_k, d_cap(1);
     H2_CUDA(cudaMemsetAsync(d_cap.p, 0, sizeof(int), s_));
     auto K = [&](int l, int b) -> int& { return h->k[h->koff[l] + b]; };
@@ -630,107 +645,116 @@ void Builder::assemble(h2_handle_s* h) {
         Om_.release(); Yo_.release(); Yt_.release(); Ot_.release();
         auto Pp = [&](int l, int b, int lp) { return Pall.p + bstart(l, b) + qoff[lp] * N_; };
 
-        // per-box Gram matrices B_lp(s) = P_lp[s]^T P_lp[s] of the column boxes of far blocks,
-        // F_lp(r) = sum of B over r's far blocks, M_lp(t) = sum of F over t and its ancestors
+        // QR downsweep (Section 3.2).  Far block (r, s) of level l lies in the sibling piece of
+        // its pair level lp (and in the global piece lp = 0), so the far block row of box t is
+        // sum_lp P_lp[t] C_lp(t)^T, C_lp(t) the stacked P_lp[s] of the far blocks of t and of
+        // its ancestors.  Rs(l, s, lp) = R of P_lp[s]; R(l, t, lp) = R of [R(l-1, parent, lp);
+        // Rs(l, s, lp) for the far blocks (t, s) of t itself] (the parent's factor when t has
+        // none).  Every factor is c x c (c = qw_[lp]) with reff <= c non-zero rows.
         using Key = std::tuple<int, int, int>;  // (level, box, lp)
-        std::map<Key, int64_t> boff, foff, moff;
-        std::map<Key, std::vector<int64_t>> flist;
-        int64_t gtot = 0;
-        auto q2 = [&](int lp) { return (int64_t)qw_[lp] * qw_[lp]; };
+        struct RInfo { int64_t off; int reff; };
+        std::map<Key, RInfo> rs, rt;
+        std::map<Key, std::vector<int>> own;   // (level, t, lp) -> far column boxes of t
+        int64_t rtot = 0;
+        auto c2 = [&](int lp) { return (int64_t)qw_[lp] * qw_[lp]; };
         for (int l = 1; l <= L; ++l)
-            for (auto [r, sb] : T_.far[l]) {
-                // the sibling piece of the block's pair level, and the global piece (every block)
+            for (auto [r, sb] : T_.far[l])
                 for (const int lp : {pair_level(l, r, sb), 0}) {
                     if (!qw_[lp]) continue;
                     Key kb{l, sb, lp};
-                    if (!boff.count(kb)) { boff[kb] = gtot; gtot += q2(lp); }
-                    flist[Key{l, r, lp}].push_back(boff[kb]);
+                    if (!rs.count(kb)) {
+                        rs[kb] = RInfo{rtot, std::min(qw_[lp], bsize(l, sb))};
+                        rtot += c2(lp);
+                    }
+                    own[Key{l, r, lp}].push_back(sb);
                 }
-            }
-        for (auto& [key, lst] : flist) { foff[key] = gtot; gtot += q2(std::get<2>(key)); }
         for (int l = 1; l <= L; ++l)
             for (int t = 0; t < (1 << l); ++t)
                 for (int lp = 0; lp <= l; ++lp) {
                     if (!qw_[lp]) continue;
-                    const bool has = foff.count(Key{l, t, lp}) || (l - 1 >= lp && moff.count(Key{l - 1, t >> 1, lp}));
-                    if (has) { moff[Key{l, t, lp}] = gtot; gtot += q2(lp); }
+                    auto par = rt.find(Key{l - 1, t >> 1, lp});
+                    auto ow = own.find(Key{l, t, lp});
+                    if (ow == own.end()) {
+                        if (par != rt.end()) rt[Key{l, t, lp}] = par->second;   // alias
+                        continue;
+                    }
+                    int rows = par != rt.end() ? par->second.reff : 0;
+                    for (int sb : ow->second) rows += rs[Key{l, sb, lp}].reff;
+                    rt[Key{l, t, lp}] = RInfo{rtot, std::min(qw_[lp], rows)};
+                    rtot += c2(lp);
                 }
-        gram.reserve((size_t)std::max<int64_t>(gtot, 1));
-        for (auto& [key, off] : boff) {
-            auto [l, sb, lp] = key;
-            const int q = qw_[lp];
-            gb_.add(Pp(l, sb, lp), (int)N_, 1, Pp(l, sb, lp), (int)N_, 0, gram.p + off, q, q, q, bsize(l, sb), 1.0, 0.0);
-        }
-        gb_.run(s_);
+        Rb.reserve((size_t)std::max<int64_t>(rtot, 1));
         {
-            std::vector<int64_t> oo, io;
-            std::vector<int> len, bg, en;
-            for (auto& [key, lst] : flist) {
-                oo.push_back(foff[key]);
-                len.push_back((int)q2(std::get<2>(key)));
-                bg.push_back((int)io.size());
-                io.insert(io.end(), lst.begin(), lst.end());
-                en.push_back((int)io.size());
+            std::vector<StackJob> jobs;
+            std::vector<RowSeg> segs;
+            for (auto& [key, ri] : rs) {
+                auto [l, sb, lp] = key;
+                const int q = qw_[lp];
+                jobs.push_back(StackJob{(int)segs.size(), (int)segs.size() + 1, q, Rb.p + ri.off, q, nullptr, nullptr});
+                segs.push_back(RowSeg{Pp(l, sb, lp), bsize(l, sb), (int)N_});
             }
-            sum_lists((int)oo.size(), dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
-                      dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), gram.p, gram.p, 0, s_);
-            H2_CUDA(cudaStreamSynchronize(s_));
+            stacked_r(jobs, segs, stk_, s_);
         }
         for (int l = 1; l <= L; ++l) {
-            std::vector<int64_t> oo, io;
-            std::vector<int> len, bg, en;
+            std::vector<StackJob> jobs;
+            std::vector<RowSeg> segs;
             for (int t = 0; t < (1 << l); ++t)
                 for (int lp = 0; lp <= l; ++lp) {
-                    auto it = moff.find(Key{l, t, lp});
-                    if (it == moff.end()) continue;
-                    oo.push_back(it->second);
-                    len.push_back((int)q2(lp));
-                    bg.push_back((int)io.size());
-                    auto f = foff.find(Key{l, t, lp});
-                    if (f != foff.end()) io.push_back(f->second);
-                    auto mp = moff.find(Key{l - 1, t >> 1, lp});
-                    if (mp != moff.end()) io.push_back(mp->second);
-                    en.push_back((int)io.size());
+                    auto ow = own.find(Key{l, t, lp});
+                    if (ow == own.end() || !qw_[lp]) continue;
+                    const int q = qw_[lp];
+                    const RInfo ri = rt[Key{l, t, lp}];
+                    StackJob jb{(int)segs.size(), 0, q, Rb.p + ri.off, q, nullptr, nullptr};
+                    auto par = rt.find(Key{l - 1, t >> 1, lp});
+                    if (par != rt.end() && par->second.reff) segs.push_back(RowSeg{Rb.p + par->second.off, par->second.reff, q});
+                    for (int sb : ow->second) {
+                        const RInfo& si = rs[Key{l, sb, lp}];
+                        if (si.reff) segs.push_back(RowSeg{Rb.p + si.off, si.reff, q});
+                    }
+                    jb.seg_end = (int)segs.size();
+                    jobs.push_back(jb);
                 }
-            sum_lists((int)oo.size(), dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
-                      dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), gram.p, gram.p, 0, s_);
-            H2_CUDA(cudaStreamSynchronize(s_));
+            stacked_r(jobs, segs, stk_, s_);
         }
 
-        // leaves: G_t = sum_lp P_lp[t] M_lp(t) P_lp[t]^T, truncated eigen-decomposition
+        // leaves: SVD of W_t = [P_lp[t] R(L, t, lp)^T]_lp through W_t^T (stacked R P^T blocks)
         const int nleaf = 1 << L;
-        Tall.reserve((size_t)N_ * Q);
-        fill_zero(Tall.p, (size_t)N_ * Q, s_);
-        std::vector<int64_t> goff(nleaf);
-        int64_t gt = 0, ut = 0;
+        std::vector<int64_t> toff(nleaf + 1, 0);
+        std::vector<int> trows(nleaf, 0);
         for (int t = 0; t < nleaf; ++t) {
-            goff[t] = gt;
+            for (int lp = 0; lp <= L; ++lp) {
+                auto it = rt.find(Key{L, t, lp});
+                if (it != rt.end()) trows[t] += it->second.reff;
+            }
+            toff[t + 1] = toff[t] + (int64_t)trows[t] * bsize(L, t);
+        }
+        Tall.reserve((size_t)std::max<int64_t>(toff[nleaf], 1));
+        int64_t ut = 0;
+        for (int t = 0; t < nleaf; ++t) {
             utmp_off[t] = ut;
-            gt += (int64_t)bsize(L, t) * bsize(L, t);
             ut += (int64_t)bsize(L, t) * bsize(L, t);
         }
-        Gbuf.reserve((size_t)gt);
         Utmp.reserve((size_t)ut);
-        for (int t = 0; t < nleaf; ++t)
-            for (int lp = 0; lp <= L; ++lp) {
-                auto it = moff.find(Key{L, t, lp});
-                if (it == moff.end()) continue;
-                const int q = qw_[lp];
-                gb_.add(Pp(L, t, lp), (int)N_, 0, gram.p + it->second, q, 0,
-                        Tall.p + bstart(L, t) + qoff[lp] * N_, (int)N_, bsize(L, t), q, q, 1.0, 0.0);
-            }
-        gb_.run(s_);
-        for (int t = 0; t < nleaf; ++t)
-            gb_.add(Tall.p + bstart(L, t), (int)N_, 0, Pall.p + bstart(L, t), (int)N_, 1, Gbuf.p + goff[t], bsize(L, t),
-                    bsize(L, t), bsize(L, t), (int)Q, 1.0, 0.0);
-        gb_.run(s_);
         {
-            std::vector<int> nn(nleaf);
-            for (int t = 0; t < nleaf; ++t) nn[t] = bsize(L, t);
+            std::vector<StackJob> jobs;
+            std::vector<RowSeg> segs;
             d_k.reserve(nleaf);
-            jacobi_eig_trunc(nleaf, dev_list(d_i64a_, goff, 0), dev_list(d_i32a_, nn, 1),
-                             *std::max_element(nn.begin(), nn.end()), Gbuf.p,
-                             dev_list(d_i64b_, utmp_off, 2), Utmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
+            for (int t = 0; t < nleaf; ++t) {
+                int row = 0;
+                for (int lp = 0; lp <= L; ++lp) {
+                    auto it = rt.find(Key{L, t, lp});
+                    if (it == rt.end() || !it->second.reff) continue;
+                    const int q = qw_[lp];
+                    gb_.add(Rb.p + it->second.off, q, 0, Pp(L, t, lp), (int)N_, 1, Tall.p + toff[t] + row, trows[t],
+                            it->second.reff, bsize(L, t), q, 1.0, 0.0);
+                    row += it->second.reff;
+                }
+                jobs.push_back(StackJob{(int)segs.size(), (int)segs.size() + (trows[t] ? 1 : 0), bsize(L, t),
+                                        Utmp.p + utmp_off[t], bsize(L, t), d_k.p + t, nullptr});
+                if (trows[t]) segs.push_back(RowSeg{Tall.p + toff[t], trows[t], trows[t]});
+            }
+            gb_.run(s_);
+            stacked_svd_trunc(jobs, segs, stk_, tau_basis_, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nleaf);
             for (int t = 0; t < nleaf; ++t) K(L, t) = kk[t];
         }
@@ -748,48 +772,48 @@ void Builder::assemble(h2_handle_s* h) {
             gb_.add(Utmp.p + utmp_off[t], bsize(L, t), 1, Pall.p + bstart(L, t), (int)N_, 0, Pi[L].p + rowoff[L][t],
                     (int)Krows[L], K(L, t), (int)Q, bsize(L, t), 1.0, 0.0);
         gb_.run(s_);
-        // upsweep: every box gets a (2 kmax)^2 slot for its stacked transfer matrices
+        // upsweep: SVD of [U_c1^T W_p|c1; U_c2^T W_p|c2] = [Pi(c1); Pi(c2)] R(l, p, lp)^T, grouped by lp;
+        // every box gets a (2 kmax)^2 slot for its stacked transfer matrices
         const int nmax = 2 * o_.kmax;
         Uhtmp.reserve((size_t)std::max<int64_t>((int64_t)h->koff[L] * nmax * nmax, 1));
         for (int64_t i = 0; i < h->koff[L]; ++i) uhtmp_off[i] = i * nmax * nmax;
         for (int l = L - 1; l >= 1; --l) {
             const int nb = 1 << l;
             const int64_t Kc = Krows[l + 1];
-            DevBuf<double> Tb((size_t)Kc * Q);
-            fill_zero(Tb.p, (size_t)Kc * Q, s_);
-            std::vector<int64_t> go(nb), uo(nb);
-            std::vector<int> nn(nb);
-            int64_t g2 = 0;
+            std::vector<int64_t> to(nb + 1, 0);
+            std::vector<int> nn(nb), tr(nb, 0);
             for (int p = 0; p < nb; ++p) {
                 nn[p] = K(l + 1, 2 * p) + K(l + 1, 2 * p + 1);
-                go[p] = g2;
-                g2 += (int64_t)nn[p] * nn[p];
-                uo[p] = uhtmp_off[h->koff[l] + p];
-            }
-            Gbuf.reserve((size_t)std::max<int64_t>(g2, 1));
-            for (int p = 0; p < nb; ++p) {
-                if (!nn[p]) continue;
-                const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
                 for (int lp = 0; lp <= l; ++lp) {
-                    auto it = moff.find(Key{l, p, lp});
-                    if (it == moff.end()) continue;
-                    const int q = qw_[lp];
-                    gb_.add(V + qoff[lp] * Kc, (int)Kc, 0, gram.p + it->second, q, 0,
-                            Tb.p + rowoff[l + 1][2 * p] + qoff[lp] * Kc, (int)Kc, nn[p], q, q, 1.0, 0.0);
+                    auto it = rt.find(Key{l, p, lp});
+                    if (it != rt.end()) tr[p] += it->second.reff;
                 }
+                to[p + 1] = to[p] + (int64_t)tr[p] * nn[p];
             }
-            gb_.run(s_);
-            for (int p = 0; p < nb; ++p) {
-                if (!nn[p]) continue;
-                const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
-                gb_.add(Tb.p + rowoff[l + 1][2 * p], (int)Kc, 0, V, (int)Kc, 1, Gbuf.p + go[p], nn[p], nn[p], nn[p],
-                        (int)Q, 1.0, 0.0);
-            }
-            gb_.run(s_);
+            DevBuf<double> Tb((size_t)std::max<int64_t>(to[nb], 1));
+            std::vector<StackJob> jobs;
+            std::vector<RowSeg> segs;
             d_k.reserve(nb);
-            jacobi_eig_trunc(nb, dev_list(d_i64a_, go, 0), dev_list(d_i32a_, nn, 1), *std::max_element(nn.begin(), nn.end()),
-                             Gbuf.p, dev_list(d_i64b_, uo, 2),
-                             Uhtmp.p, d_k.p, thr, o_.kmax, d_cap.p, s_);
+            for (int p = 0; p < nb; ++p) {
+                const bool any = nn[p] && tr[p];
+                if (any) {
+                    const double* V = Pi[l + 1].p + rowoff[l + 1][2 * p];
+                    int row = 0;
+                    for (int lp = 0; lp <= l; ++lp) {
+                        auto it = rt.find(Key{l, p, lp});
+                        if (it == rt.end() || !it->second.reff) continue;
+                        const int q = qw_[lp];
+                        gb_.add(Rb.p + it->second.off, q, 0, V + qoff[lp] * Kc, (int)Kc, 1, Tb.p + to[p] + row, tr[p],
+                                it->second.reff, nn[p], q, 1.0, 0.0);
+                        row += it->second.reff;
+                    }
+                }
+                jobs.push_back(StackJob{(int)segs.size(), (int)segs.size() + (any ? 1 : 0), nn[p],
+                                        Uhtmp.p + uhtmp_off[h->koff[l] + p], std::max(nn[p], 1), d_k.p + p, nullptr});
+                if (any) segs.push_back(RowSeg{Tb.p + to[p], tr[p], tr[p]});
+            }
+            gb_.run(s_);
+            stacked_svd_trunc(jobs, segs, stk_, tau_basis_, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nb);
             for (int p = 0; p < nb; ++p) K(l, p) = kk[p];
             level_rows(l);
@@ -864,8 +888,8 @@ void Builder::assemble(h2_handle_s* h) {
 void Builder::run(h2_handle_s* h) {
     const double t0 = now_s();
     const int nleaf = 1 << L_;
-    if (T_.leaf_max > eig_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: leaf size above 96 is not supported");
-    if (2 * o_.kmax > eig_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: kmax above 48 is not supported");
+    if (T_.leaf_max > svd_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: leaf size above 96 is not supported");
+    if (2 * o_.kmax > svd_max_order()) fail(H2_ERR_INVALID_ARG, "h2_build: kmax above 48 is not supported");
     {
         std::vector<int32_t> perm(N_), rl(N_);
         for (int64_t i = 0; i < N_; ++i) perm[i] = (int32_t)T_.perm[i];

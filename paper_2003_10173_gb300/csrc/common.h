@@ -198,15 +198,51 @@ struct TsqrWork {
 };
 void tsqr_panels(int count, const int64_t* y_off, const int64_t* q_off, const int* m, int c, double* Y, int ldy,
                  double* Q, int ldq, TsqrWork& w, cudaStream_t s);
+// Sign convention of orthonormal bases: for every item, the column of `rows` entries at Q + q_off
+// is negated when its dot product with the column at Y + y_off is negative, so that the basis
+// is the Q factor of Y = QR with a non-negative diagonal of R.
+struct SignItem {
+    int64_t q_off, y_off;
+    int rows;
+};
+void align_signs(int count, const SignItem* d_items, double* Q, const double* Y, cudaStream_t s);
 // Maximum column 2-norm of each panel: out[i] = max_j ||Y_i[:, j]||.
 void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c, const double* Y,
                        int ldy, double* out, cudaStream_t s);
-// Symmetric eigen-decomposition (cyclic Jacobi) of count n_i x n_i matrices, keeping the
-// eigenvectors with eigenvalue > thr (at most kmax), sorted descending.
-// max_n: the largest n_i (host value; sizes the kernel's shared memory).
-void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, int max_n, const double* A,
-                      const int64_t* d_u_off, double* U, int* d_k_out, double thr, int kmax,
-                      int* d_cap_flag, cudaStream_t s);
+
+// ---- stacked QR and truncated SVD (svd.cu) ----------------------------------
+// One row block of a stacked matrix: rows x c at p (column-major, leading dimension ld).
+struct RowSeg {
+    const double* p;
+    int rows;
+    int ld;
+};
+// A matrix given as the stack of segments [seg_begin, seg_end), each with c columns.
+struct StackJob {
+    int seg_begin, seg_end;
+    int c;
+    double* out;      // stacked_r: R (c x c, upper, zeros below); stacked_svd_trunc: U (c x k)
+    int ldo;          // leading dimension of out
+    int* k_out;       // stacked_svd_trunc: number of kept singular vectors
+    double* sv_out;   // stacked_svd_trunc: all c singular values, descending (may be null)
+};
+struct StackWork {
+    DevBuf<StackJob> d_jobs, d_jobs2;
+    DevBuf<RowSeg> d_segs, d_segs2;
+    DevBuf<double> parts, gwork;
+    Stager st_jobs, st_jobs2, st_segs, st_segs2;
+};
+// R factors (Householder) of every job's stacked matrix (c <= 256 columns; any row count:
+// matrices above a few thousand rows are split over several CTAs).  The stacked matrices must
+// not overlap the outputs.  Host vectors; device pointers inside.
+void stacked_r(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, cudaStream_t s);
+// For every job, W^T is the stacked matrix (W is c x rows, c <= 96): the left singular vectors
+// of W with singular value > thr (at most kmax; *cap_flag = 1 if the cap removed one), sorted by
+// descending singular value, written to out (c x k); k to *k_out.  QR of W^T, then one-sided
+// Jacobi on the c x c triangle.
+void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, double thr,
+                       int kmax, int* d_cap_flag, cudaStream_t s);
+int svd_max_order();
 
 // ---- small helper kernels (misc.cu) ------------------------------------------
 void fill_zero(double* p, size_t count, cudaStream_t s);
@@ -226,10 +262,6 @@ void scatter_rows(int64_t N, int ncols, const int32_t* d_perm, const double* src
                   double* dst, int64_t ldd, cudaStream_t s);
 // sum over blocks of |x|^2 and a flag for non-finite values: out[0] += ..., out[1] = 1 if nan
 void scan_finite(int64_t N, int ncols, const double* x, int64_t ld, int* d_flag, cudaStream_t s);
-// out[i] = sum_{j in list i} in[j] for count matrices of size len_i
-void sum_lists(int count, const int64_t* d_out_off, const int* d_len, const int* d_begin,
-               const int* d_end, const int64_t* d_in_off, const double* in, double* out,
-               int accumulate, cudaStream_t s);
 // norms of vectors: out[j] = ||x[:, j]||^2
 void col_sqnorms(int64_t N, int ncols, const double* x, int64_t ld, double* out, cudaStream_t s);
 void scale_cols(int64_t N, int ncols, double* x, int64_t ld, const double* d_scale, cudaStream_t s);
@@ -248,6 +280,5 @@ uint64_t rng_key(uint64_t seed, int stream_id, int level);
 // C (n x n, lower, ld n) with C C^T = A for a symmetric positive semidefinite A (ld n, lower
 // triangle used and overwritten); pivots at rounding level leave their column of C zero.
 void psd_cholesky(double* A, int n, double* C, cudaStream_t s);
-int eig_max_order();
 
 }  // namespace h2

@@ -7,11 +7,8 @@
 //   panel after block Gram-Schmidt projection against the columns found so far.
 // * panel_colnorm_max: largest column norm of each panel (the a-posteriori
 //   range test of the adaptive sampler).
-// * jacobi_eig_trunc: cyclic two-sided Jacobi eigen-decomposition (Jacobi 1846;
-//   parallel round-robin ordering of Brent and Luk 1985) of the small Gram
-//   matrices of block rows, one CTA per matrix, keeping the leading
-//   eigenvectors above a threshold: the truncation step of the recompression
-//   (Section 3.2: "truncated to the target accuracy via an SVD").
+// * align_signs: the sign convention of the range bases (non-negative diagonal
+//   of R in Y = QR).
 #include <cfloat>
 
 #include <mutex>
@@ -159,151 +156,6 @@ __global__ void __launch_bounds__(NT) colnorm_max_kernel(const int64_t* __restri
         double mx = 0.0;
         for (int k = 0; k < c; ++k) mx = fmax(mx, sqrt(res[k]));
         out[blockIdx.x] = mx;
-    }
-}
-
-// Jacobi eigen-decomposition of one symmetric matrix per CTA held in shared memory.
-constexpr int EIG_MAXN = 96;
-
-__global__ void __launch_bounds__(NT) jacobi_kernel(const int64_t* __restrict__ a_off,
-                                                     const int* __restrict__ nn,
-                                                     const double* __restrict__ Aall,
-                                                     const int64_t* __restrict__ u_off,
-                                                     double* __restrict__ Uall, int* __restrict__ kout,
-                                                     double thr, int kmax, int* __restrict__ cap_flag) {
-    extern __shared__ double smem[];
-    const int n = nn[blockIdx.x];
-    const int np = n + (n & 1);          // even order for the round-robin schedule
-    const int ld = np + 1;
-    double* A = smem;                     // np x np, ld
-    double* V = smem + np * ld;           // np x np, ld
-    __shared__ double cs[EIG_MAXN / 2], sn[EIG_MAXN / 2];
-    __shared__ int pp[EIG_MAXN / 2], qq[EIG_MAXN / 2];
-    __shared__ double red[NW * 2];
-    __shared__ int rank[EIG_MAXN];
-    __shared__ int kk;
-    const double* Ag = Aall + a_off[blockIdx.x];
-    for (int e = threadIdx.x; e < np * np; e += NT) {
-        const int i = e % np, j = e / np;
-        A[i + j * ld] = (i < n && j < n) ? Ag[i + (int64_t)j * n] : 0.0;
-        V[i + j * ld] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (n == 0) {
-        if (threadIdx.x == 0) kout[blockIdx.x] = 0;
-        return;
-    }
-    const int half = np / 2;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        // convergence: off-diagonal mass relative to the whole matrix
-        double off = 0.0, tot = 0.0;
-        for (int e = threadIdx.x; e < np * np; e += NT) {
-            const int i = e % np, j = e / np;
-            const double a = A[i + j * ld];
-            tot = fma(a, a, tot);
-            if (i != j) off = fma(a, a, off);
-        }
-        double v2[2] = {off, tot};
-        {
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                double x = v2[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) red[w * 2 + q] = x;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double a = 0.0, b = 0.0;
-                for (int ww = 0; ww < NW; ++ww) { a += red[ww * 2]; b += red[ww * 2 + 1]; }
-                red[0] = a;
-                red[1] = b;
-            }
-            __syncthreads();
-        }
-        const bool done = !(red[0] > 1e-30 * red[1]);
-        __syncthreads();
-        if (done) break;
-        for (int r = 0; r < np - 1; ++r) {
-            // rotation parameters of the round's disjoint pairs
-            if (threadIdx.x < half) {
-                const int k = threadIdx.x;
-                int p, q;
-                if (k == 0) { p = np - 1; q = r; }
-                else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
-                if (p > q) { const int t = p; p = q; q = t; }
-                const double apq = A[p + q * ld];
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0) {
-                    const double app = A[p + p * ld], aqq = A[q + q * ld];
-                    const double theta = (aqq - app) / (2.0 * apq);
-                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-                    c = 1.0 / sqrt(fma(t, t, 1.0));
-                    s = t * c;
-                }
-                pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
-            }
-            __syncthreads();
-            // A <- A J and V <- V J (columns p, q of every pair)
-            for (int e = threadIdx.x; e < np * half; e += NT) {
-                const int row = e % np, k = e / np;
-                const int p = pp[k], q = qq[k];
-                const double c = cs[k], s = sn[k];
-                const double ap = A[row + p * ld], aq = A[row + q * ld];
-                A[row + p * ld] = c * ap - s * aq;
-                A[row + q * ld] = s * ap + c * aq;
-                const double vp = V[row + p * ld], vq = V[row + q * ld];
-                V[row + p * ld] = c * vp - s * vq;
-                V[row + q * ld] = s * vp + c * vq;
-            }
-            __syncthreads();
-            // A <- J^T A (rows p, q of every pair)
-            for (int e = threadIdx.x; e < np * half; e += NT) {
-                const int col = e % np, k = e / np;
-                const int p = pp[k], q = qq[k];
-                const double c = cs[k], s = sn[k];
-                const double ap = A[p + col * ld], aq = A[q + col * ld];
-                A[p + col * ld] = c * ap - s * aq;
-                A[q + col * ld] = s * ap + c * aq;
-            }
-            __syncthreads();
-            if (threadIdx.x < half) {
-                const int p = pp[threadIdx.x], q = qq[threadIdx.x];
-                A[p + q * ld] = 0.0;
-                A[q + p * ld] = 0.0;
-            }
-            __syncthreads();
-        }
-    }
-    // order eigenvalues descending (ties by index), keep those above thr
-    if (threadIdx.x < n) {
-        const int i = threadIdx.x;
-        const double li = A[i + i * ld];
-        int rnk = 0;
-        for (int j = 0; j < n; ++j) {
-            const double lj = A[j + j * ld];
-            if (lj > li || (lj == li && j < i)) ++rnk;
-        }
-        rank[i] = rnk;
-    }
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int j = 0; j < n; ++j) k += (A[j + j * ld] > thr) ? 1 : 0;
-        if (k > kmax) {
-            atomicExch(cap_flag, 1);
-            k = kmax;
-        }
-        kk = k;
-        kout[blockIdx.x] = k;
-    }
-    __syncthreads();
-    double* U = Uall + u_off[blockIdx.x];
-    const int k = kk;
-    for (int e = threadIdx.x; e < n * n; e += NT) {
-        const int row = e % n, i = e / n;
-        const int rnk = rank[i];
-        if (rnk < k) U[row + (int64_t)rnk * n] = V[row + i * ld];
     }
 }
 
@@ -594,24 +446,30 @@ void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c,
     after_launch("colnorm_max");
 }
 
-void jacobi_eig_trunc(int count, const int64_t* d_a_off, const int* d_n, int max_n, const double* A,
-                      const int64_t* d_u_off, double* U, int* d_k_out, double thr, int kmax,
-                      int* d_cap_flag, cudaStream_t s) {
-    if (count <= 0) return;
-    if (max_n < 0 || max_n > EIG_MAXN) fail(H2_ERR_INVALID_ARG, "jacobi: matrix order above 96");
-    static std::once_flag attr_set;
-    std::call_once(attr_set, [&] {
-        const int top = 2 * EIG_MAXN * (EIG_MAXN + 1) * (int)sizeof(double);
-        H2_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, top));
-    });
-    // shared memory for the largest matrix of this launch only: more CTAs per SM when they are small
-    const int np = max_n + (max_n & 1);
-    const size_t smem = std::max<size_t>(2 * (size_t)np * (np + 1) * sizeof(double), 16);
-    jacobi_kernel<<<count, NT, smem, s>>>(d_a_off, d_n, A, d_u_off, U, d_k_out, thr, kmax, d_cap_flag);
-    after_launch("jacobi_eig");
+namespace {
+
+// Column j of Q is negated when q_j^T y_j < 0 (one CTA per column).
+__global__ void __launch_bounds__(NT) align_signs_kernel(const SignItem* __restrict__ items, double* __restrict__ Q,
+                                                         const double* __restrict__ Y) {
+    __shared__ double sh[NW];
+    __shared__ double res[1];
+    const SignItem it = items[blockIdx.x];
+    double p[1] = {0.0};
+    for (int i = threadIdx.x; i < it.rows; i += NT) p[0] = fma(Q[it.q_off + i], Y[it.y_off + i], p[0]);
+    block_sum<1>(p, sh, res);
+    if (res[0] < 0.0)
+        for (int i = threadIdx.x; i < it.rows; i += NT) Q[it.q_off + i] = -Q[it.q_off + i];
 }
 
-int eig_max_order() { return EIG_MAXN; }
+}  // namespace
+
+void align_signs(int count, const SignItem* d_items, double* Q, const double* Y, cudaStream_t s) {
+    if (count <= 0) return;
+    align_signs_kernel<<<count, NT, 0, s>>>(d_items, Q, Y);
+    after_launch("align_signs");
+}
+
+
 
 namespace {
 

@@ -1,0 +1,414 @@
+// Batched R factors of stacked row blocks and truncated SVDs of block-row factors.
+//
+// The recompression of Section 3.2 needs, for every box, (i) the R factor of the
+// column side of its far block row (the QR downsweep) and (ii) the leading left
+// singular vectors of the weighted block-row factor W = [P_lp R_lp^T]_lp (the SVD
+// upsweep).  Both are computed here without forming a Gram matrix, so that
+// singular values are resolved to about eps * sigma_max instead of
+// sqrt(eps) * sigma_max:
+//
+//  * stacked_r: Householder QR (LAPACK dlarfg convention) of a matrix given as a
+//    stack of row blocks.  One CTA per matrix streams its rows through shared
+//    memory in chunks under the running c x c triangle R (the incremental form of
+//    a tall-skinny QR: every chunk is annihilated against R by c reflectors that
+//    touch one row of R and the chunk).  Matrices taller than a few thousand rows
+//    are first split over several CTAs whose R factors are stacked once more.
+//  * stacked_svd_trunc: the same QR of W^T (W is m x sum(q), m <= 96), then the
+//    one-sided Jacobi method (Hestenes 1958; round-robin ordering of Brent and
+//    Luk 1985) on the columns of the m x m lower triangle R^T (W = R^T Q^T): at
+//    convergence R^T V = U Sigma with orthogonal columns, whose normalised values
+//    are the left singular vectors of W.  Rotating R^T rather than R converges
+//    in about ten sweeps on the graded block rows (columns of R are not graded)
+//    and needs no accumulated rotation matrix.  The vectors with singular value
+//    above the threshold (at most kmax) are kept, sorted by descending value.
+#include <algorithm>
+#include <cfloat>
+#include <mutex>
+
+#include "common.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr int SQ_NT = 256;
+constexpr int SQ_NW = SQ_NT / 32;
+constexpr int SVD_MAXC = 96;
+constexpr int kSplitRows = 4096;   // a single matrix taller than this is split over several CTAs
+constexpr int kPartRows = 1024;    // rows per CTA of a split matrix
+constexpr size_t kSmemCap = 200 * 1024;
+
+constexpr int kSmemMaxC = 144;     // wider matrices keep their working matrix in global memory
+constexpr int kMaxC = 1024;
+constexpr int kGlobalCtas = 152;   // CTAs of a global-memory launch (one working matrix each)
+
+// rows of a chunk streamed under R: shared memory holds (c + chunk) x c doubles
+__host__ __device__ inline int chunk_rows(int c) { return c <= 96 ? 64 : (c <= 128 ? 32 : (c <= kSmemMaxC ? 16 : 64)); }
+// leading dimension of the working matrix [R; chunk]: odd, so that the columns of a warp's
+// column pairs fall in different shared-memory banks
+__host__ __device__ inline int work_ld(int c) { return (c + chunk_rows(c)) | 1; }
+
+// Householder reflector of column j of the stacked [R; chunk] (rows c .. c+ch-1 hold the
+// chunk), computed by one warp: zeroes the chunk part of column j against R[j, j].
+__device__ inline void reflector(double* A, int lda, int c, int ch, int j, double* tau, int lane) {
+    double x2 = 0.0;
+    for (int i = lane; i < ch; i += 32) {
+        const double y = A[c + i + (int64_t)j * lda];
+        x2 = fma(y, y, x2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    const double alpha = A[j + (int64_t)j * lda];
+    double tj = 0.0, scale = 0.0, beta = alpha;
+    if (x2 > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
+        tj = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+    }
+    if (tj != 0.0)
+        for (int i = lane; i < ch; i += 32) A[c + i + (int64_t)j * lda] *= scale;
+    __syncwarp();
+    if (lane == 0) {
+        tau[j] = tj;
+        A[j + (int64_t)j * lda] = beta;
+    }
+    __syncwarp();
+}
+
+// Apply reflector j (v = [1 at row j; chunk rows of column j]) to column k of [R; chunk].
+__device__ inline void apply_reflector(double* A, int lda, int c, int ch, int j, int k, double tj, int lane) {
+    double w = 0.0;
+    for (int i = lane; i < ch; i += 32) w = fma(A[c + i + (int64_t)j * lda], A[c + i + (int64_t)k * lda], w);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    w += A[j + (int64_t)k * lda];
+    const double f = tj * w;
+    for (int i = lane; i < ch; i += 32)
+        A[c + i + (int64_t)k * lda] = fma(-f, A[c + i + (int64_t)j * lda], A[c + i + (int64_t)k * lda]);
+    __syncwarp();
+    if (lane == 0) A[j + (int64_t)k * lda] -= f;
+    __syncwarp();
+}
+
+// R factor (upper c x c, rows 0..c-1 of A, leading dimension lda = c + chunk rows) of the
+// stacked row blocks segs[b..e).  Entry state of A is irrelevant; every thread returns
+// after a barrier with R complete.
+__device__ void stacked_qr(double* A, int lda, int c, const RowSeg* __restrict__ segs, int b, int e,
+                           double* tau) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ch = chunk_rows(c);
+    for (int x = threadIdx.x; x < c * c; x += SQ_NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
+    __syncthreads();
+    for (int sgi = b; sgi < e; ++sgi) {
+        const RowSeg sg = segs[sgi];
+        for (int r0 = 0; r0 < sg.rows; r0 += ch) {
+            const int h = min(ch, sg.rows - r0);
+            // load the chunk (zero rows beyond its end)
+            for (int x = threadIdx.x; x < ch * c; x += SQ_NT) {
+                const int i = x % ch, k = x / ch;
+                A[c + i + (int64_t)k * lda] = (i < h) ? sg.p[r0 + i + (int64_t)k * sg.ld] : 0.0;
+            }
+            __syncthreads();
+            if (warp == 0) reflector(A, lda, c, ch, 0, tau, lane);
+            __syncthreads();
+            for (int j = 0; j < c; ++j) {
+                const double tj = tau[j];
+                // columns k > j, owned by warp k % SQ_NW; the owner of j + 1 forms its reflector
+                // right after updating it, so one barrier per column suffices
+                int k = j + 1 + ((warp - (j + 1)) % SQ_NW + SQ_NW) % SQ_NW;
+                for (; k < c; k += SQ_NW) {
+                    if (tj != 0.0) apply_reflector(A, lda, c, ch, j, k, tj, lane);
+                    if (k == j + 1) reflector(A, lda, c, ch, k, tau, lane);
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// One CTA per job; with gwork the CTAs loop over the jobs, each with its own working matrix
+// in global memory (gstride doubles).  The c x c triangle of the incremental QR holds the
+// rank of the stack in the rows of the columns where it appears (a stack with fewer rows
+// than columns, or with leading zero columns, leaves other rows zero), so the output is
+// compacted: the min(c, rows) rows of largest norm are written first (R^T R, the only use of
+// R, does not depend on the order of its rows) and the remaining rows -- zero in exact
+// arithmetic -- are written as zeros.
+__global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __restrict__ jobs, int njobs,
+                                                          const RowSeg* __restrict__ segs, double* __restrict__ gwork,
+                                                          int64_t gstride) {
+    extern __shared__ double smem[];
+    __shared__ double tau[kMaxC];
+    __shared__ double rn[kMaxC];
+    __shared__ int src[kMaxC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int jbi = blockIdx.x; jbi < njobs; jbi += gridDim.x) {
+        const StackJob jb = jobs[jbi];
+        const int c = jb.c;
+        if (c <= 0) continue;
+        const int lda = work_ld(c);
+        double* A = gwork ? gwork + (int64_t)blockIdx.x * gstride : smem;
+        stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
+        int rows = 0;
+        for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs[i].rows;
+        const int reff = min(c, rows);
+        for (int j = warp; j < c; j += SQ_NW) {   // squared norms of the rows of R
+            double x = 0.0;
+            for (int k = j + lane; k < c; k += 32) {
+                const double a = A[j + (int64_t)k * lda];
+                x = fma(a, a, x);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) rn[j] = x;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < c; j += SQ_NT) {   // rank by descending norm (ties by index)
+            const double x = rn[j];
+            int r = 0;
+            for (int i = 0; i < c; ++i) {
+                const double y = rn[i];
+                r += (y > x || (y == x && i < j)) ? 1 : 0;
+            }
+            if (r < reff) src[r] = j;
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < c * c; x += SQ_NT) {
+            const int r = x % c, k = x / c;
+            jb.out[r + (int64_t)k * jb.ldo] = (r < reff) ? A[src[r] + (int64_t)k * lda] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __restrict__ jobs,
+                                                            const RowSeg* __restrict__ segs, double thr, int kmax,
+                                                            int* __restrict__ cap_flag) {
+    extern __shared__ double smem[];
+    __shared__ double tau[SVD_MAXC];
+    __shared__ double sig[SVD_MAXC + 1];
+    __shared__ int rank[SVD_MAXC];
+    __shared__ int kk;
+    const StackJob jb = jobs[blockIdx.x];
+    const int c = jb.c;
+    if (c <= 0) {
+        if (threadIdx.x == 0) *jb.k_out = 0;
+        return;
+    }
+    const int np = c + (c & 1);          // even order for the round-robin schedule (zero column added)
+    const int lda = work_ld(c);
+    const int ldb = c | 1;
+    double* A = smem;                         // lda x c: [R; chunk]
+    double* B = smem + (int64_t)lda * c;      // ldb x np: R^T and a zero padding column
+    stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
+    for (int x = threadIdx.x; x < c * np; x += SQ_NT) {
+        const int i = x % c, k = x / c;
+        B[i + (int64_t)k * ldb] = (k < c && i >= k) ? A[k + (int64_t)i * lda] : 0.0;
+    }
+    __syncthreads();
+    // one-sided Jacobi on the columns of B = R^T (W = B Q^T): 8 threads per column pair,
+    // 32 pairs at a time; at convergence the columns of B V are orthogonal and their
+    // normalised values are the left singular vectors of W
+    const int g = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    const int half = np / 2;
+    const double tol = 4.0 * sqrt((double)c) * DBL_EPSILON;   // orthogonality reached: no rotation
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        int rotated = 0;
+        for (int r = 0; r < np - 1; ++r) {
+            for (int k0 = 0; k0 < half; k0 += 32) {
+                const int k = k0 + g;
+                const bool act = k < half;
+                int p = 0, q = 0;
+                if (act) {
+                    if (k == 0) { p = np - 1; q = r; }
+                    else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+                    if (p > q) { const int t = p; p = q; q = t; }
+                }
+                double al = 0.0, be = 0.0, ga = 0.0;
+                if (act)
+                    for (int i = sub; i < c; i += 8) {
+                        const double ap = B[i + (int64_t)p * ldb], aq = B[i + (int64_t)q * ldb];
+                        al = fma(ap, ap, al);
+                        be = fma(aq, aq, be);
+                        ga = fma(ap, aq, ga);
+                    }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (act && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                    const double cs = 1.0 / sqrt(fma(t, t, 1.0));
+                    const double sn = cs * t;
+                    for (int i = sub; i < c; i += 8) {
+                        const double ap = B[i + (int64_t)p * ldb], aq = B[i + (int64_t)q * ldb];
+                        B[i + (int64_t)p * ldb] = cs * ap - sn * aq;
+                        B[i + (int64_t)q * ldb] = sn * ap + cs * aq;
+                    }
+                    rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        if (!__syncthreads_or(rotated)) break;
+    }
+    // singular values = column norms; rank by descending value (ties by index)
+    for (int j0 = 0; j0 < np; j0 += 32) {   // uniform trip count: the shuffles below need every lane
+        const int j = j0 + g;
+        double s2 = 0.0;
+        if (j < np)
+            for (int i = sub; i < c; i += 8) {
+                const double a = B[i + (int64_t)j * ldb];
+                s2 = fma(a, a, s2);
+            }
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+        if (sub == 0 && j < np) sig[j] = sqrt(s2);
+    }
+    __syncthreads();
+    if (threadIdx.x < c) {
+        const int i = threadIdx.x;
+        const double si = sig[i];
+        int rk = 0;
+        for (int j = 0; j < c; ++j) {
+            const double sj = sig[j];
+            if (sj > si || (sj == si && j < i)) ++rk;
+        }
+        rank[i] = rk;
+        if (jb.sv_out) jb.sv_out[rk] = si;
+    }
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int j = 0; j < c; ++j) k += (sig[j] > thr) ? 1 : 0;
+        if (k > kmax) {
+            atomicExch(cap_flag, 1);
+            k = kmax;
+        }
+        kk = k;
+        *jb.k_out = k;
+    }
+    __syncthreads();
+    const int k = kk;
+    for (int x = threadIdx.x; x < c * c; x += SQ_NT) {
+        const int row = x % c, j = x / c;
+        const int rk = rank[j];
+        if (rk < k) jb.out[row + (int64_t)rk * jb.ldo] = B[row + (int64_t)j * ldb] / sig[j];
+    }
+}
+
+size_t qr_smem_bytes(int c) { return (size_t)work_ld(c) * c * sizeof(double); }
+
+size_t svd_smem_bytes(int c) {
+    const int np = c + (c & 1);
+    return (size_t)work_ld(c) * c * sizeof(double) + (size_t)(c | 1) * np * sizeof(double);
+}
+
+}  // namespace
+
+void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& segs_in, StackWork& w,
+               cudaStream_t s) {
+    if (jobs_in.empty()) return;
+    // A single matrix taller than kSplitRows is split over several CTAs (part jobs of at most
+    // kPartRows rows each, c x c R factors in w.parts); its final job stacks the part factors.
+    std::vector<StackJob> jobs, parts;
+    std::vector<RowSeg> segs, psegs;
+    struct Split { size_t job; size_t first_part; int count; };
+    std::vector<Split> splits;
+    for (const StackJob& jb : jobs_in) {
+        if (jb.c <= 0) continue;
+        if (jb.c > kMaxC) fail(H2_ERR_INVALID_ARG, "stacked_r: more than 1024 columns");
+        int64_t rows = 0;
+        for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs_in[i].rows;
+        StackJob j = jb;
+        if (rows <= kSplitRows) {
+            j.seg_begin = (int)segs.size();
+            for (int i = jb.seg_begin; i < jb.seg_end; ++i) segs.push_back(segs_in[i]);
+            j.seg_end = (int)segs.size();
+            jobs.push_back(j);
+            continue;
+        }
+        Split sp{jobs.size(), parts.size(), 0};
+        for (int i = jb.seg_begin; i < jb.seg_end; ++i) {
+            const RowSeg sg = segs_in[i];
+            for (int r0 = 0; r0 < sg.rows; r0 += kPartRows) {
+                psegs.push_back(RowSeg{sg.p + r0, std::min(kPartRows, sg.rows - r0), sg.ld});
+                parts.push_back(StackJob{(int)psegs.size() - 1, (int)psegs.size(), jb.c, nullptr, jb.c, nullptr, nullptr});
+                ++sp.count;
+            }
+        }
+        splits.push_back(sp);
+        jobs.push_back(j);   // segments filled once the part factors have addresses
+    }
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
+        H2_CUDA(cudaFuncSetAttribute(stacked_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    });
+    auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
+                      DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
+        if (js.empty()) return;
+        int cm = 0;
+        for (auto& j : js) cm = std::max(cm, j.c);
+        upload(dj, js, s, stj);
+        upload(dsg, ss, s, sts);
+        size_t dyn = qr_smem_bytes(cm);
+        double* gw = nullptr;
+        int64_t gstride = 0;
+        unsigned grid = (unsigned)js.size();
+        if (cm > kSmemMaxC) {   // wide matrices: the working matrices live in global memory
+            grid = std::min<unsigned>(grid, kGlobalCtas);
+            gstride = (int64_t)work_ld(cm) * cm;
+            w.gwork.reserve((size_t)gstride * grid);
+            gw = w.gwork.p;
+            dyn = 0;
+        }
+        stacked_r_kernel<<<grid, SQ_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p, gw, gstride);
+        after_launch("stacked_r");
+    };
+    if (!parts.empty()) {
+        int64_t elems = 0;
+        for (auto& pj : parts) elems += (int64_t)pj.c * pj.c;
+        w.parts.reserve((size_t)elems);
+        int64_t off = 0;
+        for (auto& pj : parts) {
+            pj.out = w.parts.p + off;
+            off += (int64_t)pj.c * pj.c;
+        }
+        launch(parts, psegs, w.d_jobs2, w.d_segs2, w.st_jobs2, w.st_segs2);
+        for (const Split& sp : splits) {
+            StackJob& fj = jobs[sp.job];
+            fj.seg_begin = (int)segs.size();
+            for (int i = 0; i < sp.count; ++i) {
+                const StackJob& pj = parts[sp.first_part + i];
+                const int prow = psegs[pj.seg_begin].rows;
+                segs.push_back(RowSeg{pj.out, std::min(prow, pj.c), pj.c});
+            }
+            fj.seg_end = (int)segs.size();
+        }
+    }
+    launch(jobs, segs, w.d_jobs, w.d_segs, w.st_jobs, w.st_segs);
+}
+
+void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, double thr,
+                       int kmax, int* d_cap_flag, cudaStream_t s) {
+    if (jobs.empty()) return;
+    int cm = 0;
+    for (auto& j : jobs) cm = std::max(cm, j.c);
+    if (cm > SVD_MAXC) fail(H2_ERR_INVALID_ARG, "stacked_svd: matrix order above 96");
+    upload(w.d_jobs, jobs, s, w.st_jobs);
+    upload(w.d_segs, segs, s, w.st_segs);
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
+        H2_CUDA(cudaFuncSetAttribute(stacked_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)svd_smem_bytes(SVD_MAXC)));
+    });
+    const size_t smem = std::max<size_t>(svd_smem_bytes(std::max(cm, 1)), 16);
+    stacked_svd_kernel<<<(unsigned)jobs.size(), SQ_NT, smem, s>>>(w.d_jobs.p, w.d_segs.p, thr, kmax, d_cap_flag);
+    after_launch("stacked_svd");
+}
+
+int svd_max_order() { return SVD_MAXC; }
+
+}  // namespace h2

@@ -60,10 +60,12 @@ def nested_bases(tree: ClusterTree, k: int, seed: int):
     return U
 
 
-def planted_h2(tree: ClusterTree, part: Partition, k: int, near_rank: int, seed: int) -> np.ndarray:
+def planted_h2(tree: ClusterTree, part: Partition, k: int, near_rank: int, seed: int, grade: float = 1.0) -> np.ndarray:
     """Symmetric H^2 matrix on the given partition: far blocks U_t S U_s^T with nested
     orthonormal bases of rank k; off-diagonal near blocks of rank near_rank; dense
-    symmetric diagonal leaf blocks."""
+    symmetric diagonal leaf blocks.  With grade < 1 the couplings are S = G_t M G_s with
+    G = diag(grade^i): basis direction i of every box carries weight grade^i, so the far
+    block rows have geometrically graded singular values."""
     rng = np.random.default_rng(seed + 1)
     U = nested_bases(tree, k, seed)
     L = tree.L
@@ -73,6 +75,7 @@ def planted_h2(tree: ClusterTree, part: Partition, k: int, near_rank: int, seed:
             if t < s:
                 continue
             S = rng.standard_normal((U[l][t].shape[1], U[l][s].shape[1]))
+            S = (grade ** np.arange(S.shape[0]))[:, None] * S * (grade ** np.arange(S.shape[1]))[None, :]
             B = U[l][t] @ S @ U[l][s].T
             A[tree.rows(l, t), tree.rows(l, s)] = B
             A[tree.rows(l, s), tree.rows(l, t)] = B.T

@@ -164,3 +164,85 @@ def test_mutation_transposed_piece_is_caught(monkeypatch):
     monkeypatch.setattr(O, "peel", bad_peel)
     h, res = _build(A, n, leaf, ADM_WEAK, q0=8, kmax=16)
     assert _rel(A, O.expand_dense(h)) > 1e-3
+
+
+@pytest.mark.parametrize("adm", [ADM_STRONG, ADM_WEAK])
+def test_rank_replay_reproduces_adaptive_build(adm):
+    """Rank replay (the probe counts, norm estimate and basis ranks of a finished construction
+    given as data) reproduces that construction: same samples and ranks, same matrix to
+    rounding.  This is the oracle mode that consumes another implementation's decisions."""
+    n, m = 24, 120
+    mask = W.sensor_mask(n * n, m, 41)
+    op = O.HeatHessian(n, 0.01, 0.5, 0.01, mask)
+    h, res = O.build(op, W.grid_coords(n), 32, adm, 0.7, 1e-6, 24, 16, 16, 256, True, 3)
+    probes = [res.range_probes.get(l, 0) for l in range(h.tree.L + 1)]
+    assert any(res.passed[l] == -1 for l in range(1, h.tree.L + 1)) or min(probes[1:]) > 0
+    hr, rr = O.replay_build(op, W.grid_coords(n), 32, adm, 0.7, 1e-6, 24, 3, res.norm_est, probes,
+                            [np.asarray(k) for k in h.k])
+    assert rr.samples == res.samples - res.norm_its
+    for l in range(h.tree.L + 1):
+        np.testing.assert_array_equal(hr.k[l], h.k[l])
+    A, B = O.expand_dense(h), O.expand_dense(hr)
+    assert np.linalg.norm(A - B, 2) <= 1e-13 * res.norm_est
+
+
+def test_rank_replay_keeps_given_ranks_below_threshold():
+    """Replayed ranks override the threshold: one rank fewer at every leaf changes the result
+    by about the dropped singular value (a planted mistake that the 1e-12 comparison sees)."""
+    n, m = 24, 120
+    mask = W.sensor_mask(n * n, m, 41)
+    op = O.HeatHessian(n, 0.01, 0.5, 0.01, mask)
+    h, res = O.build(op, W.grid_coords(n), 32, ADM_STRONG, 0.7, 1e-6, 24, 16, 16, 256, True, 3)
+    L = h.tree.L
+    probes = [res.range_probes.get(l, 0) for l in range(L + 1)]
+    ranks = [np.asarray(k).copy() for k in h.k]
+    ranks[L] = np.maximum(ranks[L] - 1, 0)
+    for l in range(1, L):   # parents cannot keep more than their children offer
+        ranks[l] = np.minimum(ranks[l], ranks[l + 1][0::2] + ranks[l + 1][1::2])
+    hr, _ = O.replay_build(op, W.grid_coords(n), 32, ADM_STRONG, 0.7, 1e-6, 24, 3, res.norm_est, probes, ranks)
+    np.testing.assert_array_equal(hr.k[L], ranks[L])
+    d = np.linalg.norm(O.expand_dense(h) - O.expand_dense(hr), 2) / res.norm_est
+    assert d > 1e-9
+
+
+def test_tight_tolerance_graded_planted():
+    """A planted H^2 matrix whose far block rows have geometrically graded singular values
+    (grade 0.2 per basis direction): at tol 1e-9 dozens of kept singular values lie between
+    tau_basis and 1e-7 ||A||, below the square root of the rounding unit times the largest
+    one, and the construction still meets the tolerance against the dense matrix."""
+    n, leaf = 16, 16
+    tree = ClusterTree(W.grid_coords(n), leaf)
+    A = planted.planted_h2(tree, Partition(tree, ADM_STRONG, 0.7), 14, 2, 4, grade=0.2)
+    nrm = np.linalg.norm(A, 2)
+    h, res = O.build(O.DenseOperator(A), W.grid_coords(n), leaf, ADM_STRONG, 0.7, 1e-9, 32, 16, 16, 256, True, 5,
+                     norm_est=nrm)
+    svs = np.concatenate(list(h.sv.values()))
+    assert np.sum((svs > res.tau_basis) & (svs < 1e-7 * nrm)) >= 20
+    assert np.linalg.norm(O.expand_dense(h) - A, 2) <= 1e-9 * nrm
+
+
+def test_replay_sensitivity_adaptive_64():
+    """How closely two correct implementations can agree at the 64^2 adaptive configuration
+    (leaf 64, strong 0.7, tol 1e-6): the oracle's own rank-replay construction moves by more
+    than 1e-12 relative when the operator's products are perturbed at the level of one
+    rounding (1e-16 relative).  The range bases of the finest levels have more probes than
+    the sampled blocks' numerical rank, and the projection pass applies all sibling blocks'
+    bases at once, so the coarse levels' residual couples every basis vector (weak ones
+    included) into the pieces.  The GPU parity bound for this configuration, 2e-11, is a
+    small multiple of this measured sensitivity; at 32^2 the same comparison is 1e-12."""
+    n, m = 64, 256
+    mask = W.sensor_mask(n * n, m, 1002)
+    op = O.HeatHessian(n, 0.01, 0.5, 0.01, mask)
+    h, res = O.build(op, W.grid_coords(n), 64, ADM_STRONG, 0.7, 1e-6, 32, 32, 16, 256, True, 7)
+    L = h.tree.L
+    probes = [res.range_probes.get(l, 0) for l in range(L + 1)]
+    rng = np.random.default_rng(5)
+
+    def perturbed(X):
+        Y = op(X)
+        return Y * (1.0 + 1e-16 * rng.standard_normal(Y.shape))
+
+    hp, _ = O.replay_build(perturbed, W.grid_coords(n), 64, ADM_STRONG, 0.7, 1e-6, 32, 7, res.norm_est, probes,
+                           [np.asarray(k) for k in h.k])
+    d = np.linalg.norm(O.expand_dense(hp) - O.expand_dense(h), 2) / res.norm_est
+    assert 1e-12 < d < 1e-11
