@@ -37,13 +37,35 @@ import workloads as W  # noqa: E402
 
 METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
 CFG = W.MEDIUM_N256
-# DRAM bytes (read + write) per gemm_tiles_kernel launch of the bench command, from an ncu capture
-# of every launch of that kernel (dram__bytes_read.sum + dram__bytes_write.sum, 1,510 launches);
-# reset to None whenever the kernel changes
-GEMM_TRAFFIC_PER_LAUNCH = 27.32e6
+# DRAM bytes (read + write) of one launch of the roofline's kernel (mv_leaf_near_kernel, FP64,
+# nrhs 256, 256 x 256 workload) from an ncu capture of that launch (profiles/); None until it
+# is captured, and reset to None whenever the kernel changes
+MATVEC_TRAFFIC_PER_LAUNCH = None
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
+
+
+def fp64_peak_measured(torch, stream) -> float:
+    """Dense FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, 4096 x 4096 float64), best of 5,
+    CUDA events on the current stream."""
+    n = 4096
+    g = torch.Generator(device="cuda").manual_seed(1)
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(a, b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
 
 
 def peaks():
@@ -351,7 +373,7 @@ def learned_ranks_section(h2, torch, stream) -> dict:
         Gs = h2.build_batched(ops, trees, b.tol, fine)
         for q, t, G in zip(chunk, trees, Gs):
             f = h2.rank_features(t, q.kappa * q.T, q.m / q.N, b.tol)
-            lv, tg = h2.rank_targets(G.stats())
+            lv, tg = h2.rank_targets(G)
             feats.append(f[lv])
             targ += tg
             G.close()
@@ -521,55 +543,128 @@ def inversion_section(h2, torch, stream) -> dict:
     return out
 
 
-def cpu_baseline_sample(n_sample: int = 128, nrhs_list=(1, 32, 256), reps: int = 1) -> dict:
-    """The oracle as it stands on a bounded sample of the workload: the same operator family
-    (kappa 0.01, 6.25 % sensors, leaf 64, strong 0.7, tol 1e-6) at n = 128, built by the oracle,
-    then its matvec timed for nrhs 1, 32, 256 (algorithmic bytes as for the GPU)."""
+def _spec(cfg: dict, nrhs) -> dict:
+    p, b = cfg["problem"], cfg["build"]
+    return {"n": p.n, "m": p.m, "kappa": p.kappa, "T": p.T, "sigma": p.sigma, "sensor_seed": p.sensor_seed,
+            "leaf": b.leaf, "adm": b.adm, "eta": b.eta, "tol": b.tol, "kmax": b.kmax, "q0": b.q0, "b_inc": b.b_inc,
+            "q_max": b.q_max, "adaptive": bool(b.adaptive), "seed": b.seed, "nrhs": list(nrhs), "rhs_seed": 5}
+
+
+def oracle_worker(spec: dict) -> dict:
+    """The oracle as it stands, in this process: build the configuration's H^2 (or load its factors
+    from spec["load"]), then time its matvec for every nrhs (reps times).  Returns times, bytes and
+    counts; spec["dump"] saves the factors for a later worker."""
     import oracle as O
 
-    p = CFG["problem"]
-    b = CFG["build"]
-    n = n_sample
-    m = int(round(p.m * (n * n) / p.N))
-    mask = W.sensor_mask(n * n, m, p.sensor_seed)
-    op = O.HeatHessian(n, p.kappa, p.T, p.sigma, mask)
-    t0 = time.perf_counter()
-    h, res = O.build(op, W.grid_coords(n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
-                     b.adaptive, b.seed)
-    t_build = time.perf_counter() - t0
+    n = spec["n"]
+    N = n * n
+    out = {"threads_env": os.environ.get("OMP_NUM_THREADS"), "cores": os.cpu_count()}
+    if spec.get("load"):
+        z = np.load(spec["load"])
+        tree = O.ClusterTree(W.grid_coords(n), spec["leaf"])
+        h = O.from_factor_arrays(tree, O.Partition(tree, spec["adm"], spec["eta"]), z["ranks"], z["U"], z["E"], z["S"],
+                                 z["D"])
+        out["build_s"] = None
+    else:
+        mask = W.sensor_mask(N, spec["m"], spec["sensor_seed"])
+        op = O.HeatHessian(n, spec["kappa"], spec["T"], spec["sigma"], mask)
+        t0 = time.perf_counter()
+        h, res = O.build(op, W.grid_coords(n), spec["leaf"], spec["adm"], spec["eta"], spec["tol"], spec["kmax"],
+                         spec["q0"], spec["b_inc"], spec["q_max"], spec["adaptive"], spec["seed"])
+        out["build_s"] = time.perf_counter() - t0
+        out["samples"] = int(res.samples - res.norm_its)
+        if spec.get("dump"):
+            r, U, E, S, D = O.factor_arrays(h)
+            np.savez(spec["dump"], ranks=r, U=U, E=E, S=S, D=D)
     ent = O.storage_entries(h)
     st = {"entries_D": ent["D"], "entries_S": ent["S"], "entries_U": ent["U"], "entries_E": ent["E"]}
-    tot_bytes, tot_t = 0.0, 0.0
-    for nrhs in nrhs_list:
-        X = W.rhs(n * n, nrhs, 5)
-        for _ in range(reps):
+    out["matvec_s"], out["bytes"] = {}, {}
+    for nr in spec["nrhs"]:
+        X = W.rhs(N, nr, spec["rhs_seed"])
+        ts = []
+        for _ in range(spec.get("reps", 1)):
             t0 = time.perf_counter()
             O.matvec(h, X)
-            tot_t += time.perf_counter() - t0
-            tot_bytes += matvec_bytes(st, n * n, nrhs)
-    return {"value": tot_bytes / tot_t / 1e9, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle build of the same heat-Hessian family at n={n} (N={n * n}, {m} sensors) "
-                      f"in {t_build:.1f} s, then oracle matvec with nrhs {list(nrhs_list)} x{reps}",
-            "build_s": t_build, "samples": int(res.samples - res.norm_its)}
+            ts.append(time.perf_counter() - t0)
+        out["matvec_s"][str(nr)] = ts
+        out["bytes"][str(nr)] = matvec_bytes(st, N, nr)
+    return out
+
+
+def run_oracle_worker(spec: dict, threads: int | None = None, timeout: float = 1800.0) -> dict:
+    """oracle_worker in a child process (so that the BLAS thread count can be fixed at start-up)."""
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", json.dumps(spec)], env=env,
+                       capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle worker failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def gbps(res: dict) -> float:
+    by = sum(res["bytes"][k] * len(v) for k, v in res["matvec_s"].items())
+    return by / sum(sum(v) for v in res["matvec_s"].values()) / 1e9
+
+
+def oracle_side_measurements(main_res: dict | None = None, dump: str | None = None) -> dict:
+    """The oracle beyond the headline sample: its matvec at one thread on the factors it built
+    (loaded from `dump`), and the 32 x 32 configuration (weak partition, 64 fixed probes,
+    nrhs 16) built and applied at all cores and at one thread."""
+    out = {}
+    if dump:
+        one = run_oracle_worker(dict(_spec(CFG, CFG["nrhs"]), load=dump), threads=1)
+        out["headline_matvec_1thread_GBps"] = gbps(one)
+        out["headline_matvec_1thread_s"] = {k: float(np.mean(v)) for k, v in one["matvec_s"].items()}
+    for th, key in ((None, "nproc"), (1, "1thread")):
+        r = run_oracle_worker(dict(_spec(W.SMALL_N32, W.SMALL_N32["nrhs"]), reps=3), threads=th)
+        out[f"small_n32_{key}"] = {"build_s": r["build_s"], "matvec_GBps": gbps(r), "samples": r["samples"],
+                                   "threads": th or os.cpu_count()}
+    return out
+
+
+def cpu_baseline_full() -> dict:
+    """The oracle as it stands on the headline workload itself: the FP64 construction of the
+    256 x 256 Hessian (once; its time is reported as build_s), then its matvec with nrhs 1, 32,
+    256 (the sample the value is measured on), at all host cores; plus one-thread and 32 x 32
+    measurements (oracle_side_measurements)."""
+    dump = os.path.join(tempfile.gettempdir(), f"h2bench_oracle_{os.getpid()}.npz")
+    try:
+        res = run_oracle_worker(dict(_spec(CFG, CFG["nrhs"]), dump=dump))
+        side = oracle_side_measurements(res, dump)
+    finally:
+        if os.path.exists(dump):
+            os.remove(dump)
+    mv = {k: float(np.mean(v)) for k, v in res["matvec_s"].items()}
+    return {"value": gbps(res), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle matvec with nrhs {list(CFG['nrhs'])} of the oracle-built H^2 of the headline workload "
+                      f"({CFG['name']}, N={CFG['problem'].N}); the oracle construction itself took "
+                      f"{res['build_s']:.1f} s at {os.cpu_count()} cores",
+            "same_config": True, "build_s": res["build_s"], "samples": res["samples"], "matvec_s": mv, **side}
 
 
 def run_reference(args) -> None:
+    """The oracle arm: the headline workload (same configuration, metric and unit as the GPU arm):
+    the oracle builds the 256 x 256 H^2 once (set-up, timed and reported), then every step
+    applies its matvec to nrhs 1, 32 and 256 right-hand sides; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
 
-    p = CFG["problem"]
-    b = CFG["build"]
-    n = 128
-    m = int(round(p.m * (n * n) / p.N))
-    mask = W.sensor_mask(n * n, m, p.sensor_seed)
-    op = O.HeatHessian(n, p.kappa, p.T, p.sigma, mask)
-    h, res = O.build(op, W.grid_coords(n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
+    p, b = CFG["problem"], CFG["build"]
+    N = p.N
+    mask = W.sensor_mask(N, p.m, p.sensor_seed)
+    op = O.HeatHessian(p.n, p.kappa, p.T, p.sigma, mask)
+    t0 = time.perf_counter()
+    h, res = O.build(op, W.grid_coords(p.n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
                      b.adaptive, b.seed)
+    build_s = time.perf_counter() - t0
     ent = O.storage_entries(h)
     st = {"entries_D": ent["D"], "entries_S": ent["S"], "entries_U": ent["U"], "entries_E": ent["E"]}
-    Xs = {nr: W.rhs(n * n, nr, 5) for nr in CFG["nrhs"]}
+    Xs = {nr: W.rhs(N, nr, CFG["rhs_seed"] + nr) for nr in CFG["nrhs"]}
 
     def step():
         by, tt = 0.0, 0.0
@@ -577,7 +672,7 @@ def run_reference(args) -> None:
             t0 = time.perf_counter()
             O.matvec(h, X)
             tt += time.perf_counter() - t0
-            by += matvec_bytes(st, n * n, nr)
+            by += matvec_bytes(st, N, nr)
         return by, tt
 
     for _ in range(args.warmup):
@@ -590,16 +685,36 @@ def run_reference(args) -> None:
         tt += t_
     wall = time.perf_counter() - t0
     val = tb / tt / 1e9
-    sample = (f"oracle matvec (nrhs {list(CFG['nrhs'])}) of the oracle-built H^2 of the same heat-Hessian "
-              f"family at n={n} (N={n * n}); the n=256 build does not fit a bounded CPU sample")
+    dump = os.path.join(tempfile.gettempdir(), f"h2bench_ref_{os.getpid()}.npz")
+    side = {}
+    try:
+        r, U, E, S, D = O.factor_arrays(h)
+        np.savez(dump, ranks=r, U=U, E=E, S=S, D=D)
+        side = oracle_side_measurements(None, dump)
+    except Exception as e:   # the side measurements are context; the arm's value stands without them
+        side = {"side_measurements_failed": str(e)[-300:]}
+    finally:
+        if os.path.exists(dump):
+            os.remove(dump)
+    sample = (f"oracle matvec (nrhs {list(CFG['nrhs'])}) of the oracle-built H^2 of the headline workload "
+              f"({CFG['name']}, N={N}) per step; the oracle construction (set-up) took {build_s:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CFG["name"], "N": p.N, "nrhs": list(CFG["nrhs"]), "tol": b.tol},
+            "config": config_of(CFG),
             "cpu_baseline": {"value": val, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "build_s": build_s, "samples": int(res.samples - res.norm_its),
+                             **side},
             "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def config_of(cfg: dict) -> dict:
+    p, b = cfg["problem"], cfg["build"]
+    return {"workload": cfg["name"], "N": p.N, "grid": f"{p.n}x{p.n}", "sensors": p.m, "kappa": p.kappa,
+            "leaf": b.leaf, "adm": "strong", "eta": b.eta, "kmax": b.kmax, "tol": b.tol,
+            "nrhs": list(cfg["nrhs"]), "mode": "FP64",
+            "l2": "H2 factors larger than L2 (no flush needed)", "parallelism": "replicas"}
 
 
 def main():
@@ -618,7 +733,11 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
     ap.add_argument("--precision-n", type=int, default=512, help="grid size of the precision section")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_worker is not None:
+        print(json.dumps(oracle_worker(json.loads(args.oracle_worker))), flush=True)
+        return
     global CFG
     if args.n is not None:
         CFG = scaled(CFG, args.n)
@@ -640,7 +759,7 @@ def main():
     # CPU baseline before any GPU work of this process (spawned pool not needed: single process)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample()
+        cpu = cpu_baseline_full()
 
     import paper_2003_10173_gb300 as h2
     from paper_2003_10173_gb300 import build_lib
@@ -660,6 +779,8 @@ def main():
           for nr in nrhs_list}
     Yd = {nr: torch.empty_like(Xd[nr]) for nr in nrhs_list}
 
+    nr_roof = max(nrhs_list)
+
     def step(profile=False):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -670,9 +791,12 @@ def main():
         for nr in nrhs_list:
             a = torch.cuda.Event(enable_timing=True)
             c = torch.cuda.Event(enable_timing=True)
+            # per-stage events (on this stream) around the widest matvec: the roofline's kernel
+            G.profile(nr == nr_roof)
             a.record(stream)
             G.matvec(Xd[nr], Yd[nr], nr, h2.H2_FP64, stream=stream)
             c.record(stream)
+            G.profile(False)
             mv[nr] = (a, c)
         return G, (ev0, ev1), mv
 
@@ -696,7 +820,7 @@ def main():
     t_end.record(stream)
     torch.cuda.synchronize()
     launches = h2.launch_count() - launches0
-    gemm_ms, gemm_flops, gemm_n = h2.gemm_profile_read()
+    gemm_ms, gemm_flops, gemm_n, gemm_bytes = h2.gemm_profile_read()
     h2.gemm_profile(False)
     clk = clocks.stop()
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist)
@@ -710,32 +834,56 @@ def main():
     value = aggregate_throughput(tot_bytes, tot_mv_s, dist) / 1e9
     hbm, hbm_src, fp64 = peaks()
 
-    # roofline of the dominant matvec kernel (leaf expansion + near field) at nrhs = 1, FP64
+    fp64_meas = fp64_peak_measured(torch, stream)
+    # roofline of the metric's dominant kernel: the FP64 gather kernel of the leaf expansion and
+    # near field (mv_leaf_near_kernel) in the nrhs = 256 matvec, timed with per-stage CUDA events on
+    # the matvec's stream inside the timed steps; algorithmic flops of that stage: every stored
+    # off-diagonal near block applied twice (D and D^T), every diagonal block once, plus U_t yh_t
+    _, sizes = tree.boxes(tree.L)
+    stage_ms = {}
+    for G, _, _ in results:
+        for k, (ms, nl) in G.profile_read().items():
+            if nl:
+                stage_ms.setdefault(k, []).append(ms)
+    ln_ms = float(np.mean(stage_ms["leaf_near"]))
+    ln_flops = near_flops(st, sizes, nr_roof) + 2.0 * nr_roof * st["entries_U"]
+    ln_tf = ln_flops / (ln_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": ln_tf, "peak": fp64_meas, "unit": "TFLOP/s",
+                "frac": ln_tf / fp64_meas, "traffic": MATVEC_TRAFFIC_PER_LAUNCH,
+                "kernel": f"mv_leaf_near_kernel (FP64 gather: near field + leaf expansion, nrhs={nr_roof})",
+                "peak_source": "measured: cuBLAS DGEMM 4096^3 (torch.matmul float64) on this GPU, best of 5",
+                "flops_per_launch": ln_flops, "ms_per_launch": ln_ms,
+                "stage_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
+                "fp64_peak_derived_TFLOPs": fp64,
+                "traffic_note": "DRAM read+write bytes of one launch at this size (ncu, profiles/); "
+                                "algorithmic bytes per launch: %.3e" % (st["entries_D"] * 8 + 2 * N * nr_roof * 8)}
+    # the construction's FP64 batched GEMM (operator DSTs, piece subtraction, stacked-QR inputs),
+    # timed per launch with events on the build stream over the timed steps
+    gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+    roofline_build_gemm = {"bound": "alu", "achieved": gemm_tf, "peak": fp64_meas, "unit": "TFLOP/s",
+                           "frac": (gemm_tf / fp64_meas) if gemm_tf else None, "traffic": None,
+                           "kernel": "gemm_tiles_kernel (FP64 batched GEMM of the construction)",
+                           "peak_source": "measured: cuBLAS DGEMM (as roofline)",
+                           "launches": gemm_n, "ms": gemm_ms,
+                           "flops_per_launch": gemm_flops / max(gemm_n, 1), "ms_per_launch": gemm_ms / max(gemm_n, 1),
+                           "algorithmic_bytes_per_launch": gemm_bytes / max(gemm_n, 1),
+                           "traffic_note": "per-launch DRAM bytes vary with the problem list; sampled launches "
+                                           "in profiles/gemm_tiles_n128_n256.md"}
+    # FP64 near field at nrhs = 1 (the atomic scatter kernel), outside the timed region
     Gp = results[-1][0]
     Gp.profile(True)
     for _ in range(5):
         Gp.matvec(Xd[1], Yd[1], 1, h2.H2_FP64, stream=stream)
     prof = Gp.profile_read()
     Gp.profile(False)
-    _, sizes = tree.boxes(tree.L)
     nr_ms, nr_n = prof["near"]
     nr_s = nr_ms / nr_n / 1e3
     achieved = near_flops(st, sizes, 1) / nr_s / 1e12
-    roofline_matvec = {"bound": "alu", "achieved": achieved, "peak": fp64, "unit": "TFLOP/s",
-                       "frac": achieved / fp64, "traffic": None,
-                       "kernel": "mv_scatter_kernel<double,...,1,true> (near field, nrhs=1)",
-                       "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                       "hbm_GBps": st["entries_D"] * 8 / nr_s / 1e9}
-    # dominant kernel of a step (about two thirds of the device time): the construction's FP64
-    # batched GEMM, timed per launch with events on the build stream over the timed steps
-    gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
-    roofline = {"bound": "alu", "achieved": gemm_tf, "peak": fp64, "unit": "TFLOP/s",
-                "frac": (gemm_tf / fp64) if gemm_tf else None, "traffic": GEMM_TRAFFIC_PER_LAUNCH,
-                "kernel": "gemm_tiles_kernel (FP64 batched GEMM: operator DSTs, piece subtraction, Gram)",
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                "launches": gemm_n, "ms": gemm_ms,
-                "flops_per_launch": gemm_flops / max(gemm_n, 1), "ms_per_launch": gemm_ms / max(gemm_n, 1)}
-    near_bytes = st["entries_D"] * 8
+    roofline_matvec_nrhs1 = {"bound": "alu", "achieved": achieved, "peak": fp64_meas, "unit": "TFLOP/s",
+                             "frac": achieved / fp64_meas, "traffic": None,
+                             "kernel": "mv_scatter_kernel<double,...,1,true> (near field, nrhs=1)",
+                             "peak_source": "measured: cuBLAS DGEMM (as roofline)",
+                             "hbm_GBps": st["entries_D"] * 8 / nr_s / 1e9}
     hbm_view = {"nrhs1_matvec_GBps": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9,
                 "frac_of_hbm": by[1] / (np.mean(mv_ms[1]) / 1e3) / 1e9 / hbm, "hbm_peak_GBps": hbm,
                 "hbm_peak_source": hbm_src}
@@ -754,13 +902,15 @@ def main():
     if rank == 0 and not args.no_batching:
         batching = batching_section(h2, torch, stream)
 
-    # end to end through the public call with host buffers (pinned) and copies in the timed region
+    # end to end through the public C-ABI call with HOST buffers (h2_matvec_host: pinned host X and
+    # Y, host-to-device copy, matvec, device-to-host copy inside the call and the timed region)
     Gp2 = results[-1][0]
     Xh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
     Yh = {nr: torch.empty((nr, N), dtype=torch.float64, pin_memory=True) for nr in nrhs_list}
     for nr in nrhs_list:
         Xh[nr].copy_(Xd[nr].cpu())
-    Xe = {nr: torch.empty_like(Xd[nr]) for nr in nrhs_list}
+    for nr in nrhs_list:      # warm-up: staging buffers grown, graphs captured
+        Gp2.matvec_host(Xh[nr], Yh[nr], nr, h2.H2_FP64, stream=stream)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     reps = 3
@@ -768,16 +918,15 @@ def main():
     e0.record(stream)
     for _ in range(reps):
         for nr in nrhs_list:
-            Xe[nr].copy_(Xh[nr], non_blocking=True)
-            Gp2.matvec(Xe[nr], Yd[nr], nr, h2.H2_FP64, stream=stream)
-            Yh[nr].copy_(Yd[nr], non_blocking=True)
+            Gp2.matvec_host(Xh[nr], Yh[nr], nr, h2.H2_FP64, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e_bytes = reps * sum(by[nr] for nr in nrhs_list)
     e2e = {"value": aggregate_throughput(e2e_bytes, e2e_s, dist) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list),
-           "d2h_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list)}
+           "d2h_bytes_per_step": sum(N * nr * 8 for nr in nrhs_list),
+           "call": "h2_matvec_host (C ABI, pinned host buffers)"}
 
     # accuracy of the last build (2-norm, power iteration through the GPU matvec and operator)
     rel_err = None
@@ -805,10 +954,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CFG["name"], "N": N, "grid": f"{p.n}x{p.n}", "sensors": p.m, "kappa": p.kappa,
-                       "leaf": b.leaf, "adm": "strong", "eta": b.eta, "kmax": b.kmax, "tol": b.tol,
-                       "nrhs": nrhs_list, "mode": "FP64",
-                       "l2": "H2 factors larger than L2 (no flush needed)", "parallelism": "replicas"},
+            "config": config_of(CFG),
             "build_s": float(np.mean(build_ms)) / 1e3,
             "rel_err_2norm": rel_err,
             "samples": st["samples"], "norm_products": st["norm_products"], "max_rank": st["max_rank"],
@@ -817,7 +963,8 @@ def main():
             "matvec_GBps": {str(nr): by[nr] / (np.mean(mv_ms[nr]) / 1e3) / 1e9 for nr in nrhs_list},
             "stored_bytes_fp64": (st["entries_D"] + st["entries_S"] + st["entries_U"] + st["entries_E"]) * 8,
             "hbm_view": hbm_view,
-            "roofline": roofline, "roofline_matvec": roofline_matvec,
+            "roofline": roofline, "roofline_build_gemm": roofline_build_gemm,
+            "roofline_matvec_nrhs1": roofline_matvec_nrhs1,
             "stage_ms_nrhs1": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
             "build_phase_s": {k: st[k] for k in ("t_norm", "t_op", "t_peel", "t_assemble")},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -835,7 +982,7 @@ def main():
         if inversion is not None:
             line["inversion"] = inversion
         if cpu is not None:
-            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     for G, _, _ in results:
         G.close()

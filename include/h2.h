@@ -259,7 +259,19 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
               int mode, h2_stream_t stream);
 
 /*
- * Same product as h2_matvec, for callers that cannot allocate device memory: for
+ * Y = A X as h2_matvec, with X and Y in host memory (X: n x nrhs, leading dimension ldx >= n;
+ * Y: n x nrhs, ldy >= n; element types as h2_matvec for `mode`).  The library copies X into a
+ * device staging buffer owned by the handle, applies h2_matvec to it on `stream` and copies Y
+ * back; the call returns when Y is complete on the host (it synchronises the stream).  Page-
+ * locked host buffers (cudaHostAlloc, cudaHostRegister) give asynchronous copies at full bus
+ * speed; pageable buffers work too.  The staging buffers grow to the largest call and are
+ * released with the handle.  Errors: INVALID_ARG, CUDA, OOM.
+ */
+int h2_matvec_host(h2_handle_t h, const void* X_host, int64_t ldx, void* Y_host, int64_t ldy, int64_t nrhs, int mode,
+                   h2_stream_t stream);
+
+/*
+ * The product of h2_matvec, for callers that cannot allocate device memory: for
  * example code whose device memory is entirely managed by another allocator (a
  * framework's caching pool that has already reserved the free memory), or
  * latency-critical loops that must not pay the implicit device-wide
@@ -268,12 +280,23 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
  * library's device image, which every GPU that loads the library holds until the
  * process exits; calls needing more (coefficient rows of the handle x nrhs x 8 bytes
  * in H2_FP64, x 4 bytes otherwise) fail with H2_ERR_INVALID_ARG and a message giving
- * the size.  The first call on a device looks up the array's device address with
- * that device current; make that first call before any stream capture.  All calls
- * share the array and it keeps the contents of the last call (no element needs to
- * start at zero: every element a call reads it has written before), so calls whose
- * executions overlap on the GPU, on any handle or stream, race on it: serialise them.
- * Arguments and errors as h2_matvec.  The paper has no counterpart of this entry point.
+ * the size.  The array's device address is looked up, with the device current, when
+ * a handle is created on that device (h2_build, h2_import and every other call that
+ * returns a handle do it), which also loads the part of the library's device image
+ * that holds the array while allocating is still allowed; a call with a handle of a
+ * device whose address was never looked up does the lookup itself, so it should come
+ * before any stream capture.  All calls share the array and it keeps the contents of
+ * the last call (no element needs to start at zero: every element a call reads it
+ * has written before), so calls whose executions overlap on the GPU, on any handle
+ * or stream, race on it: serialise them.
+ * Arithmetic: always the non-tensor-core kernels.  H2_FP64 and H2_FP32 run the
+ * kernels h2_matvec runs in those modes (at nrhs <= 4 they add with atomics, so the
+ * last bits can differ from call to call); H2_BF16 (BF16 storage and inputs, FP32
+ * arithmetic) equals h2_matvec up to FP32 summation order, which differs from
+ * h2_matvec's tensor-core path at nrhs >= 64.  H2_TF32 and H2_TF32X3 need the
+ * tensor-core path's operand workspace and are rejected with H2_ERR_INVALID_ARG.
+ * Other arguments and errors as h2_matvec.  The paper has no counterpart of this
+ * entry point.
  */
 int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                       int mode, h2_stream_t stream);
@@ -301,9 +324,11 @@ int h2_profile_read(h2_handle_t h, double* ms_out, int64_t* launches_out);
 /* Process-wide timing of the batched FP64 GEMM kernel used by the construction and
  * by the shipped operators: when enabled (1), CUDA events are recorded around every
  * GEMM launch on its stream.  h2_gemm_profile_read synchronises the device, returns the
- * accumulated milliseconds, algorithmic flops (sum of 2 m n k) and launches, and resets. */
+ * accumulated milliseconds, algorithmic flops (sum of 2 m n k), algorithmic bytes (sum of
+ * 8 (m k + k n + m n), plus 8 m n for C read when beta != 0) and launches, and resets.
+ * Any output pointer may be NULL. */
 int h2_gemm_profile(int enable);
-int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out);
+int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out, double* bytes_out);
 
 /* Synchronise the device and report whether a kernel of handle h recorded a failed bounded
  * wait (H2_ERR_DEVICE_CHECK) since h was created; H2_OK otherwise. */
@@ -459,6 +484,13 @@ int h2_rankmodel_load(const char* path, h2_rankmodel_t* out);
  * may be NULL) receives the raw predictions.  Synchronous. */
 int h2_rankmodel_q_levels(h2_rankmodel_t m, h2_tree_t tree, double kappa_T, double density, double tol,
                           int pad, int q_max, int32_t* q_host, float* y_host);
+
+/* Training targets of the model from a finished construction h: for every sampled level l
+ * (levels with an identity range are skipped), levels_host[i] = l and targets_host[i] =
+ * log2(1 + need_l), need_l the probe count whose range basis passed the adaptive test
+ * (h2_stats.range_need).  *count receives the number of entries (at most L); either array may
+ * be NULL to query the count.  Host arrays.  Errors: INVALID_ARG. */
+int h2_rankmodel_targets(h2_handle_t h, int32_t* levels_host, float* targets_host, int* count);
 
 /* ---- synthetic Hessians shipped with the library ------------------------- */
 

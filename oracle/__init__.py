@@ -9,7 +9,8 @@ Section 3.2 (matvec, recompression, norms), Section 3.3 (construction from
 Hessian-vector products), with numpy library primitives (QR, SVD, matmul)
 as steps.
 """
-from .h2 import H2Matrix, assemble, expand_dense, frobenius_norm, matvec, power_norm, storage_entries
+from .h2 import (H2Matrix, assemble, expand_dense, factor_arrays, frobenius_norm, from_factor_arrays, matvec,
+                 power_norm, storage_entries)
 from .heat import DenseOperator, HeatHessian, LowRankOperator
 from .peel import PeelResult, TreeOperator, apply_pieces, global_lowrank, norm2_estimate, peel, psd_cholesky
 from .tree import ADM_STRONG, ADM_WEAK, ClusterTree, Partition

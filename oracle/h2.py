@@ -260,6 +260,70 @@ def storage_entries(h: H2Matrix) -> dict:
     }
 
 
+def factor_arrays(h: H2Matrix):
+    """The factors in the flat layout of the library's import/export calls: ranks of every box
+    (levels 0..L, 2^l boxes each); leaf bases |t| x k_t; transfer matrices k_c x k_parent of
+    every box c of levels 2..L (level-1 boxes have none: the root's rank is 0); couplings of
+    the lower far blocks per level in partition order; near blocks with t >= s in partition
+    order; all column-major FP64."""
+    tree, part = h.tree, h.part
+    L = tree.L
+    ranks = np.concatenate([np.asarray(h.k[l], dtype=np.int32) for l in range(L + 1)])
+    U = [h.U[t].flatten(order="F") for t in range(1 << L)]
+    E = [h.E[(l, c)].flatten(order="F") for l in range(2, L + 1) for c in range(1 << l)]
+    S = [h.S[(l, int(t), int(s))].flatten(order="F") for l in range(1, L + 1) for t, s in part.far[l] if t > s]
+    D = [h.D[(int(t), int(s))].flatten(order="F") for t, s in part.near if t >= s]
+    cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0)
+    return ranks, cat(U), cat(E), cat(S), cat(D)
+
+
+def from_factor_arrays(tree: ClusterTree, part: Partition, ranks, U, E, S, D) -> H2Matrix:
+    """An H2Matrix holding given factors in the layout of factor_arrays."""
+    L = tree.L
+    h = H2Matrix(tree, part)
+    o = 0
+    for l in range(L + 1):
+        h.k[l] = np.asarray(ranks[o:o + (1 << l)], dtype=np.int64)
+        o += 1 << l
+    o = 0
+    for t in range(1 << L):
+        r = tree.rows(L, t)
+        m, k = r.stop - r.start, int(h.k[L][t])
+        h.U[t] = np.asarray(U[o:o + m * k]).reshape((m, k), order="F")
+        h.Uexp[L][t] = h.U[t]
+        o += m * k
+    o = 0
+    for l in range(2, L + 1):
+        for c in range(1 << l):
+            kc, kp = int(h.k[l][c]), int(h.k[l - 1][c >> 1])
+            h.E[(l, c)] = np.asarray(E[o:o + kc * kp]).reshape((kc, kp), order="F")
+            o += kc * kp
+    for l in range(1, L + 1):
+        for c in range(1 << l):
+            if (l, c) not in h.E:
+                h.E[(l, c)] = np.zeros((int(h.k[l][c]), int(h.k[l - 1][c >> 1])))
+    for l in range(L - 1, 0, -1):
+        for t in range(1 << l):
+            h.Uexp[l][t] = np.vstack([h.Uexp[l + 1][2 * t] @ h.E[(l + 1, 2 * t)],
+                                      h.Uexp[l + 1][2 * t + 1] @ h.E[(l + 1, 2 * t + 1)]])
+    h.Uexp[0][0] = np.zeros((tree.N, 0))
+    o = 0
+    for l in range(1, L + 1):
+        for t, s in part.far[l]:
+            if t > s:
+                kt, ks = int(h.k[l][t]), int(h.k[l][s])
+                h.S[(l, int(t), int(s))] = np.asarray(S[o:o + kt * ks]).reshape((kt, ks), order="F")
+                o += kt * ks
+    o = 0
+    for t, s in part.near:
+        if t >= s:
+            rt, rs = tree.rows(L, t), tree.rows(L, s)
+            mt, ms = rt.stop - rt.start, rs.stop - rs.start
+            h.D[(int(t), int(s))] = np.asarray(D[o:o + mt * ms]).reshape((mt, ms), order="F")
+            o += mt * ms
+    return h
+
+
 def power_norm(apply, N: int, v0: np.ndarray, maxit: int = 200, rtol: float = 1e-2):
     """2-norm of a symmetric operator by power iteration, stopping once two significant
     digits are stable (Section 3.2)."""

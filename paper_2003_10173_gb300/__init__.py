@@ -132,12 +132,14 @@ _SIGS = {
     "h2_rankmodel_save": (_I, [_P, ctypes.c_char_p]),
     "h2_rankmodel_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "h2_matvec_noalloc": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
+    "h2_matvec_host": (_I, [_P, _P, _I64, _P, _I64, _I64, _I, _P]),
+    "h2_rankmodel_targets": (_I, [_P, _P, _P, _P]),
     "h2_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "h2_profile": (_I, [_P, _I]),
     "h2_device_status": (_I, [_P]),
     "h2_profile_read": (_I, [_P, _P, _P]),
     "h2_gemm_profile": (_I, [_I]),
-    "h2_gemm_profile_read": (_I, [_P, _P, _P]),
+    "h2_gemm_profile_read": (_I, [_P, _P, _P, _P]),
     "h2_free": (None, [_P]),
     "h2_invert_opts_default": (_I, [ctypes.POINTER(InvertOpts)]),
     "h2_invert": (_I, [_P, ctypes.POINTER(InvertOpts), ctypes.POINTER(BuildOpts), ctypes.POINTER(_P),
@@ -436,6 +438,13 @@ class H2:
         n = self.stats()["n"]
         _check(lib().h2_matvec(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode, _stream_ptr(stream)))
 
+    def matvec_host(self, X, Y, nrhs: int, mode: int = H2_FP64, stream=None, ldx: int | None = None,
+                    ldy: int | None = None):
+        """h2_matvec_host: X and Y in host memory (CPU tensors or arrays; pinned for full-speed copies);
+        returns when Y is complete."""
+        n = self.stats()["n"]
+        _check(lib().h2_matvec_host(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode, _stream_ptr(stream)))
+
     def matvec_noalloc(self, X, Y, nrhs: int, mode: int = H2_FP64, stream=None, ldx: int | None = None,
                        ldy: int | None = None):
         """h2_matvec with the library's fixed 32 MiB device scratch instead of an allocated workspace."""
@@ -496,9 +505,10 @@ def gemm_profile(enable: bool = True):
 
 
 def gemm_profile_read():
-    ms, fl, n = _D(), _D(), _I64()
-    _check(lib().h2_gemm_profile_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
-    return ms.value, fl.value, n.value
+    """(milliseconds, algorithmic flops, launches, algorithmic bytes) of the GEMM launches since the last read."""
+    ms, fl, n, by = _D(), _D(), _I64(), _D()
+    _check(lib().h2_gemm_profile_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n), ctypes.byref(by)))
+    return ms.value, fl.value, n.value, by.value
 
 
 def build_batched(ops, trees, tol: float, opts: BuildOpts | None = None):
@@ -637,15 +647,13 @@ class RankModel:
             pass
 
 
-def rank_targets(stats: dict):
-    """(levels, log2(1 + need)) of the sampled levels of a build's statistics (identity levels skipped)."""
-    lv, tg = [], []
-    for l in range(1, stats["levels"] + 1):
-        if stats["range_passed"][l] < 0:
-            continue
-        lv.append(l)
-        tg.append(float(np.log2(1.0 + stats["range_need"][l])))
-    return lv, tg
+def rank_targets(G: "H2"):
+    """(levels, log2(1 + need)) of the sampled levels of a construction (h2_rankmodel_targets)."""
+    lv = (ctypes.c_int32 * H2_MAX_LEVELS)()
+    tg = (ctypes.c_float * H2_MAX_LEVELS)()
+    n = ctypes.c_int()
+    _check(lib().h2_rankmodel_targets(G._h, lv, tg, ctypes.byref(n)))
+    return [int(lv[i]) for i in range(n.value)], [float(tg[i]) for i in range(n.value)]
 
 
 def launch_count() -> int:

@@ -657,10 +657,12 @@ void Builder::assemble(h2_handle_s* h) {
         std::map<Key, std::vector<int>> own;   // (level, t, lp) -> far column boxes of t
         int64_t rtot = 0;
         auto c2 = [&](int lp) { return (int64_t)qw_[lp] * qw_[lp]; };
+        const int wide_c = stacked_r_max_columns();
+        auto wide = [&](int lp) { return qw_[lp] > wide_c; };
         for (int l = 1; l <= L; ++l)
             for (auto [r, sb] : T_.far[l])
                 for (const int lp : {pair_level(l, r, sb), 0}) {
-                    if (!qw_[lp]) continue;
+                    if (!qw_[lp] || wide(lp)) continue;
                     Key kb{l, sb, lp};
                     if (!rs.count(kb)) {
                         rs[kb] = RInfo{rtot, std::min(qw_[lp], bsize(l, sb))};
@@ -671,7 +673,7 @@ void Builder::assemble(h2_handle_s* h) {
         for (int l = 1; l <= L; ++l)
             for (int t = 0; t < (1 << l); ++t)
                 for (int lp = 0; lp <= l; ++lp) {
-                    if (!qw_[lp]) continue;
+                    if (!qw_[lp] || wide(lp)) continue;
                     auto par = rt.find(Key{l - 1, t >> 1, lp});
                     auto ow = own.find(Key{l, t, lp});
                     if (ow == own.end()) {
@@ -717,6 +719,94 @@ void Builder::assemble(h2_handle_s* h) {
             stacked_r(jobs, segs, stk_, s_);
         }
 
+        // Groups wider than stacked_r takes (the global piece of a hybrid construction with a
+        // budget above its limit, or levels with that many probes): Gram matrices M(l, t, lp) =
+        // C_lp(t)^T C_lp(t) by a downsweep of per-box sums instead of R factors.  Such a group
+        // enters a box's SVD through a semidefinite Cholesky factor of P_lp[t] M P_lp[t]^T (its
+        // block of W W^T), which resolves its small singular values to sqrt(eps) sigma_max only.
+        std::map<Key, int64_t> gcol, gm;
+        std::map<Key, std::vector<int64_t>> gown;
+        std::map<Key, bool> gm_own;
+        int64_t gtot = 0;
+        for (int l = 1; l <= L; ++l)
+            for (auto [r, sb] : T_.far[l])
+                for (const int lp : {pair_level(l, r, sb), 0}) {
+                    if (!qw_[lp] || !wide(lp)) continue;
+                    Key kb{l, sb, lp};
+                    if (!gcol.count(kb)) { gcol[kb] = gtot; gtot += c2(lp); }
+                    gown[Key{l, r, lp}].push_back(gcol[kb]);
+                }
+        for (int l = 1; l <= L; ++l)
+            for (int t = 0; t < (1 << l); ++t)
+                for (int lp = 0; lp <= l; ++lp) {
+                    if (!qw_[lp] || !wide(lp)) continue;
+                    auto par = gm.find(Key{l - 1, t >> 1, lp});
+                    if (!gown.count(Key{l, t, lp})) {
+                        if (par != gm.end()) gm[Key{l, t, lp}] = par->second;
+                        continue;
+                    }
+                    gm[Key{l, t, lp}] = gtot;
+                    gm_own[Key{l, t, lp}] = true;
+                    gtot += c2(lp);
+                }
+        DevBuf<double> Gw((size_t)std::max<int64_t>(gtot, 1));
+        if (!gcol.empty()) {
+            for (auto& [key, off] : gcol) {
+                auto [l, sb, lp] = key;
+                const int q = qw_[lp];
+                gb_.add(Pp(l, sb, lp), (int)N_, 1, Pp(l, sb, lp), (int)N_, 0, Gw.p + off, q, q, q, bsize(l, sb), 1.0, 0.0);
+            }
+            gb_.run(s_);
+            for (int l = 1; l <= L; ++l) {
+                std::vector<int64_t> oo, io;
+                std::vector<int> len, bg, en;
+                for (int t = 0; t < (1 << l); ++t)
+                    for (int lp = 0; lp <= l; ++lp) {
+                        if (!gm_own.count(Key{l, t, lp})) continue;
+                        oo.push_back(gm[Key{l, t, lp}]);
+                        len.push_back((int)c2(lp));
+                        bg.push_back((int)io.size());
+                        auto par = gm.find(Key{l - 1, t >> 1, lp});
+                        if (par != gm.end()) io.push_back(par->second);
+                        for (int64_t o : gown[Key{l, t, lp}]) io.push_back(o);
+                        en.push_back((int)io.size());
+                    }
+                if (oo.empty()) continue;
+                sum_lists((int)oo.size(), dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
+                          dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), Gw.p, Gw.p, 0, s_);
+                H2_CUDA(cudaStreamSynchronize(s_));
+            }
+        }
+        // block of W W^T of a wide group for the rows V (rows x q, leading dimension ldv):
+        // G = V M V^T into Gsm, then its Cholesky factor into the stack at out (leading dimension ldo)
+        DevBuf<double> Vm, Gsm;
+        struct WideItem { const double* V; int ldv; int rows; int lp; const double* M; double* out; int ldo; };
+        auto wide_blocks = [&](const std::vector<WideItem>& items) {
+            if (items.empty()) return;
+            int64_t vt = 0, gt2 = 0;
+            for (auto& it : items) { vt += (int64_t)it.rows * qw_[it.lp]; gt2 += (int64_t)it.rows * it.rows; }
+            Vm.reserve((size_t)vt);
+            Gsm.reserve((size_t)gt2);
+            int64_t vo = 0, go = 0;
+            std::vector<CholItem> ch;
+            for (auto& it : items) {
+                const int q = qw_[it.lp];
+                gb_.add(it.V, it.ldv, 0, it.M, q, 0, Vm.p + vo, it.rows, it.rows, q, q, 1.0, 0.0);
+                vo += (int64_t)it.rows * q;
+            }
+            gb_.run(s_);
+            vo = 0;
+            for (auto& it : items) {
+                const int q = qw_[it.lp];
+                gb_.add(Vm.p + vo, it.rows, 0, it.V, it.ldv, 1, Gsm.p + go, it.rows, it.rows, it.rows, q, 1.0, 0.0);
+                ch.push_back(CholItem{Gsm.p + go, it.out, it.rows, it.rows, it.ldo});
+                vo += (int64_t)it.rows * q;
+                go += (int64_t)it.rows * it.rows;
+            }
+            gb_.run(s_);
+            psd_chol_small(ch, stk_, s_);
+        };
+
         // leaves: SVD of W_t = [P_lp[t] R(L, t, lp)^T]_lp through W_t^T (stacked R P^T blocks)
         const int nleaf = 1 << L;
         std::vector<int64_t> toff(nleaf + 1, 0);
@@ -725,6 +815,7 @@ void Builder::assemble(h2_handle_s* h) {
             for (int lp = 0; lp <= L; ++lp) {
                 auto it = rt.find(Key{L, t, lp});
                 if (it != rt.end()) trows[t] += it->second.reff;
+                if (gm.count(Key{L, t, lp})) trows[t] += bsize(L, t);
             }
             toff[t + 1] = toff[t] + (int64_t)trows[t] * bsize(L, t);
         }
@@ -738,22 +829,31 @@ void Builder::assemble(h2_handle_s* h) {
         {
             std::vector<StackJob> jobs;
             std::vector<RowSeg> segs;
+            std::vector<WideItem> witems;
             d_k.reserve(nleaf);
             for (int t = 0; t < nleaf; ++t) {
                 int row = 0;
                 for (int lp = 0; lp <= L; ++lp) {
                     auto it = rt.find(Key{L, t, lp});
-                    if (it == rt.end() || !it->second.reff) continue;
-                    const int q = qw_[lp];
-                    gb_.add(Rb.p + it->second.off, q, 0, Pp(L, t, lp), (int)N_, 1, Tall.p + toff[t] + row, trows[t],
-                            it->second.reff, bsize(L, t), q, 1.0, 0.0);
-                    row += it->second.reff;
+                    if (it != rt.end() && it->second.reff) {
+                        const int q = qw_[lp];
+                        gb_.add(Rb.p + it->second.off, q, 0, Pp(L, t, lp), (int)N_, 1, Tall.p + toff[t] + row, trows[t],
+                                it->second.reff, bsize(L, t), q, 1.0, 0.0);
+                        row += it->second.reff;
+                    }
+                    auto wg = gm.find(Key{L, t, lp});
+                    if (wg != gm.end()) {
+                        witems.push_back(WideItem{Pp(L, t, lp), (int)N_, bsize(L, t), lp, Gw.p + wg->second,
+                                                  Tall.p + toff[t] + row, trows[t]});
+                        row += bsize(L, t);
+                    }
                 }
                 jobs.push_back(StackJob{(int)segs.size(), (int)segs.size() + (trows[t] ? 1 : 0), bsize(L, t),
                                         Utmp.p + utmp_off[t], bsize(L, t), d_k.p + t, nullptr});
                 if (trows[t]) segs.push_back(RowSeg{Tall.p + toff[t], trows[t], trows[t]});
             }
             gb_.run(s_);
+            wide_blocks(witems);
             stacked_svd_trunc(jobs, segs, stk_, tau_basis_, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nleaf);
             for (int t = 0; t < nleaf; ++t) K(L, t) = kk[t];
@@ -787,12 +887,14 @@ void Builder::assemble(h2_handle_s* h) {
                 for (int lp = 0; lp <= l; ++lp) {
                     auto it = rt.find(Key{l, p, lp});
                     if (it != rt.end()) tr[p] += it->second.reff;
+                    if (nn[p] && gm.count(Key{l, p, lp})) tr[p] += nn[p];
                 }
                 to[p + 1] = to[p] + (int64_t)tr[p] * nn[p];
             }
             DevBuf<double> Tb((size_t)std::max<int64_t>(to[nb], 1));
             std::vector<StackJob> jobs;
             std::vector<RowSeg> segs;
+            std::vector<WideItem> witems;
             d_k.reserve(nb);
             for (int p = 0; p < nb; ++p) {
                 const bool any = nn[p] && tr[p];
@@ -801,11 +903,18 @@ void Builder::assemble(h2_handle_s* h) {
                     int row = 0;
                     for (int lp = 0; lp <= l; ++lp) {
                         auto it = rt.find(Key{l, p, lp});
-                        if (it == rt.end() || !it->second.reff) continue;
-                        const int q = qw_[lp];
-                        gb_.add(Rb.p + it->second.off, q, 0, V + qoff[lp] * Kc, (int)Kc, 1, Tb.p + to[p] + row, tr[p],
-                                it->second.reff, nn[p], q, 1.0, 0.0);
-                        row += it->second.reff;
+                        if (it != rt.end() && it->second.reff) {
+                            const int q = qw_[lp];
+                            gb_.add(Rb.p + it->second.off, q, 0, V + qoff[lp] * Kc, (int)Kc, 1, Tb.p + to[p] + row,
+                                    tr[p], it->second.reff, nn[p], q, 1.0, 0.0);
+                            row += it->second.reff;
+                        }
+                        auto wg = gm.find(Key{l, p, lp});
+                        if (wg != gm.end()) {
+                            witems.push_back(WideItem{V + qoff[lp] * Kc, (int)Kc, nn[p], lp, Gw.p + wg->second,
+                                                      Tb.p + to[p] + row, tr[p]});
+                            row += nn[p];
+                        }
                     }
                 }
                 jobs.push_back(StackJob{(int)segs.size(), (int)segs.size() + (any ? 1 : 0), nn[p],
@@ -813,6 +922,7 @@ void Builder::assemble(h2_handle_s* h) {
                 if (any) segs.push_back(RowSeg{Tb.p + to[p], tr[p], tr[p]});
             }
             gb_.run(s_);
+            wide_blocks(witems);
             stacked_svd_trunc(jobs, segs, stk_, tau_basis_, o_.kmax, d_cap.p, s_);
             std::vector<int> kk = read_ints(d_k.p, nb);
             for (int p = 0; p < nb; ++p) K(l, p) = kk[p];

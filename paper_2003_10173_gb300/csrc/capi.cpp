@@ -412,6 +412,21 @@ int h2_rankmodel_q_levels(h2_rankmodel_t m, h2_tree_t tree, double kappa_T, doub
     });
 }
 
+int h2_rankmodel_targets(h2_handle_t h, int32_t* levels, float* targets, int* count) {
+    return guard([&] {
+        require(h && count, "h2_rankmodel_targets: NULL handle or count");
+        int n = 0;
+        for (int l = 1; l <= h->stats.levels; ++l) {
+            if (h->stats.range_passed[l] < 0) continue;   // identity range: nothing was learned here
+            if (levels) levels[n] = l;
+            if (targets) targets[n] = (float)std::log2(1.0 + (double)h->stats.range_need[l]);
+            ++n;
+        }
+        *count = n;
+        return H2_OK;
+    });
+}
+
 int h2_import(h2_tree_t tree, const int32_t* ranks, const double* U, const double* E, const double* S,
               const double* D, int keep_fp32, int keep_bf16, h2_handle_t* out) {
     return guard([&] {
@@ -559,6 +574,20 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
     });
 }
 
+int h2_matvec_host(h2_handle_t h, const void* X_host, int64_t ldx, void* Y_host, int64_t ldy, int64_t nrhs, int mode,
+                   h2_stream_t stream) {
+    return guard([&] {
+        require(h != nullptr, "h2_matvec_host: NULL handle");
+        require(nrhs >= 0, "h2_matvec_host: nrhs < 0");
+        if (nrhs == 0) return H2_OK;
+        require(X_host != nullptr && Y_host != nullptr, "h2_matvec_host: NULL X or Y");
+        require(ldx >= h->N && ldy >= h->N, "h2_matvec_host: leading dimension smaller than n");
+        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec_host: unknown mode");
+        h2::run_matvec_host(h, X_host, ldx, Y_host, ldy, nrhs, mode, (cudaStream_t)stream);
+        return H2_OK;
+    });
+}
+
 int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
                       h2_stream_t stream) {
     return guard([&] {
@@ -596,9 +625,9 @@ int h2_gemm_profile(int enable) {
     });
 }
 
-int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out) {
+int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out, double* bytes_out) {
     return guard([&] {
-        h2::gemm_profile_read(ms_out, flops_out, launches_out);
+        h2::gemm_profile_read(ms_out, flops_out, launches_out, bytes_out);
         return H2_OK;
     });
 }

@@ -170,7 +170,7 @@ class GemmBatch {
 };
 
 void gemm_profile_enable(int on);
-void gemm_profile_read(double* ms, double* flops, int64_t* launches);
+void gemm_profile_read(double* ms, double* flops, int64_t* launches, double* bytes);
 
 // ---- dense linear-algebra kernels (la.cu) ----------------------------------
 // Householder QR of panels in place with explicit orthonormal factor written to Q.
@@ -226,13 +226,16 @@ struct StackJob {
     int* k_out;       // stacked_svd_trunc: number of kept singular vectors
     double* sv_out;   // stacked_svd_trunc: all c singular values, descending (may be null)
 };
+struct CholItem;
 struct StackWork {
+    DevBuf<unsigned char> d_chol;
+    Stager st_chol;
     DevBuf<StackJob> d_jobs, d_jobs2;
     DevBuf<RowSeg> d_segs, d_segs2;
-    DevBuf<double> parts, gwork;
+    DevBuf<double> parts;
     Stager st_jobs, st_jobs2, st_segs, st_segs2;
 };
-// R factors (Householder) of every job's stacked matrix (c <= 256 columns; any row count:
+// R factors (Householder) of every job's stacked matrix (c <= 144 columns; any row count:
 // matrices above a few thousand rows are split over several CTAs).  The stacked matrices must
 // not overlap the outputs.  Host vectors; device pointers inside.
 void stacked_r(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, cudaStream_t s);
@@ -243,6 +246,19 @@ void stacked_r(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& seg
 void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, double thr,
                        int kmax, int* d_cap_flag, cudaStream_t s);
 int svd_max_order();
+// Widest matrix (columns) that stacked_r factors in shared memory; wider groups of the
+// recompression use Gram matrices instead.
+int stacked_r_max_columns();
+// Factors of small symmetric positive semidefinite m x m matrices (m <= 96) by Cholesky with
+// symmetric pivoting: for every item, out (m x m, leading dimension ldo) receives F^T with
+// F F^T = G (G: leading dimension ldg, lower triangle used); the factorisation stops once the
+// largest remaining pivot is at or below m 2^-52 max(diag G) (those rows of out are zero).
+struct CholItem {
+    const double* G;
+    double* out;
+    int m, ldg, ldo;
+};
+void psd_chol_small(const std::vector<CholItem>& items, StackWork& w, cudaStream_t s);
 
 // ---- small helper kernels (misc.cu) ------------------------------------------
 void fill_zero(double* p, size_t count, cudaStream_t s);
@@ -262,6 +278,11 @@ void scatter_rows(int64_t N, int ncols, const int32_t* d_perm, const double* src
                   double* dst, int64_t ldd, cudaStream_t s);
 // sum over blocks of |x|^2 and a flag for non-finite values: out[0] += ..., out[1] = 1 if nan
 void scan_finite(int64_t N, int ncols, const double* x, int64_t ld, int* d_flag, cudaStream_t s);
+// out[i] = sum_{j in list i} in[j] for count matrices of size len_i (in and out may be one buffer
+// when no output is also an input)
+void sum_lists(int count, const int64_t* d_out_off, const int* d_len, const int* d_begin,
+               const int* d_end, const int64_t* d_in_off, const double* in, double* out,
+               int accumulate, cudaStream_t s);
 // norms of vectors: out[j] = ||x[:, j]||^2
 void col_sqnorms(int64_t N, int ncols, const double* x, int64_t ld, double* out, cudaStream_t s);
 void scale_cols(int64_t N, int ncols, double* x, int64_t ld, const double* d_scale, cudaStream_t s);

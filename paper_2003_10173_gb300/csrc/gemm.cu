@@ -167,7 +167,7 @@ struct GemmProfile {
     int on = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used;
     std::vector<cudaEvent_t> pool;
-    double ms = 0.0, flops = 0.0;
+    double ms = 0.0, flops = 0.0, bytes = 0.0;
     int64_t launches = 0;
     cudaEvent_t take() {
         if (pool.empty()) {
@@ -186,7 +186,7 @@ GemmProfile g_prof;
 
 void gemm_profile_enable(int on) { g_prof.on = on; }
 
-void gemm_profile_read(double* ms, double* flops, int64_t* launches) {
+void gemm_profile_read(double* ms, double* flops, int64_t* launches, double* bytes) {
     H2_CUDA(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lock(g_prof.mu);
     for (auto& u : g_prof.used) {
@@ -200,8 +200,10 @@ void gemm_profile_read(double* ms, double* flops, int64_t* launches) {
     if (ms) *ms = g_prof.ms;
     if (flops) *flops = g_prof.flops;
     if (launches) *launches = g_prof.launches;
+    if (bytes) *bytes = g_prof.bytes;
     g_prof.ms = 0.0;
     g_prof.flops = 0.0;
+    g_prof.bytes = 0.0;
     g_prof.launches = 0;
 }
 
@@ -276,7 +278,10 @@ void GemmBatch::run(cudaStream_t s) {
             ea = g_prof.take();
             eb = g_prof.take();
             H2_CUDA(cudaEventRecord(ea, s));
-            for (const GemmProb& p : probs_) g_prof.flops += 2.0 * p.m * (double)p.n * (double)p.k;
+            for (const GemmProb& p : probs_) {
+                g_prof.flops += 2.0 * p.m * (double)p.n * (double)p.k;
+                g_prof.bytes += 8.0 * ((double)p.m * p.k + (double)p.k * p.n + (double)p.m * p.n * (p.beta != 0.0 ? 2 : 1));
+            }
             g_prof.launches += 1;
         }
         gemm_tiles_kernel<<<(unsigned)tiles.size(), NT, 0, s>>>(d_probs_.p, d_tiles_.p, d_work_.p);

@@ -175,6 +175,8 @@ struct h2_handle_s {
     h2::MatvecPlan plan;
     h2::TcPlan tc;
     h2::Workspace ws;
+    // device staging of X and Y for h2_matvec_host (grown to the largest call)
+    h2::DevBuf<unsigned char> host_x, host_y;
     h2_stats stats{};
     // per-stage timing (h2_profile)
     int prof = 0;
@@ -213,6 +215,9 @@ void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy
 void profile_read(h2_handle_s* h, double* ms, int64_t* n);
 void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                         int mode, cudaStream_t s);
+// X, Y in host memory: copy in, run_matvec on device staging buffers, copy out, synchronise.
+void run_matvec_host(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
+                     cudaStream_t s);
 bool tc_supported(const h2_handle_s* h);
 void tc_reserve(h2_handle_s* h, int mode, int nrhs);
 // ws_rmaj: the coefficient workspace is right-hand-side-major (ws[row * ws_ld + rhs]) instead of

@@ -725,9 +725,11 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
                         cudaStream_t s) {
     if (nrhs <= 0) return;
     if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: nrhs above 2,000,000");
+    if (mode == H2_TF32 || mode == H2_TF32X3)
+        fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: H2_TF32 and H2_TF32X3 need the tensor-core path's operand "
+                                 "workspace; use H2_FP32, H2_BF16 or h2_matvec");
     const size_t elt = (mode == H2_FP64) ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)h->plan.ws_rows * (size_t)nrhs * elt;
-    if (mode == H2_TF32 || mode == H2_TF32X3) mode = H2_FP32;   // the tensor-core path needs a staged operand copy: not here
     if (need > kNoAllocScratchBytes)
         fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: needs " + std::to_string(need) + " bytes of scratch (" +
                                      std::to_string(h->plan.ws_rows) + " coefficient rows x " + std::to_string(nrhs) +
@@ -857,6 +859,11 @@ void layout_factors(h2_handle_s* h) {
 }
 
 void build_plan(h2_handle_s* h, cudaStream_t s) {
+    // Every handle creation looks up the address of h2_matvec_noalloc's scratch array on the
+    // current device here, while allocating is still allowed: the lookup loads this file's
+    // device module (lazily loaded modules reserve their __device__ arrays when they load),
+    // so that a later h2_matvec_noalloc call never triggers that reservation.
+    noalloc_scratch();
     const h2_tree_s& T = *h->tree;
     const int L = T.L;
     auto K = [&](int l, int b) { return h->k[h->koff[l] + b]; };
@@ -1132,6 +1139,21 @@ constexpr size_t kMaxGraphs = 8;
 // The launch sequence of a repeated call (same buffers, sizes and mode) is captured in a CUDA
 // graph on its second occurrence and replayed afterwards, so that the many small launches of a
 // few-right-hand-side product are not paced by the host.  Profiled calls always launch directly.
+void run_matvec_host(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs, int mode,
+                     cudaStream_t s) {
+    if (nrhs <= 0) return;
+    if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_host: nrhs above 2,000,000");
+    const size_t ex = mode == H2_FP64 ? 8 : (mode == H2_BF16 ? 2 : 4);
+    const size_t ey = mode == H2_FP64 ? 8 : 4;
+    const size_t n = (size_t)h->N;
+    h->host_x.reserve(n * ex * (size_t)nrhs);
+    h->host_y.reserve(n * ey * (size_t)nrhs);
+    H2_CUDA(cudaMemcpy2DAsync(h->host_x.p, n * ex, X, (size_t)ldx * ex, n * ex, (size_t)nrhs, cudaMemcpyHostToDevice, s));
+    run_matvec(h, h->host_x.p, h->N, h->host_y.p, h->N, nrhs, mode, s);
+    H2_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * ey, h->host_y.p, n * ey, n * ey, (size_t)nrhs, cudaMemcpyDeviceToHost, s));
+    H2_CUDA(cudaStreamSynchronize(s));
+}
+
 void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
                 int mode, cudaStream_t s) {
     if (nrhs <= 0) return;

@@ -76,6 +76,21 @@ __global__ void scan_finite_kernel(int64_t N, int ncols, const double* __restric
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
 
+__global__ void sum_lists_kernel(const int64_t* __restrict__ out_off, const int* __restrict__ len,
+                                 const int* __restrict__ beg, const int* __restrict__ end,
+                                 const int64_t* __restrict__ in_off, const double* __restrict__ in,
+                                 double* __restrict__ out, int accumulate) {
+    const int o = blockIdx.x;
+    const int n = len[o];
+    const int b = beg[o], en = end[o];
+    double* dst = out + out_off[o];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        double s = accumulate ? dst[e] : 0.0;
+        for (int j = b; j < en; ++j) s += in[in_off[j] + e];
+        dst[e] = s;
+    }
+}
+
 __global__ void col_sqnorms_kernel(int64_t N, const double* __restrict__ x, int64_t ld, double* __restrict__ out) {
     const double* c = x + blockIdx.x * ld;
     double s = 0.0;
@@ -167,6 +182,14 @@ void scan_finite(int64_t N, int ncols, const double* x, int64_t ld, int* d_flag,
     after_launch("scan_finite");
 }
 
+
+void sum_lists(int count, const int64_t* d_out_off, const int* d_len, const int* d_begin,
+               const int* d_end, const int64_t* d_in_off, const double* in, double* out,
+               int accumulate, cudaStream_t s) {
+    if (count <= 0) return;
+    sum_lists_kernel<<<count, NT, 0, s>>>(d_out_off, d_len, d_begin, d_end, d_in_off, in, out, accumulate);
+    after_launch("sum_lists");
+}
 
 void col_sqnorms(int64_t N, int ncols, const double* x, int64_t ld, double* out, cudaStream_t s) {
     if (ncols <= 0) return;

@@ -23,6 +23,7 @@
 //    above the threshold (at most kmax) are kept, sorted by descending value.
 #include <algorithm>
 #include <cfloat>
+#include <cstring>
 #include <mutex>
 
 #include "common.h"
@@ -38,12 +39,10 @@ constexpr int kSplitRows = 4096;   // a single matrix taller than this is split 
 constexpr int kPartRows = 1024;    // rows per CTA of a split matrix
 constexpr size_t kSmemCap = 200 * 1024;
 
-constexpr int kSmemMaxC = 144;     // wider matrices keep their working matrix in global memory
-constexpr int kMaxC = 1024;
-constexpr int kGlobalCtas = 152;   // CTAs of a global-memory launch (one working matrix each)
+constexpr int kSmemMaxC = 144;     // widest matrix of stacked_r (its working matrix in shared memory)
 
 // rows of a chunk streamed under R: shared memory holds (c + chunk) x c doubles
-__host__ __device__ inline int chunk_rows(int c) { return c <= 96 ? 64 : (c <= 128 ? 32 : (c <= kSmemMaxC ? 16 : 64)); }
+__host__ __device__ inline int chunk_rows(int c) { return c <= 48 ? 128 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)); }
 // leading dimension of the working matrix [R; chunk]: odd, so that the columns of a warp's
 // column pairs fall in different shared-memory banks
 __host__ __device__ inline int work_ld(int c) { return (c + chunk_rows(c)) | 1; }
@@ -90,63 +89,176 @@ __device__ inline void apply_reflector(double* A, int lda, int c, int ch, int j,
     __syncwarp();
 }
 
-// R factor (upper c x c, rows 0..c-1 of A, leading dimension lda = c + chunk rows) of the
-// stacked row blocks segs[b..e).  Entry state of A is irrelevant; every thread returns
-// after a barrier with R complete.
+// R factor (upper c x c, rows 0..c-1 of A) of the stacked row blocks segs[b..e).  The
+// segments' rows are packed into chunks of up to chunk_rows(c) rows (a chunk may span
+// segments), so that short segments cost only their own rows.  Entry state of A is
+// irrelevant; every thread returns after a barrier with R complete.
 __device__ void stacked_qr(double* A, int lda, int c, const RowSeg* __restrict__ segs, int b, int e,
                            double* tau) {
+    __shared__ const double* rp[128];
+    __shared__ int rld[128];
+    __shared__ int hs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ch = chunk_rows(c);
     for (int x = threadIdx.x; x < c * c; x += SQ_NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
-    __syncthreads();
-    for (int sgi = b; sgi < e; ++sgi) {
-        const RowSeg sg = segs[sgi];
-        for (int r0 = 0; r0 < sg.rows; r0 += ch) {
-            const int h = min(ch, sg.rows - r0);
-            // load the chunk (zero rows beyond its end)
-            for (int x = threadIdx.x; x < ch * c; x += SQ_NT) {
-                const int i = x % ch, k = x / ch;
-                A[c + i + (int64_t)k * lda] = (i < h) ? sg.p[r0 + i + (int64_t)k * sg.ld] : 0.0;
+    int sgi = b, off = 0;   // next row: segment sgi, row off (the same in every thread)
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) {   // the rows of the next chunk
+            int h = 0, s2 = sgi, o2 = off;
+            while (h < ch && s2 < e) {
+                const RowSeg sg = segs[s2];
+                if (o2 >= sg.rows) { ++s2; o2 = 0; continue; }
+                rp[h] = sg.p + o2;
+                rld[h] = sg.ld;
+                ++h;
+                ++o2;
+            }
+            hs = h;
+        }
+        __syncthreads();
+        const int h = hs;
+        if (h == 0) break;
+        // the same walk in every thread keeps (sgi, off) uniform
+        {
+            int hh = 0;
+            while (hh < ch && sgi < e) {
+                const int rows = segs[sgi].rows;
+                if (off >= rows) { ++sgi; off = 0; continue; }
+                const int take = min(ch - hh, rows - off);
+                hh += take;
+                off += take;
+            }
+        }
+        for (int x = threadIdx.x; x < h * c; x += SQ_NT) {
+            const int i = x % h, k = x / h;
+            A[c + i + (int64_t)k * lda] = rp[i][(int64_t)k * rld[i]];
+        }
+        __syncthreads();
+        if (warp == 0) reflector(A, lda, c, h, 0, tau, lane);
+        __syncthreads();
+        for (int j = 0; j < c; ++j) {
+            const double tj = tau[j];
+            // columns k > j, owned by warp k % SQ_NW; the owner of j + 1 forms its reflector
+            // right after updating it, so one barrier per column suffices
+            int k = j + 1 + ((warp - (j + 1)) % SQ_NW + SQ_NW) % SQ_NW;
+            for (; k < c; k += SQ_NW) {
+                if (tj != 0.0) apply_reflector(A, lda, c, h, j, k, tj, lane);
+                if (k == j + 1) reflector(A, lda, c, h, k, tau, lane);
             }
             __syncthreads();
-            if (warp == 0) reflector(A, lda, c, ch, 0, tau, lane);
-            __syncthreads();
-            for (int j = 0; j < c; ++j) {
-                const double tj = tau[j];
-                // columns k > j, owned by warp k % SQ_NW; the owner of j + 1 forms its reflector
-                // right after updating it, so one barrier per column suffices
-                int k = j + 1 + ((warp - (j + 1)) % SQ_NW + SQ_NW) % SQ_NW;
-                for (; k < c; k += SQ_NW) {
-                    if (tj != 0.0) apply_reflector(A, lda, c, ch, j, k, tj, lane);
-                    if (k == j + 1) reflector(A, lda, c, ch, k, tau, lane);
-                }
-                __syncthreads();
-            }
         }
     }
 }
 
-// One CTA per job; with gwork the CTAs loop over the jobs, each with its own working matrix
-// in global memory (gstride doubles).  The c x c triangle of the incremental QR holds the
+// Householder QR with column pivoting (largest remaining column norm first) of the c x c
+// upper triangle R in rows 0..c-1 of A, in place: R P = Q3 R3.  perm[j] receives the column of
+// R that became column j.  Used before the one-sided Jacobi method: on the pivoted triangle it
+// needs about a third of the sweeps.
+__device__ void pivoted_qr(double* A, int lda, int c, int* perm, double* cn, double* tau) {
+    __shared__ int piv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < c; k += SQ_NT) perm[k] = k;
+    __syncthreads();
+    for (int j = 0; j < c; ++j) {
+        // norms of the trailing parts of columns j..c-1 (rows j..c-1), one warp per column
+        for (int k = j + warp; k < c; k += SQ_NW) {
+            double x = 0.0;
+            for (int i = j + lane; i < c; i += 32) {
+                const double a = A[i + (int64_t)k * lda];
+                x = fma(a, a, x);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) cn[k] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int p = j;
+            for (int k = j + 1; k < c; ++k)
+                if (cn[k] > cn[p]) p = k;
+            piv = p;
+            const int t = perm[j];
+            perm[j] = perm[p];
+            perm[p] = t;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != j)
+            for (int i = threadIdx.x; i < c; i += SQ_NT) {
+                const double t = A[i + (int64_t)j * lda];
+                A[i + (int64_t)j * lda] = A[i + (int64_t)p * lda];
+                A[i + (int64_t)p * lda] = t;
+            }
+        __syncthreads();
+        // reflector of column j on rows j..c-1 (one warp), then its application to columns > j
+        if (warp == 0) {
+            double x2 = 0.0;
+            for (int i = j + 1 + lane; i < c; i += 32) {
+                const double y = A[i + (int64_t)j * lda];
+                x2 = fma(y, y, x2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            const double alpha = A[j + (int64_t)j * lda];
+            double tj = 0.0, scale = 0.0, beta = alpha;
+            if (x2 > 0.0) {
+                beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
+                tj = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            if (tj != 0.0)
+                for (int i = j + 1 + lane; i < c; i += 32) A[i + (int64_t)j * lda] *= scale;
+            __syncwarp();
+            if (lane == 0) {
+                tau[j] = tj;
+                A[j + (int64_t)j * lda] = beta;
+            }
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        if (tj != 0.0)
+            for (int k = j + 1 + warp; k < c; k += SQ_NW) {
+                double w = 0.0;
+                for (int i = j + 1 + lane; i < c; i += 32) w = fma(A[i + (int64_t)j * lda], A[i + (int64_t)k * lda], w);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                w += A[j + (int64_t)k * lda];
+                const double f = tj * w;
+                for (int i = j + 1 + lane; i < c; i += 32)
+                    A[i + (int64_t)k * lda] = fma(-f, A[i + (int64_t)j * lda], A[i + (int64_t)k * lda]);
+                __syncwarp();
+                if (lane == 0) A[j + (int64_t)k * lda] -= f;
+            }
+        __syncthreads();
+    }
+    // the reflectors below the diagonal are not needed: only R3 is used
+    for (int x = threadIdx.x; x < c * c; x += SQ_NT) {
+        const int i = x % c, k = x / c;
+        if (i > k) A[i + (int64_t)k * lda] = 0.0;
+    }
+    __syncthreads();
+}
+
+// One CTA per job.  The c x c triangle of the incremental QR holds the
 // rank of the stack in the rows of the columns where it appears (a stack with fewer rows
 // than columns, or with leading zero columns, leaves other rows zero), so the output is
 // compacted: the min(c, rows) rows of largest norm are written first (R^T R, the only use of
 // R, does not depend on the order of its rows) and the remaining rows -- zero in exact
 // arithmetic -- are written as zeros.
 __global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __restrict__ jobs, int njobs,
-                                                          const RowSeg* __restrict__ segs, double* __restrict__ gwork,
-                                                          int64_t gstride) {
+                                                          const RowSeg* __restrict__ segs) {
     extern __shared__ double smem[];
-    __shared__ double tau[kMaxC];
-    __shared__ double rn[kMaxC];
-    __shared__ int src[kMaxC];
+    __shared__ double tau[kSmemMaxC];
+    __shared__ double rn[kSmemMaxC];
+    __shared__ int src[kSmemMaxC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int jbi = blockIdx.x; jbi < njobs; jbi += gridDim.x) {
         const StackJob jb = jobs[jbi];
         const int c = jb.c;
         if (c <= 0) continue;
         const int lda = work_ld(c);
-        double* A = gwork ? gwork + (int64_t)blockIdx.x * gstride : smem;
+        double* A = smem;
         stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
         int rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs[i].rows;
@@ -187,6 +299,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
     __shared__ double tau[SVD_MAXC];
     __shared__ double sig[SVD_MAXC + 1];
     __shared__ int rank[SVD_MAXC];
+    __shared__ int perm[SVD_MAXC];
     __shared__ int kk;
     const StackJob jb = jobs[blockIdx.x];
     const int c = jb.c;
@@ -200,17 +313,48 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
     double* A = smem;                         // lda x c: [R; chunk]
     double* B = smem + (int64_t)lda * c;      // ldb x np: R^T and a zero padding column
     stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
+    // W^T = Q1 R1 and R1 P = Q3 R3 give W = P R3^T (Q1 Q3)^T: the left singular vectors of W
+    // are those of R3^T with their rows permuted by P
+    pivoted_qr(A, lda, c, perm, sig, tau);
     for (int x = threadIdx.x; x < c * np; x += SQ_NT) {
         const int i = x % c, k = x / c;
         B[i + (int64_t)k * ldb] = (k < c && i >= k) ? A[k + (int64_t)i * lda] : 0.0;
     }
     __syncthreads();
+    const int g = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    // columns of B at rounding level (norm <= c eps max norm) are set to zero: a perturbation
+    // of B at rounding level, and Jacobi rotations against them would not converge
+    for (int j0 = 0; j0 < np; j0 += 32) {
+        const int j = j0 + g;
+        double s2 = 0.0;
+        if (j < np)
+            for (int i = sub; i < c; i += 8) {
+                const double a = B[i + (int64_t)j * ldb];
+                s2 = fma(a, a, s2);
+            }
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+        if (sub == 0 && j < np) sig[j] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int j = 0; j < np; ++j) mx = fmax(mx, sig[j]);
+        tau[0] = mx * ((double)c * DBL_EPSILON) * ((double)c * DBL_EPSILON);
+    }
+    __syncthreads();
+    const double floor2 = tau[0];
+    for (int x = threadIdx.x; x < c * np; x += SQ_NT) {
+        const int i = x % c, k = x / c;
+        if (sig[k] <= floor2) B[i + (int64_t)k * ldb] = 0.0;
+    }
+    __syncthreads();
     // one-sided Jacobi on the columns of B = R^T (W = B Q^T): 8 threads per column pair,
     // 32 pairs at a time; at convergence the columns of B V are orthogonal and their
     // normalised values are the left singular vectors of W
-    const int g = threadIdx.x >> 3, sub = threadIdx.x & 7;
     const int half = np / 2;
-    const double tol = 4.0 * sqrt((double)c) * DBL_EPSILON;   // orthogonality reached: no rotation
+    const double tol = 2.0 * (double)c * DBL_EPSILON;   // orthogonality reached (rounding of the dot products)
     for (int sweep = 0; sweep < 60; ++sweep) {
         int rotated = 0;
         for (int r = 0; r < np - 1; ++r) {
@@ -295,7 +439,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
     for (int x = threadIdx.x; x < c * c; x += SQ_NT) {
         const int row = x % c, j = x / c;
         const int rk = rank[j];
-        if (rk < k) jb.out[row + (int64_t)rk * jb.ldo] = B[row + (int64_t)j * ldb] / sig[j];
+        if (rk < k) jb.out[perm[row] + (int64_t)rk * jb.ldo] = B[row + (int64_t)j * ldb] / sig[j];
     }
 }
 
@@ -319,7 +463,7 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     std::vector<Split> splits;
     for (const StackJob& jb : jobs_in) {
         if (jb.c <= 0) continue;
-        if (jb.c > kMaxC) fail(H2_ERR_INVALID_ARG, "stacked_r: more than 1024 columns");
+        if (jb.c > kSmemMaxC) fail(H2_ERR_INVALID_ARG, "stacked_r: more than 144 columns");
         int64_t rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs_in[i].rows;
         StackJob j = jb;
@@ -346,26 +490,23 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     });
-    auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
+    // one launch per shared-memory size of the jobs' working matrices (in increasing order), so
+    // that narrow matrices are not launched with the shared memory of the widest
+    auto launch = [&](std::vector<StackJob> js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
         if (js.empty()) return;
-        int cm = 0;
-        for (auto& j : js) cm = std::max(cm, j.c);
+        std::stable_sort(js.begin(), js.end(),
+                         [](const StackJob& a, const StackJob& b) { return qr_smem_bytes(a.c) < qr_smem_bytes(b.c); });
         upload(dj, js, s, stj);
         upload(dsg, ss, s, sts);
-        size_t dyn = qr_smem_bytes(cm);
-        double* gw = nullptr;
-        int64_t gstride = 0;
-        unsigned grid = (unsigned)js.size();
-        if (cm > kSmemMaxC) {   // wide matrices: the working matrices live in global memory
-            grid = std::min<unsigned>(grid, kGlobalCtas);
-            gstride = (int64_t)work_ld(cm) * cm;
-            w.gwork.reserve((size_t)gstride * grid);
-            gw = w.gwork.p;
-            dyn = 0;
+        for (size_t b = 0; b < js.size();) {
+            size_t e = b;
+            const size_t dyn = std::max<size_t>(qr_smem_bytes(js[b].c), 16);
+            while (e < js.size() && qr_smem_bytes(js[e].c) == qr_smem_bytes(js[b].c)) ++e;
+            stacked_r_kernel<<<(unsigned)(e - b), SQ_NT, dyn, s>>>(dj.p + b, (int)(e - b), dsg.p);
+            after_launch("stacked_r");
+            b = e;
         }
-        stacked_r_kernel<<<grid, SQ_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p, gw, gstride);
-        after_launch("stacked_r");
     };
     if (!parts.empty()) {
         int64_t elems = 0;
@@ -397,18 +538,134 @@ void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowS
     int cm = 0;
     for (auto& j : jobs) cm = std::max(cm, j.c);
     if (cm > SVD_MAXC) fail(H2_ERR_INVALID_ARG, "stacked_svd: matrix order above 96");
-    upload(w.d_jobs, jobs, s, w.st_jobs);
+    // one launch per shared-memory size (in increasing order), as for stacked_r
+    std::vector<StackJob> js = jobs;
+    auto need = [](const StackJob& j) { return j.c > 0 ? svd_smem_bytes(j.c) : (size_t)16; };
+    std::stable_sort(js.begin(), js.end(), [&](const StackJob& a, const StackJob& b) { return need(a) < need(b); });
+    upload(w.d_jobs, js, s, w.st_jobs);
     upload(w.d_segs, segs, s, w.st_segs);
     static std::once_flag attr;
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)svd_smem_bytes(SVD_MAXC)));
     });
-    const size_t smem = std::max<size_t>(svd_smem_bytes(std::max(cm, 1)), 16);
-    stacked_svd_kernel<<<(unsigned)jobs.size(), SQ_NT, smem, s>>>(w.d_jobs.p, w.d_segs.p, thr, kmax, d_cap_flag);
-    after_launch("stacked_svd");
+    for (size_t b = 0; b < js.size();) {
+        size_t e = b;
+        while (e < js.size() && need(js[e]) == need(js[b])) ++e;
+        stacked_svd_kernel<<<(unsigned)(e - b), SQ_NT, need(js[b]), s>>>(w.d_jobs.p + b, w.d_segs.p, thr, kmax,
+                                                                          d_cap_flag);
+        after_launch("stacked_svd");
+        b = e;
+    }
 }
 
 int svd_max_order() { return SVD_MAXC; }
+
+int stacked_r_max_columns() { return kSmemMaxC; }
+
+namespace {
+
+// Cholesky factorisation with symmetric (diagonal) pivoting of a symmetric positive
+// semidefinite matrix (the rank-revealing form: the largest remaining diagonal is the next
+// pivot, and the factorisation stops once it is at rounding level), one CTA per matrix.
+// The trailing Schur complement is kept in full (both triangles) so that rows and columns can
+// be swapped; columns 0..j-1 hold the finished columns of L.
+__global__ void __launch_bounds__(SQ_NT) psd_chol_small_kernel(const CholItem* __restrict__ items) {
+    extern __shared__ double A[];   // m x m, leading dimension m + 1
+    __shared__ int perm[SVD_MAXC];
+    __shared__ int piv;
+    __shared__ double pval, drop_s;
+    const CholItem it = items[blockIdx.x];
+    const int m = it.m, ld = m + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int x = threadIdx.x; x < m * m; x += SQ_NT) {
+        const int i = x % m, j = x / m;
+        A[i + j * ld] = (i >= j) ? it.G[i + (int64_t)j * it.ldg] : it.G[j + (int64_t)i * it.ldg];
+    }
+    if (threadIdx.x < m) perm[threadIdx.x] = threadIdx.x;
+    __syncthreads();
+    if (warp == 0) {
+        double mx = 0.0;
+        for (int i = lane; i < m; i += 32) mx = fmax(mx, A[i + i * ld]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) drop_s = (double)m * 0x1p-52 * mx;
+    }
+    __syncthreads();
+    const double drop = drop_s;
+    int jend = m;
+    for (int j = 0; j < m; ++j) {
+        if (warp == 0) {   // pivot: the largest remaining diagonal
+            double bv = -1.0;
+            int bi = j;
+            for (int i = j + lane; i < m; i += 32) {
+                const double v = A[i + i * ld];
+                if (v > bv) { bv = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { piv = bi; pval = bv; }
+        }
+        __syncthreads();
+        if (!(pval > drop)) { jend = j; break; }   // the same in every thread: the rest is rounding
+        const int p = piv;
+        if (p != j) {
+            for (int c = threadIdx.x; c < m; c += SQ_NT) {   // swap rows j and p
+                const double t = A[j + c * ld];
+                A[j + c * ld] = A[p + c * ld];
+                A[p + c * ld] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += SQ_NT) {   // swap columns j and p
+                const double t = A[r + j * ld];
+                A[r + j * ld] = A[r + p * ld];
+                A[r + p * ld] = t;
+            }
+            if (threadIdx.x == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+            __syncthreads();
+        }
+        const double ljj = sqrt(A[j + j * ld]);
+        __syncthreads();
+        for (int i = j + threadIdx.x; i < m; i += SQ_NT) A[i + j * ld] = (i == j) ? ljj : A[i + j * ld] / ljj;
+        __syncthreads();
+        const int r = m - j - 1;
+        for (int x = threadIdx.x; x < r * r; x += SQ_NT) {   // full trailing Schur complement
+            const int i = j + 1 + x % r, k = j + 1 + x / r;
+            A[i + k * ld] -= A[i + j * ld] * A[k + j * ld];
+        }
+        __syncthreads();
+    }
+    // out = F^T with F = P L (F F^T = G): row j of out holds column j of L at the original indices
+    for (int x = threadIdx.x; x < m * m; x += SQ_NT) {
+        const int jr = x % m, i = x / m;   // out row jr, pivot position i
+        const double v = (jr < jend && i >= jr) ? A[i + jr * ld] : 0.0;
+        it.out[jr + (int64_t)perm[i] * it.ldo] = v;
+    }
+}
+
+}  // namespace
+
+void psd_chol_small(const std::vector<CholItem>& items, StackWork& w, cudaStream_t s) {
+    if (items.empty()) return;
+    for (const CholItem& it : items)
+        if (it.m < 1 || it.m > SVD_MAXC) fail(H2_ERR_INVALID_ARG, "psd_chol_small: order out of range");
+    int mm = 1;
+    for (const CholItem& it : items) mm = std::max(mm, it.m);
+    std::vector<unsigned char> raw(items.size() * sizeof(CholItem));
+    std::memcpy(raw.data(), items.data(), raw.size());
+    upload(w.d_chol, raw, s, w.st_chol);
+    static std::once_flag attr;
+    std::call_once(attr, [&] {
+        H2_CUDA(cudaFuncSetAttribute(psd_chol_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(SVD_MAXC * (SVD_MAXC + 1) * sizeof(double))));
+    });
+    psd_chol_small_kernel<<<(unsigned)items.size(), SQ_NT, (size_t)mm * (mm + 1) * sizeof(double), s>>>(
+        reinterpret_cast<const CholItem*>(w.d_chol.p));
+    after_launch("psd_chol_small");
+}
 
 }  // namespace h2

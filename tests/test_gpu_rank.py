@@ -237,7 +237,7 @@ def test_learned_start_saves_operator_calls(h2):
     feats, targ = [], []
     for (p, _, t), G in zip(train, Gs):
         f = h2.rank_features(t, p.kappa * p.T, p.m / p.N, tol)
-        lv, tg = h2.rank_targets(G.stats())
+        lv, tg = h2.rank_targets(G)
         feats.append(f[lv])
         targ += tg
     X = np.concatenate(feats).astype(np.float32)

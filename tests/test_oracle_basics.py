@@ -172,3 +172,21 @@ def test_pair_level():
     assert Partition.pair_level(2, 2, 3) == 2
     assert Partition.pair_level(3, 0, 7) == 1
     assert Partition.pair_level(3, 4, 6) == 2
+
+
+def test_factor_layout_round_trip():
+    """tests/factors.py: oracle factors -> h2_import layout -> oracle H2Matrix gives the same
+    matrix (the test helper that reads exported GPU factors into the oracle)."""
+    import factors
+    import oracle as O
+
+    n = 24
+    mask = W.sensor_mask(n * n, 100, 7)
+    op = O.HeatHessian(n, 0.01, 0.5, 0.01, mask)
+    h = O.build(op, W.grid_coords(n), 32, ADM_STRONG, 0.7, 1e-6, 24, 16, 16, 128, True, 3)[0]
+    g = factors.import_to_oracle(h.tree, h.part, *factors.oracle_to_import(h))
+    A = O.expand_dense(h)
+    assert np.abs(O.expand_dense(g) - A).max() <= 1e-14 * np.abs(A).max()   # BLAS layouts differ: rounding only
+    X = W.rhs(n * n, 3, 1)
+    Y = O.matvec(h, X)
+    assert np.abs(O.matvec(g, X) - Y).max() <= 1e-14 * np.abs(Y).max()
