@@ -252,8 +252,12 @@ int h2_build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2
  * leading dimension ldx >= n) and Y (n x nrhs, ldy >= n) are device buffers in
  * original node order; their element types follow `mode` (see H2_FP64..H2_BF16).
  * X and Y must not overlap.  Enqueued on `stream`; returns before completion.
- * Errors: INVALID_ARG (sizes, NULL pointers, a mode whose storage copy was not
- * kept), CUDA, OOM.
+ * The coefficient workspace belongs to the handle: FP64 calls with up to 32 right-hand
+ * sides use the part reserved at the handle's creation; wider calls and the reduced-
+ * precision modes grow it once (an allocation) and keep it.  A call repeated with the same
+ * buffers, sizes and mode is captured in a CUDA graph on its second occurrence and
+ * replayed afterwards.  Errors: INVALID_ARG (sizes, NULL pointers, a mode whose storage
+ * copy was not kept), CUDA, OOM.
  */
 int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t nrhs,
               int mode, h2_stream_t stream);

@@ -188,7 +188,13 @@ struct h2_handle_s {
     std::vector<MvGraph> graphs;
     uint64_t graph_clock = 0;
     cudaStream_t cap = nullptr;
+    // second stream of the small-nrhs matvec (near field beside the tree sweeps) and its events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~h2_handle_s() {
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
             if (g.graph) cudaGraphDestroy(g.graph);

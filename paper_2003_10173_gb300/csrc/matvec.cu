@@ -371,8 +371,10 @@ __global__ void __launch_bounds__(256) mv_small_stage_kernel(const MvOut* __rest
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             if (OUT_Y) {
+                // the near-field scatter may be adding into Y concurrently (another stream): atomic
                 TY* y = Y + perm[o.out_off + i] + (int64_t)r * ldy;
-                *y = accumulate ? (TY)(*y + acc[q][r]) : (TY)acc[q][r];
+                if (accumulate) atomicAdd(y, (TY)acc[q][r]);
+                else *y = (TY)acc[q][r];
             } else {
                 TA* y = ws + o.out_off + i + (int64_t)r * ws_ld;
                 *y = accumulate ? (TA)(*y + acc[q][r]) : acc[q][r];
@@ -471,11 +473,12 @@ __global__ void __launch_bounds__(SW * 32) mv_scatter_kernel(const SymItem* __re
                     for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
                 }
             } else {
-                // FP64 storage is FP64-pipe bound: fewer registers, more resident warps
-#pragma unroll 8
-                for (int c = 0; c < 32; ++c) {
+                // FP64 storage is FP64-pipe bound: loop over the tile's actual columns only (a
+                // coupling block of rank k < 32 costs k, not 32, FP64 instructions per lane)
+#pragma unroll 4
+                for (int c = 0; c < nc; ++c) {
                     TA d = (TA)0;
-                    if (rin && c < nc) d = cvt<TA>(M[i + (int64_t)(j0 + c) * it.ldm]);
+                    if (rin) d = cvt<TA>(M[i + (int64_t)(j0 + c) * it.ldm]);
                     T[c][lane] = d;
 #pragma unroll
                     for (int r = 0; r < NR; ++r) yt[r] = fma(d, __shfl_sync(0xffffffffu, xs[r], c), yt[r]);
@@ -486,8 +489,10 @@ __global__ void __launch_bounds__(SW * 32) mv_scatter_kernel(const SymItem* __re
                 TA ys[NR];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) ys[r] = (TA)0;
-#pragma unroll 8
-                for (int row = 0; row < 32; ++row) {
+                // rows of this tile (the FP32 path fills all 32, with zeros beyond the block)
+                const int nr = (sizeof(TS) <= 4) ? 32 : min(32, it.rows - i0);
+#pragma unroll 4
+                for (int row = 0; row < nr; ++row) {
                     const TA d = T[lane][row];
 #pragma unroll
                     for (int r = 0; r < NR; ++r) ys[r] = fma(d, __shfl_sync(0xffffffffu, xt[r], row), ys[r]);
@@ -601,7 +606,7 @@ constexpr int kSmallNrhs = 4;
 
 template <class TS, class TX, class TY, class TA>
 void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy, int nrhs,
-               cudaStream_t s, bool prof) {
+               cudaStream_t s, bool prof, bool may_fork) {
     const MatvecPlan& P = h->plan;
     const int64_t wld = P.ws_rows;
     auto timed = [&](int kind, auto&& fn) {
@@ -616,7 +621,23 @@ void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, 
     H2_CUDA(cudaMemset2DAsync(Y, ldy * sizeof(TY), 0, h->N * sizeof(TY), nrhs, s));
     if (wld > P.yh_row0)
         H2_CUDA(cudaMemset2DAsync(ws + P.yh_row0, wld * sizeof(TA), 0, (wld - P.yh_row0) * sizeof(TA), nrhs, s));
-    timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    // The near field (the bulk of the arithmetic, independent of the coefficient sweeps) runs on a
+    // second stream beside the latency-bound chain of tree stages; both add into Y atomically.
+    // Profiled calls keep one stream so that every stage is timed on its own.
+    const bool overlap = may_fork && !prof && !P.near.items.empty();
+    if (overlap) {
+        if (!h->side) {
+            H2_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+            H2_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            H2_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
+        H2_CUDA(cudaEventRecord(h->ev_fork, s));
+        H2_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, h->side);
+        H2_CUDA(cudaEventRecord(h->ev_join, h->side));
+    } else {
+        timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+    }
     for (const MvStage& st : P.small_up)
         timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     timed(H2_STAGE_COUPLE, [&] { launch_scatter<TS, TX, TY, TA>(P.couple, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
@@ -625,13 +646,15 @@ void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, 
     timed(H2_STAGE_LEAF_NEAR, [&] {
         launch_small_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
     });
+    if (overlap) H2_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
 }
 
 template <class TS, class TX, class TY, class TA>
 void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy,
              int nrhs, cudaStream_t s, bool allow_prof = true) {
     if (nrhs <= kSmallNrhs) {
-        run_small<TS, TX, TY, TA>(h, fac, ws, X, ldx, Y, ldy, nrhs, s, allow_prof && h->prof);
+        // the no-allocation entry point (allow_prof false) creates no second stream
+        run_small<TS, TX, TY, TA>(h, fac, ws, X, ldx, Y, ldy, nrhs, s, allow_prof && h->prof, allow_prof);
         return;
     }
     for (const MvStage& st : h->plan.stages) {
@@ -858,6 +881,8 @@ void layout_factors(h2_handle_s* h) {
     h->fac64.reserve((size_t)std::max<int64_t>(off, 1));
 }
 
+constexpr int64_t kReserveNrhs = 32;
+
 void build_plan(h2_handle_s* h, cudaStream_t s) {
     // Every handle creation looks up the address of h2_matvec_noalloc's scratch array on the
     // current device here, while allocating is still allowed: the lookup loads this file's
@@ -879,6 +904,15 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
     MatvecPlan& P = h->plan;
     P.ws_rows = std::max<int64_t>(rows, 1);
     P.yh_row0 = ytop;
+    // the FP64 coefficient workspace for up to kReserveNrhs right-hand sides is reserved with the
+    // handle, so that a first h2_matvec with few right-hand sides does not allocate
+    h->ws.f64.reserve((size_t)P.ws_rows * kReserveNrhs);
+    // the second stream of the small-nrhs matvec and its events, created with the handle
+    if (!h->side) {
+        H2_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        H2_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        H2_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     auto xrow = [&](int l, int b) { return box_row[h->koff[l] + b]; };
     auto yrow = [&](int l, int b) { return ytop + box_row[h->koff[l] + b]; };
     const int64_t wld = P.ws_rows;

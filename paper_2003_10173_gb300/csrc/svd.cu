@@ -43,9 +43,12 @@ constexpr int kSmemMaxC = 144;     // widest matrix of stacked_r (its working ma
 
 // rows of a chunk streamed under R: shared memory holds (c + chunk) x c doubles
 __host__ __device__ inline int chunk_rows(int c) { return c <= 48 ? 128 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)); }
+// chunk height of the SVD kernel: fixed, so that its shared memory grows with c (one launch per level)
+constexpr int kSvdChunk = 64;
 // leading dimension of the working matrix [R; chunk]: odd, so that the columns of a warp's
 // column pairs fall in different shared-memory banks
-__host__ __device__ inline int work_ld(int c) { return (c + chunk_rows(c)) | 1; }
+__host__ __device__ inline int work_ld(int c, int ch) { return (c + ch) | 1; }
+__host__ __device__ inline int work_ld(int c) { return work_ld(c, chunk_rows(c)); }
 
 // Householder reflector of column j of the stacked [R; chunk] (rows c .. c+ch-1 hold the
 // chunk), computed by one warp: zeroes the chunk part of column j against R[j, j].
@@ -93,13 +96,12 @@ __device__ inline void apply_reflector(double* A, int lda, int c, int ch, int j,
 // segments' rows are packed into chunks of up to chunk_rows(c) rows (a chunk may span
 // segments), so that short segments cost only their own rows.  Entry state of A is
 // irrelevant; every thread returns after a barrier with R complete.
-__device__ void stacked_qr(double* A, int lda, int c, const RowSeg* __restrict__ segs, int b, int e,
+__device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __restrict__ segs, int b, int e,
                            double* tau) {
     __shared__ const double* rp[128];
     __shared__ int rld[128];
     __shared__ int hs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ch = chunk_rows(c);
     for (int x = threadIdx.x; x < c * c; x += SQ_NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
     int sgi = b, off = 0;   // next row: segment sgi, row off (the same in every thread)
     while (true) {
@@ -108,11 +110,14 @@ __device__ void stacked_qr(double* A, int lda, int c, const RowSeg* __restrict__
             int h = 0, s2 = sgi, o2 = off;
             while (h < ch && s2 < e) {
                 const RowSeg sg = segs[s2];
-                if (o2 >= sg.rows) { ++s2; o2 = 0; continue; }
-                rp[h] = sg.p + o2;
-                rld[h] = sg.ld;
-                ++h;
-                ++o2;
+                const int take = min(ch - h, sg.rows - o2);
+                for (int i = 0; i < take; ++i) {
+                    rp[h + i] = sg.p + o2 + i;
+                    rld[h + i] = sg.ld;
+                }
+                h += take;
+                o2 += take;
+                if (o2 >= sg.rows) { ++s2; o2 = 0; }
             }
             hs = h;
         }
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __rest
         if (c <= 0) continue;
         const int lda = work_ld(c);
         double* A = smem;
-        stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
+        stacked_qr(A, lda, c, chunk_rows(c), segs, jb.seg_begin, jb.seg_end, tau);
         int rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs[i].rows;
         const int reff = min(c, rows);
@@ -308,11 +313,11 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
         return;
     }
     const int np = c + (c & 1);          // even order for the round-robin schedule (zero column added)
-    const int lda = work_ld(c);
+    const int lda = work_ld(c, kSvdChunk);
     const int ldb = c | 1;
     double* A = smem;                         // lda x c: [R; chunk]
     double* B = smem + (int64_t)lda * c;      // ldb x np: R^T and a zero padding column
-    stacked_qr(A, lda, c, segs, jb.seg_begin, jb.seg_end, tau);
+    stacked_qr(A, lda, c, kSvdChunk, segs, jb.seg_begin, jb.seg_end, tau);
     // W^T = Q1 R1 and R1 P = Q3 R3 give W = P R3^T (Q1 Q3)^T: the left singular vectors of W
     // are those of R3^T with their rows permuted by P
     pivoted_qr(A, lda, c, perm, sig, tau);
@@ -445,9 +450,9 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
 
 size_t qr_smem_bytes(int c) { return (size_t)work_ld(c) * c * sizeof(double); }
 
-size_t svd_smem_bytes(int c) {
+size_t svd_smem_bytes(int c) {   // increasing in c
     const int np = c + (c & 1);
-    return (size_t)work_ld(c) * c * sizeof(double) + (size_t)(c | 1) * np * sizeof(double);
+    return (size_t)work_ld(c, kSvdChunk) * c * sizeof(double) + (size_t)(c | 1) * np * sizeof(double);
 }
 
 }  // namespace
@@ -490,23 +495,17 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     });
-    // one launch per shared-memory size of the jobs' working matrices (in increasing order), so
-    // that narrow matrices are not launched with the shared memory of the widest
-    auto launch = [&](std::vector<StackJob> js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
+    // one launch; the working matrix's size is not monotone in c (the chunk height steps down at
+    // 49, 97 and 129 columns), so the launch takes the largest requirement of its jobs
+    auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
         if (js.empty()) return;
-        std::stable_sort(js.begin(), js.end(),
-                         [](const StackJob& a, const StackJob& b) { return qr_smem_bytes(a.c) < qr_smem_bytes(b.c); });
+        size_t dyn = 16;
+        for (auto& j : js) dyn = std::max(dyn, qr_smem_bytes(j.c));
         upload(dj, js, s, stj);
         upload(dsg, ss, s, sts);
-        for (size_t b = 0; b < js.size();) {
-            size_t e = b;
-            const size_t dyn = std::max<size_t>(qr_smem_bytes(js[b].c), 16);
-            while (e < js.size() && qr_smem_bytes(js[e].c) == qr_smem_bytes(js[b].c)) ++e;
-            stacked_r_kernel<<<(unsigned)(e - b), SQ_NT, dyn, s>>>(dj.p + b, (int)(e - b), dsg.p);
-            after_launch("stacked_r");
-            b = e;
-        }
+        stacked_r_kernel<<<(unsigned)js.size(), SQ_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p);
+        after_launch("stacked_r");
     };
     if (!parts.empty()) {
         int64_t elems = 0;
@@ -538,25 +537,16 @@ void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowS
     int cm = 0;
     for (auto& j : jobs) cm = std::max(cm, j.c);
     if (cm > SVD_MAXC) fail(H2_ERR_INVALID_ARG, "stacked_svd: matrix order above 96");
-    // one launch per shared-memory size (in increasing order), as for stacked_r
-    std::vector<StackJob> js = jobs;
-    auto need = [](const StackJob& j) { return j.c > 0 ? svd_smem_bytes(j.c) : (size_t)16; };
-    std::stable_sort(js.begin(), js.end(), [&](const StackJob& a, const StackJob& b) { return need(a) < need(b); });
-    upload(w.d_jobs, js, s, w.st_jobs);
+    upload(w.d_jobs, jobs, s, w.st_jobs);
     upload(w.d_segs, segs, s, w.st_segs);
     static std::once_flag attr;
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)svd_smem_bytes(SVD_MAXC)));
     });
-    for (size_t b = 0; b < js.size();) {
-        size_t e = b;
-        while (e < js.size() && need(js[e]) == need(js[b])) ++e;
-        stacked_svd_kernel<<<(unsigned)(e - b), SQ_NT, need(js[b]), s>>>(w.d_jobs.p + b, w.d_segs.p, thr, kmax,
-                                                                          d_cap_flag);
-        after_launch("stacked_svd");
-        b = e;
-    }
+    stacked_svd_kernel<<<(unsigned)jobs.size(), SQ_NT, svd_smem_bytes(std::max(cm, 1)), s>>>(
+        w.d_jobs.p, w.d_segs.p, thr, kmax, d_cap_flag);
+    after_launch("stacked_svd");
 }
 
 int svd_max_order() { return SVD_MAXC; }
