@@ -515,7 +515,8 @@ def inversion_section(h2, torch, stream) -> dict:
     0.01 ||H~|| (condition number about 100); Newton-Schulz with the static threshold, with the
     dynamic threshold (loosest 1e-2), and order-8 hyperpower with the dynamic threshold, each from
     X_0 = I / ||A||_2 to ||A X - I||_2 <= 1e-4 (construction floor 1e-4 / (||A|| ||X_k||), about
-    1e-6 near convergence: the paper's construction threshold)."""
+    1e-6 near convergence: the paper's construction threshold).  Then the warm-started inversion of
+    a nearby Hessian from that inverse: Newton-Schulz iterations against unrolled ones."""
     c = scaled(W.MEDIUM_N256, 128)
     p, b = c["problem"], c["build"]
     gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
@@ -525,16 +526,40 @@ def inversion_section(h2, torch, stream) -> dict:
     bopts = h2.default_opts(kmax=48, q0=16, b_inc=8, q_max=512, adaptive=1, seed=b.seed, stream=stream)
     eps = 1e-4
     out = {"workload": f"heat2d_n128 regularised, A = H~ + {beta:.4g} I", "N": p.N, "eps": eps, "runs": {}}
+    def record(key, st, t0, **extra):
+        out["runs"][key] = {"iterations": st["iterations"], "converged": st["converged"],
+                            "final_err": st["final_err"], "samples_total": int(sum(st["samples"])),
+                            "samples": st["samples"], "seconds": time.perf_counter() - t0,
+                            "build_seconds": float(sum(st["t_build"])), **extra}
+
+    prev = None
     for key, order, loose in (("ns_static", 2, eps), ("ns_dynamic", 2, 1e-2), ("hyperpower8_dynamic", 8, 1e-2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         X, st = h2.invert(HA, shift=beta, order=order, eps=eps, eps_loose=loose, build_opts=bopts)
         torch.cuda.synchronize()
-        out["runs"][key] = {"order": order, "eps_loose": loose, "iterations": st["iterations"],
-                            "converged": st["converged"], "final_err": st["final_err"],
-                            "samples_total": int(sum(st["samples"])), "samples": st["samples"],
-                            "seconds": time.perf_counter() - t0, "build_seconds": float(sum(st["t_build"]))}
+        record(key, st, t0, order=order, eps_loose=loose)
+        if key == "ns_dynamic":
+            prev = X
+        else:
+            X.close()
+    # Warm start (Appendix A: the next optimisation iterate's Hessian, inverted from the previous
+    # inverse): the same family with kappa 5 % larger; Newton-Schulz from X_0 = the previous inverse
+    # against the unrolled iterations (k steps in one construction)
+    gop2 = h2.HeatOperator(p.n, 1.05 * p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+    HB = h2.H2.build(gop2, tree, b.tol, h2.default_opts(kmax=b.kmax, stream=stream))
+    out["warm_start"] = {"workload": "A' = H~' + beta I, H~' of the same family with kappa x 1.05; X_0 = the "
+                                     "ns_dynamic inverse of A"}
+    for key, kw in (("warm_ns_static", dict(order=2, eps_loose=eps)), ("warm_ns_dynamic", dict(order=2, eps_loose=1e-2)),
+                    ("warm_unrolled_2", dict(unroll=2, eps_loose=eps)), ("warm_unrolled_3", dict(unroll=3, eps_loose=eps))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, st = h2.invert(HB, shift=beta, eps=eps, build_opts=bopts, x0=prev, **kw)
+        torch.cuda.synchronize()
+        record(key, st, t0, start_err=st["err"][0], **kw)
         X.close()
+    prev.close()
+    HB.close()
     out["context_paper_p100_s"] = {"ns_static": 178, "ns_dynamic": 51, "hyperpower8": 20,
                                    "note": "minimal-surface Hessian at n = 16,384 on a P100 (Appendix A); "
                                            "another operator and machine: context only"}

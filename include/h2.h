@@ -380,7 +380,8 @@ void h2_free(h2_handle_t h);
  * res_rtol relative change); eps_loose = eps gives the static threshold.  The iteration stops at
  * E <= eps, after max_iter iterates, or when an iterate stalls (E_{k+1} > 0.9 E_k while the exact
  * iteration would reach E_k^l < 0.5 E_{k+1}).  Not a construct of this library's paper beyond
- * Appendix A; the readings above are the library's.
+ * Appendix A; the readings above are the library's.  With x0 the iteration starts from a given
+ * iterate; with unroll it constructs one unrolled iterate (see the fields below).
  */
 #define H2_MAX_INVERT_ITERS 64
 typedef struct {
@@ -393,6 +394,18 @@ typedef struct {
     int res_maxit;       /* power-iteration cap of the norm and residual estimates (default 50) */
     double res_rtol;     /* their stop: relative change (default 1e-2) */
     uint64_t seed;       /* seed of the power-iteration start vectors (default 9) */
+    /* Warm start (Appendix A: a previous approximate inverse as the initial iterate): X_0 = x0
+     * (an H^2 handle on A's tree, e.g. an earlier h2_invert result; it is only read and stays the
+     * caller's) instead of alpha I.  Default NULL. */
+    h2_handle_t x0;
+    /* Unrolled iterations (Appendix A, "Unrolling iterations"): unroll = k >= 1 constructs the k-th
+     * Newton-Schulz iterate of X_0 in one construction, X_k = X_0 sum_{i < 2^k} (I - A X_0)^i (the
+     * product prod_{j<k} (I + R_0^{2^j}) of k Newton-Schulz steps written as one geometric sum;
+     * Appendix A prints this identity garbled), evaluated on the probe blocks by Horner's rule with
+     * 2^k - 1 products of A and X_0 per probe, and constructed to the final threshold
+     * eps / (||A|| ||X_0||); the order, iterate count and threshold settings are then ignored.
+     * k <= 6.  Default 0: ordinary iterations. */
+    int unroll;
 } h2_invert_opts;
 
 typedef struct {

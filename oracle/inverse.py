@@ -15,6 +15,13 @@ Follows Appendix A of the paper:
   constructed (Section 3.3) from the sampler of the previous one, to a
   construction threshold eps_k chosen from the current residual
   E = ||A X_k - I||_2 (the paper's dynamic threshold; reading below).
+* Warm start and unrolled iterations (Appendix A, "Unrolling iterations"): the
+  iteration may start from a given X_0 (a previous approximate inverse), and k
+  Newton-Schulz steps may be constructed at once: X_k = X_0 prod_{j<k} (I + R_0^(2^j))
+  = X_0 sum_{i<2^k} R_0^i, R_0 = I - A X_0 (R_{j+1} = R_j^2 for Newton-Schulz), i.e.
+  the order-2^k hyperpower step.  Reading: the paper prints this as
+  X_{k-1}(2I + AX_{k-1}) and a binomial sum up to 2^k, which is not the Newton-Schulz
+  iteration; the geometric sum above is what k unrolled Newton-Schulz steps equal.
 
 Readings (the paper leaves them open): alpha = 1 / ||A||_2 with ||A||_2 from
 power iteration (the paper uses 1/||A||_inf; any alpha in (0, 2/lambda_max)
@@ -92,14 +99,21 @@ class InvertResult:
 
 
 def hns_invert(apply_A, norm_A: float, build, N: int, order: int = 2, eps: float = 1e-6,
-               eps_loose: float = 1e-6, theta: float = 0.1, max_iter: int = 50, seed: int = 9) -> InvertResult:
+               eps_loose: float = 1e-6, theta: float = 0.1, max_iter: int = 50, seed: int = 9,
+               x0=None, unroll: int = 0) -> InvertResult:
     """Hierarchical hyperpower inversion of the symmetric positive definite A (Algorithm 2).
 
-    build(op, tol) -> (H2Matrix, PeelResult) constructs an iterate from its sampler."""
+    build(op, tol) -> (H2Matrix, PeelResult) constructs an iterate from its sampler.
+    x0: optional (apply_X0, norm_X0) warm start; unroll = k >= 1: one construction of the k-th
+    Newton-Schulz iterate of X_0 (order 2^k, one iterate)."""
     res = InvertResult()
     res.alpha = 1.0 / norm_A
     apply_X = lambda v: res.alpha * v
     norm_X = res.alpha
+    if x0 is not None:
+        apply_X, norm_X = x0
+    if unroll > 0:
+        order, max_iter = 1 << unroll, 1
     for k in range(max_iter + 1):
         E = residual_norm(apply_A, apply_X, N, seed)
         res.errors.append(E)
@@ -109,7 +123,9 @@ def hns_invert(apply_A, norm_A: float, build, N: int, order: int = 2, eps: float
             Ep = res.errors[-2]
             if E > 0.9 * Ep and Ep ** order < 0.5 * E:
                 break
-        eps_k = construction_threshold(E, eps / (norm_A * norm_X), eps_loose, theta)
+        # an unrolled step is the final construction: built to the floor the target allows
+        eps_k = (eps / (norm_A * norm_X) if unroll > 0
+                 else construction_threshold(E, eps / (norm_A * norm_X), eps_loose, theta))
         h, peel_res = build(Sampler(apply_X, apply_A, order), eps_k)
         res.eps_k.append(eps_k)
         res.samples.append(int(peel_res.samples - peel_res.norm_its))

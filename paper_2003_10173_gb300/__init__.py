@@ -59,6 +59,7 @@ class InvertOpts(ctypes.Structure):
         ("order", ctypes.c_int), ("eps", ctypes.c_double), ("eps_loose", ctypes.c_double),
         ("theta", ctypes.c_double), ("max_iter", ctypes.c_int), ("shift", ctypes.c_double),
         ("res_maxit", ctypes.c_int), ("res_rtol", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("x0", ctypes.c_void_p), ("unroll", ctypes.c_int),
     ]
 
 
@@ -491,6 +492,8 @@ def invert(A: "H2", shift: float = 0.0, order: int = 2, eps: float = 1e-6, eps_l
     o.order, o.eps, o.theta, o.max_iter, o.shift = order, eps, theta, max_iter, shift
     o.eps_loose = eps if eps_loose is None else eps_loose
     for k, v in kw.items():
+        if k == "x0" and isinstance(v, H2):
+            v = v._h.value
         setattr(o, k, v)
     st = InvertStats()
     h = ctypes.c_void_p()

@@ -330,13 +330,20 @@ int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* bu
         h2_invert_opts io;
         h2_invert_opts_default(&io);
         if (opts) io = *opts;
-        require(io.order >= 2 && io.order <= 64, "h2_invert: order must be in 2..64");
+        require(io.unroll > 0 || (io.order >= 2 && io.order <= 64), "h2_invert: order must be in 2..64");
         require(io.eps > 0.0 && std::isfinite(io.eps), "h2_invert: eps must be positive");
         require(io.eps_loose >= io.eps && std::isfinite(io.eps_loose), "h2_invert: need eps_loose >= eps");
         require(io.theta > 0.0 && std::isfinite(io.theta), "h2_invert: theta must be positive");
         require(io.max_iter >= 0 && io.max_iter <= H2_MAX_INVERT_ITERS, "h2_invert: max_iter out of range");
         require(std::isfinite(io.shift), "h2_invert: shift must be finite");
         require(io.res_maxit >= 1 && io.res_rtol > 0.0, "h2_invert: bad power-iteration settings");
+        require(io.unroll >= 0 && io.unroll <= 6, "h2_invert: unroll must be in 0..6");
+        require(!io.x0 || (io.x0->N == A->N && io.x0->tree->L == A->tree->L),
+                "h2_invert: x0 must be a handle on A's tree");
+        if (io.unroll > 0) {
+            io.order = 1 << io.unroll;
+            io.max_iter = 1;
+        }
         h2_build_opts bo = checked_opts(io.eps, build_opts);
         h2_invert_stats local;
         h2_handle_s* X = nullptr;

@@ -2,7 +2,9 @@
 // order-l hyperpower iteration X_{k+1} = X_k sum_{i<l} R_k^i, R_k = I - A X_k (l = 2: Newton-
 // Schulz) is a new H^2 matrix constructed by peeling (Section 3.3) from a sampler that applies
 // the iteration to the probe block with H^2 matvecs of A and X_k (Algorithms 2 and 4).  A may
-// carry a diagonal shift (a regularised Hessian H + shift I).  X_0 = alpha I, alpha = 1/||A||_2.
+// carry a diagonal shift (a regularised Hessian H + shift I).  X_0 = alpha I, alpha = 1/||A||_2,
+// or a given iterate (warm start).  An unrolled step (k Newton-Schulz steps as one construction)
+// is the order-2^k hyperpower step: prod_{j<k} (I + R^{2^j}) = sum_{i<2^k} R^i.
 // Construction threshold of iterate k: max(eps / (||A|| ||X_k||), min(eps_loose, theta E^2)),
 // E = ||A X_k - I||_2 by power iteration on (X A - I)(A X - I), started from the counter-based
 // Gaussians of the error stream in original node order.
@@ -165,6 +167,10 @@ void invert(h2_handle_s* A, const h2_invert_opts& io, const h2_build_opts& bo, h
     }
     S.alpha = 1.0 / normA;
     double normX = S.alpha;
+    if (io.x0) {   // warm start from a given iterate (read only; never freed here)
+        S.X = io.x0;
+        normX = io.x0->stats.norm_est > 0.0 ? io.x0->stats.norm_est : S.alpha;
+    }
     // residual E = ||A X - I||_2 of the current iterate
     auto residual = [&]() {
         gaussian_vector(N, ident.p, io.seed, STREAM_ERR, v.p, s);
@@ -206,7 +212,9 @@ void invert(h2_handle_s* A, const h2_invert_opts& io, const h2_build_opts& bo, h
             if (k == io.max_iter) break;
             if (k > 0 && E > 0.9 * st->err[k - 1] && std::pow(st->err[k - 1], io.order) < 0.5 * E) break;
             const double floor = io.eps / (normA * normX);
-            const double eps_k = std::max(floor, std::min(io.eps_loose, io.theta * E * E));
+            // an unrolled step is the final construction: it is built to the floor that the target
+            // residual allows, not to a threshold derived from the current residual
+            const double eps_k = io.unroll > 0 ? floor : std::max(floor, std::min(io.eps_loose, io.theta * E * E));
             const double tb = now_s();
             auto* Xn = new h2_handle_s();
             try {

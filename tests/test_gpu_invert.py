@@ -99,3 +99,33 @@ def test_invert_argument_errors(h2, problem):
         h2.invert(problem["GA"], order=1)
     with pytest.raises(h2.H2Error):
         h2.invert(problem["GA"], eps=1e-6, eps_loose=1e-8)
+
+
+@pytest.mark.parametrize("unroll", [2, 3])
+def test_unrolled_from_warm_start_matches_oracle(h2, problem, unroll):
+    """Appendix A's unrolled iterations: from a warm start X_0 (here a rough inverse from two
+    Newton-Schulz iterates, imported on both sides), k Newton-Schulz steps constructed at once
+    (X_0 sum_{i<2^k} R_0^i).  GPU and oracle take the same X_0 and ||A||; equal products, residual
+    history to 1e-3, inverses within 1e-5, and the residual falls like E_0^(2^k) (down to the
+    construction floor)."""
+    p = problem
+    N = p["n"] ** 2
+    bopts = h2.default_opts(kmax=32, q0=16, b_inc=8, q_max=128, adaptive=1, seed=7)
+    X0, st0 = h2.invert(p["GA"], shift=p["beta"], eps=1e-6, eps_loose=1e-3, max_iter=2, build_opts=bopts)
+    assert st0["iterations"] == 2
+    X, st = h2.invert(p["GA"], shift=p["beta"], eps=1e-6, eps_loose=1e-6, build_opts=bopts, x0=X0, unroll=unroll)
+    assert st["iterations"] == 1 and len(st["samples"]) >= 1
+    hA, beta = p["hA"], p["beta"]
+    apply_A = lambda v: O.matvec(hA, v) + beta * v
+    build = lambda op, tol: O.build(op, p["coords"], p["leaf"], O.ADM_STRONG, 0.7, tol, 32, 16, 8, 128, True, 7)
+    hX0 = factors.import_to_oracle(p["hA"].tree, p["hA"].part, *X0.export())
+    res = inverse.hns_invert(apply_A, st["norm_A"], build, N, eps=1e-6, eps_loose=1e-6,
+                             x0=(lambda v: O.matvec(hX0, v), X0.stats()["norm_est"]), unroll=unroll)
+    assert len(res.samples) == 1 and st["samples"][0] == res.samples[0]
+    np.testing.assert_allclose(st["err"][:2], res.errors, rtol=1e-3)
+    np.testing.assert_allclose(st["eps_k"][0], res.eps_k[0], rtol=1e-3)
+    E0, E1 = st["err"][0], st["err"][1]
+    assert E1 <= max(10.0 * E0 ** (1 << unroll), 1e-5)
+    Xg = _dense(h2, X, N)
+    Xo = O.expand_dense(res.h2)
+    assert np.linalg.norm(Xg - Xo, 2) <= 1e-5 * np.linalg.norm(Xo, 2)

@@ -111,3 +111,53 @@ def test_hierarchical_inverse_of_regularised_heat_hessian():
     Xd = O.expand_dense(res.h2)
     Ainv = np.linalg.inv(A)
     assert np.linalg.norm(Xd - Ainv, 2) * np.linalg.norm(A, 2) <= 5e-6
+
+
+def test_unrolled_newton_schulz_equals_iterated_steps():
+    """k Newton-Schulz steps from X_0 equal one order-2^k hyperpower step from X_0 (the geometric
+    sum of the unrolled iteration), with exact constructions (dense), for k = 1..4; the paper's
+    printed binomial form sum_i binom(2^k, i) (-A X_0)^i is a different matrix (a planted check
+    that the reading matters)."""
+    rng = np.random.default_rng(3)
+    n = 40
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(np.linspace(1.0, 20.0, n)) @ Q.T
+    X0 = 0.9 / 20.0 * np.eye(n) + 0.01 * Q @ np.diag(rng.uniform(0, 1, n)) @ Q.T
+    I = np.eye(n)
+    for k in range(1, 5):
+        X = X0.copy()
+        for _ in range(k):
+            X = X @ (2 * I - A @ X)
+        samp = inverse.hyperpower_sample(lambda v: X0 @ v, lambda v: A @ v, I.copy(), 1 << k)
+        assert np.abs(samp - X).max() <= 1e-12 * np.abs(X).max()
+        R0 = I - A @ X0
+        geo = X0 @ sum(np.linalg.matrix_power(R0, i) for i in range(1 << k))
+        assert np.abs(geo - X).max() <= 1e-12 * np.abs(X).max()
+        from math import comb
+        printed = X0 @ sum(comb(1 << k, i) * np.linalg.matrix_power(-A @ X0, i) for i in range((1 << k) + 1))
+        assert np.abs(printed - X).max() > 1e-3 * np.abs(X).max()
+
+
+def test_unrolled_hierarchical_inverse_from_warm_start():
+    """The hierarchical driver with x0 and unroll: one construction, residual E_1 ~ E_0^(2^k)."""
+    n = 16
+    mask = W.sensor_mask(n * n, 40, 3)
+    op = O.HeatHessian(n, 0.01, 0.5, 0.01, mask)
+    Hd = op(np.eye(n * n))
+    shift = 0.05 * np.linalg.norm(Hd, 2)
+    A = Hd + shift * np.eye(n * n)
+    nA = float(np.linalg.norm(A, 2))
+    coords = W.grid_coords(n)
+
+    def build(sampler, tol):
+        return O.build(sampler, coords, 32, O.ADM_STRONG, 0.7, tol, 48, 32, 16, 256, True, 5)
+
+    # warm start: a rough inverse from two Newton-Schulz steps
+    rough = inverse.hns_invert(lambda v: A @ v, nA, build, n * n, eps=1e-12, max_iter=2)
+    X0 = rough.h2
+    E0 = rough.errors[-1]
+    res = inverse.hns_invert(lambda v: A @ v, nA, build, n * n, eps=1e-9, x0=(lambda v: O.matvec(X0, v), nA ** -1),
+                           unroll=3)
+    assert len(res.samples) == 1
+    assert res.errors[0] == pytest.approx(E0, rel=1e-6)
+    assert res.errors[1] <= max(10 * E0 ** 8, 1e-7)
