@@ -9,21 +9,12 @@ Section 3.2 (matvec, recompression, norms), Section 3.3 (construction from
 Hessian-vector products), with numpy library primitives (QR, SVD, matmul)
 as steps.
 """
-from .h2 import (H2Matrix, assemble, expand_dense, factor_arrays, frobenius_norm, from_factor_arrays, matvec,
-                 power_norm, storage_entries)
+from .h2 import (H2Matrix, assemble, basis_threshold, expand_dense, factor_arrays, frobenius_norm,
+                 from_factor_arrays, matvec, power_norm, storage_entries)
 from .heat import DenseOperator, HeatHessian, LowRankOperator
 from .peel import PeelResult, TreeOperator, apply_pieces, global_lowrank, norm2_estimate, peel, psd_cholesky
 from .tree import ADM_STRONG, ADM_WEAK, ClusterTree, Partition
-
-
-def basis_threshold(tol: float, norm_est: float, n_leaves: int) -> float:
-    """Absolute truncation threshold of the nested bases.
-
-    Reading (the paper fixes only the overall target): the leaf block rows partition
-    the rows, so independent per-row truncation errors add in quadrature in the
-    2-norm; the bases are truncated at 2 tol ||H|| / sqrt(#leaves), which keeps the
-    measured relative 2-norm error near 0.4 tol on the heat Hessians (n = 32..256)."""
-    return 2.0 * tol * norm_est / (n_leaves ** 0.5)
+from .update import compress_dense, far_columns, lowrank_update
 
 
 def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None,
