@@ -429,6 +429,32 @@ int h2_invert_opts_default(h2_invert_opts* opts);
 int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* build_opts, h2_handle_t* X_out,
               h2_invert_stats* stats);
 
+/* ---- low-rank update with recompression --------------------------------------- */
+
+/*
+ * A~ = A + B M B^T as a new H^2 matrix on A's tree (Section 3.2, Eqs. 3.3-3.4: a global low-rank
+ * update raises every block's rank by r; recompression then finds new nested bases by a QR
+ * downsweep of the block rows and a truncated-SVD upsweep, and projects the couplings on them).
+ * With M = I this is the paper's X Y^T for X = Y = B (the symmetric form that a Hessian keeps);
+ * M = -I removes B B^T.  Nothing is sampled: the update works on A's factors alone.
+ *   A      built or imported handle (only read; stays the caller's).
+ *   B      device, n x r, original node order, column-major with leading dimension ldb >= n;
+ *          may be NULL when r == 0 (then the call recompresses A alone).  Only read.
+ *   r      update rank, 0 <= r and r + (largest rank of A) <= 144.
+ *   M      host, r x r column-major; its symmetric part (M + M^T)/2 is used.  NULL: identity.
+ *   tol    relative target: the new bases are truncated at 2 tol ||A~||_2 / sqrt(#leaves), the
+ *          construction's basis threshold.
+ *   opts   may be NULL.  Used fields: kmax (<= 48; rank cap of the new bases), norm_est (> 0:
+ *          ||A~||_2 to use; else power iteration on products with A~ with seed, norm_maxit,
+ *          norm_rtol as in h2_build), keep_fp32, keep_bf16, stream (carries all work).
+ *   out    receives the new handle (free with h2_free); its stats give norm_est, tau_basis,
+ *          max_rank, t_total.
+ * Errors: INVALID_ARG (sizes, ranks above the limits), CUDA, OOM, NAN; H2_WARN_TOL_NOT_MET
+ * (still a valid handle) when kmax cut a truncation.
+ */
+int h2_lowrank_update(h2_handle_t A, const double* B, int64_t ldb, int r, const double* M, double tol,
+                      const h2_build_opts* opts, h2_handle_t* out);
+
 /* ---- learned rank model ------------------------------------------------------ */
 
 /*

@@ -142,6 +142,7 @@ _SIGS = {
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P, _P]),
     "h2_free": (None, [_P]),
+    "h2_lowrank_update": (_I, [_P, _P, _I64, _I, _P, _D, ctypes.POINTER(BuildOpts), ctypes.POINTER(_P)]),
     "h2_invert_opts_default": (_I, [ctypes.POINTER(InvertOpts)]),
     "h2_invert": (_I, [_P, ctypes.POINTER(InvertOpts), ctypes.POINTER(BuildOpts), ctypes.POINTER(_P),
                        ctypes.POINTER(InvertStats)]),
@@ -452,6 +453,19 @@ class H2:
         n = self.stats()["n"]
         _check(lib().h2_matvec_noalloc(self._h, _ptr(X), ldx or n, _ptr(Y), ldy or n, nrhs, mode,
                                        _stream_ptr(stream)))
+
+    def lowrank_update(self, B, r: int, tol: float, M=None, opts: BuildOpts | None = None, ldb: int | None = None):
+        """h2_lowrank_update: a new H2 for A + B M B^T, recompressed to tol.  B is a device tensor
+        (n x r in original order, column-major: a (r, n) row-major tensor or any pointer with ldb);
+        M a host r x r array (None: identity)."""
+        n = self.stats()["n"]
+        Mh = None if M is None else np.asfortranarray(np.asarray(M, dtype=np.float64).reshape(r, r))
+        h = ctypes.c_void_p()
+        st = lib().h2_lowrank_update(self._h, _ptr(B) if r else None, ldb or n, r,
+                                     Mh.ctypes.data if Mh is not None else None, tol,
+                                     ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+        _check(st, allow_warn=True)
+        return H2(h, st)
 
     STAGES = ("leaf_up", "up", "couple", "down", "leaf_near", "near")
 

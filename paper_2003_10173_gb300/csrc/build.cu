@@ -44,23 +44,6 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-struct Pinned {
-    void* p = nullptr;
-    size_t cap = 0;
-    ~Pinned() { host_free(p); }
-    template <class T>
-    T* get(size_t n) {
-        if (n * sizeof(T) > cap) {
-            host_free(p);
-            p = nullptr;
-            cap = 0;
-            p = host_alloc_bytes(n * sizeof(T) + 64);
-            cap = n * sizeof(T) + 64;
-        }
-        return static_cast<T*>(p);
-    }
-};
-
 class Builder {
   public:
     Builder(const h2_tree_s& T, h2_op_fn op, void* ctx, double tol, const h2_build_opts& o)

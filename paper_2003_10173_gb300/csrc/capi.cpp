@@ -11,6 +11,8 @@ int build_handle(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, cons
                  h2_handle_s* h);
 int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tree_t* trees, double tol,
                   const h2_build_opts& o, h2_handle_t* outs);
+int update_handle(h2_handle_s* A, const double* B, int64_t ldb, int r, const double* M, double tol,
+                  const h2_build_opts& o, h2_handle_s* h);
 h2_batch_s* batch_create(int count, const h2_handle_t* hs);
 void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
                   int64_t nrhs, int mode, cudaStream_t s);
@@ -303,6 +305,31 @@ int h2_rankmodel_set(h2_rankmodel_t m, const float* p, const float* am, const fl
         require(m != nullptr, "h2_rankmodel_set: NULL model");
         h2::rm_set(m, p, am, av, step);
         return H2_OK;
+    });
+}
+
+int h2_lowrank_update(h2_handle_t A, const double* B, int64_t ldb, int r, const double* M, double tol,
+                      const h2_build_opts* opts, h2_handle_t* out) {
+    return guard([&] {
+        require(out != nullptr, "h2_lowrank_update: out is NULL");
+        *out = nullptr;
+        require(A != nullptr, "h2_lowrank_update: NULL handle");
+        require(r >= 0 && r <= 144, "h2_lowrank_update: r must be in 0..144");
+        require(r == 0 || (B != nullptr && ldb >= A->N && ldb <= INT32_MAX), "h2_lowrank_update: bad B or ldb");
+        if (M)
+            for (int64_t i = 0; i < (int64_t)r * r; ++i)
+                require(std::isfinite(M[i]), "h2_lowrank_update: M must be finite");
+        h2_build_opts o = checked_opts(tol, opts);
+        auto* h = new h2_handle_s();
+        try {
+            h2::AllocScope scope((cudaStream_t)o.stream);
+            const int st = h2::update_handle(A, B, ldb, r, M, tol, o, h);
+            *out = h;
+            return st;
+        } catch (...) {
+            delete h;
+            throw;
+        }
     });
 }
 

@@ -125,6 +125,24 @@ struct Stager {
     void copy(void* dst, const void* src, size_t bytes, cudaStream_t s);
 };
 
+// Pinned host scratch for small synchronous reads and writes of device scalars (grown on demand).
+struct Pinned {
+    void* p = nullptr;
+    size_t cap = 0;
+    ~Pinned() { host_free(p); }
+    template <class T>
+    T* get(size_t n) {
+        if (n * sizeof(T) > cap) {
+            host_free(p);
+            p = nullptr;
+            cap = 0;
+            p = host_alloc_bytes(n * sizeof(T) + 64);
+            cap = n * sizeof(T) + 64;
+        }
+        return static_cast<T*>(p);
+    }
+};
+
 template <class T>
 void upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s, Stager& st) {
     d.reserve(h.size());
