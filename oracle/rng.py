@@ -32,6 +32,7 @@ STREAM_PROBE = 1      # range-finder probes
 STREAM_POWER = 2      # start vector of the 2-norm power iteration
 STREAM_ERR = 3        # start vector of the error power iteration
 STREAM_GLOBAL = 5     # probes of the global low-rank range finder
+STREAM_COLORED = 8    # probes of the coloured (strong-structure) range pass
 
 
 def mix64(z):
