@@ -116,7 +116,18 @@ typedef struct {
      * plain construction.  Requires 0 <= global_rank < n and, when > 0, n <= 14,155,776 (the
      * two-level tall-skinny QR of the whole matrix); ignored for a single leaf. */
     int global_rank;
+    /* Sampling structure (Section 3.3: which blocks one probe block samples at once).
+     * H2_SAMPLING_WEAK (default): the sibling blocks of every level, the paper's own choice.
+     * H2_SAMPLING_COLORED: the strong-admissibility far blocks of every level themselves; the
+     * column boxes are coloured so that no row box sees two boxes of one colour among its
+     * remaining blocks, and each colour (range pass) and each probe slot of the projection pass
+     * takes q0 probe columns; the near blocks come from identity probes on coloured leaves.  A
+     * comparison mode (it needs far more products): q0 <= 16 fixed probes (adaptive, q_level and
+     * global_rank are not used; global_rank must be 0), q0 below every box size with far blocks. */
+    int sampling;
 } h2_build_opts;
+
+enum { H2_SAMPLING_WEAK = 0, H2_SAMPLING_COLORED = 1 };
 
 /* Fill *opts with the defaults above.  Returns H2_ERR_INVALID_ARG if opts is NULL. */
 int h2_build_opts_default(h2_build_opts* opts);
@@ -428,6 +439,17 @@ int h2_invert_opts_default(h2_invert_opts* opts);
  * is still returned with H2_WARN_TOL_NOT_MET. */
 int h2_invert(h2_handle_t A, const h2_invert_opts* opts, const h2_build_opts* build_opts, h2_handle_t* X_out,
               h2_invert_stats* stats);
+
+/* ---- coloured sampling plan ------------------------------------------------------ */
+
+/* The probe counts of H2_SAMPLING_COLORED for a tree, without any product (Section 3.3: C_l, the
+ * number of probe blocks that sample all blocks of level l without interference).  counts (host,
+ * 3 (L + 1) + 1 ints): for level l, counts[3 l] = colours of the range pass, counts[3 l + 1] =
+ * probe slots of the projection pass, counts[3 l + 2] = lower far pairs sampled; counts[3 (L + 1)] =
+ * leaf colours of the near-block pass.  Level l then takes q (counts[3 l] + counts[3 l + 1])
+ * products and the leaf pass leaf_max counts[3 (L + 1)].  Errors: INVALID_ARG (NULL, q outside
+ * 1..16, q not below a box with far blocks). */
+int h2_colored_plan(h2_tree_t tree, int q, int* counts);
 
 /* ---- low-rank update with recompression --------------------------------------- */
 

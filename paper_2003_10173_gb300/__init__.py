@@ -33,6 +33,8 @@ H2_FP32 = 1
 H2_TF32 = 2
 H2_BF16 = 3
 H2_TF32X3 = 4
+H2_SAMPLING_WEAK = 0
+H2_SAMPLING_COLORED = 1
 
 H2_MAX_LEVELS = 32
 
@@ -47,7 +49,7 @@ class BuildOpts(ctypes.Structure):
         ("norm_maxit", ctypes.c_int), ("norm_rtol", ctypes.c_double), ("keep_fp32", ctypes.c_int),
         ("keep_bf16", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("q_level", ctypes.c_void_p), ("q_level_stride", ctypes.c_int), ("q_test", ctypes.c_int),
-        ("global_rank", ctypes.c_int),
+        ("global_rank", ctypes.c_int), ("sampling", ctypes.c_int),
     ]
 
 
@@ -142,6 +144,7 @@ _SIGS = {
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P, _P]),
     "h2_free": (None, [_P]),
+    "h2_colored_plan": (_I, [_P, _I, _P]),
     "h2_lowrank_update": (_I, [_P, _P, _I64, _I, _P, _D, ctypes.POINTER(BuildOpts), ctypes.POINTER(_P)]),
     "h2_invert_opts_default": (_I, [ctypes.POINTER(InvertOpts)]),
     "h2_invert": (_I, [_P, ctypes.POINTER(InvertOpts), ctypes.POINTER(BuildOpts), ctypes.POINTER(_P),
@@ -279,6 +282,15 @@ class Tree:
         out = np.empty((c.value, 2), dtype=np.int32)
         _check(lib().h2_tree_far(self._h, level, ctypes.byref(c), out.ctypes.data))
         return out
+
+    def colored_plan(self, q: int) -> dict:
+        """h2_colored_plan: per level the colours of the range pass, the probe slots of the projection
+        pass and the lower far pairs of coloured sampling with q probes per block, and the leaf colours."""
+        out = np.zeros(3 * (self.L + 1) + 1, dtype=np.int32)
+        _check(lib().h2_colored_plan(self._h, q, out.ctypes.data))
+        lv = out[:-1].reshape(self.L + 1, 3)
+        return {"colors": lv[:, 0].tolist(), "slots": lv[:, 1].tolist(), "pairs": lv[:, 2].tolist(),
+                "leaf_colors": int(out[-1])}
 
     def near(self) -> np.ndarray:
         c = _I64()

@@ -1087,8 +1087,11 @@ void Builder::run(h2_handle_s* h) {
 
 }  // namespace
 
+int build_colored(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, const h2_build_opts& o, h2_handle_s* h);
+
 int build_handle(h2_op_fn op, void* ctx, const h2_tree_s* tree, double tol, const h2_build_opts& o,
                  h2_handle_s* h) {
+    if (o.sampling == H2_SAMPLING_COLORED) return build_colored(op, ctx, tree, tol, o, h);
     h->tree = std::make_shared<h2_tree_s>(*tree);
     h->L = tree->L;
     h->N = tree->N;

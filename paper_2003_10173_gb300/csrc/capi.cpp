@@ -13,6 +13,7 @@ int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tr
                   const h2_build_opts& o, h2_handle_t* outs);
 int update_handle(h2_handle_s* A, const double* B, int64_t ldb, int r, const double* M, double tol,
                   const h2_build_opts& o, h2_handle_s* h);
+void colored_plan_counts(const h2_tree_s* tree, int q, int* out);
 h2_batch_s* batch_create(int count, const h2_handle_t* hs);
 void batch_matvec(h2_batch_s* b, const void* const* X, const int64_t* ldx, void* const* Y, const int64_t* ldy,
                   int64_t nrhs, int mode, cudaStream_t s);
@@ -91,6 +92,9 @@ h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
     require(o.q_test >= 1 && o.q_test <= 16, "h2_build: q_test must be in 1..16");
     require(o.q_level_stride >= 0, "h2_build: q_level_stride must be >= 0");
     require(o.global_rank >= 0, "h2_build: global_rank must be >= 0");
+    require(o.sampling == H2_SAMPLING_WEAK || o.sampling == H2_SAMPLING_COLORED, "h2_build: unknown sampling");
+    require(o.sampling != H2_SAMPLING_COLORED || (o.q0 <= 16 && o.global_rank == 0),
+            "h2_build: coloured sampling needs q0 <= 16 and global_rank 0");
     require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");
     require(!(o.norm_est < 0.0) && std::isfinite(o.norm_est), "h2_build: bad norm_est");
     return o;
@@ -304,6 +308,15 @@ int h2_rankmodel_set(h2_rankmodel_t m, const float* p, const float* am, const fl
     return guard([&] {
         require(m != nullptr, "h2_rankmodel_set: NULL model");
         h2::rm_set(m, p, am, av, step);
+        return H2_OK;
+    });
+}
+
+int h2_colored_plan(h2_tree_t tree, int q, int* counts) {
+    return guard([&] {
+        require(tree && counts, "h2_colored_plan: NULL argument");
+        require(q >= 1 && q <= 16, "h2_colored_plan: q must be in 1..16");
+        h2::colored_plan_counts(tree, q, counts);
         return H2_OK;
     });
 }

@@ -285,6 +285,12 @@ void fill_zero(double* p, size_t count, cudaStream_t s);
 void probe_fill(int64_t N, int ncols, int col0, const int32_t* d_perm, const int32_t* d_row_box,
                 int level_shift, uint64_t seed, int stream_id, int level, double* Om_orig,
                 double* Om_tree, cudaStream_t s);
+// Coloured probes (original order, N x q*ncolors, ld N; tree-order copy in Om_tree if not null):
+// column block c is Gaussian on the rows whose box at `level` (row_box >> level_shift) has
+// colour c in d_color (-1: no probes), zero elsewhere.
+void probe_fill_colored(int64_t N, int q, int ncolors, const int32_t* d_perm, const int32_t* d_row_box,
+                        int level_shift, const int32_t* d_color, uint64_t seed, int stream_id, int level,
+                        double* Om_orig, double* Om_tree, cudaStream_t s);
 // power-iteration start vector (tree-order Gaussian) scattered to original order
 void gaussian_vector(int64_t N, const int32_t* d_perm, uint64_t seed, int stream_id, double* x_orig,
                      cudaStream_t s);

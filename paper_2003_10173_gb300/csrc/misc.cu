@@ -39,6 +39,22 @@ __global__ void probe_fill_kernel(int64_t N, int ncols, int col0, const int32_t*
     }
 }
 
+// Coloured probes: column block c (q columns) is Gaussian on the rows whose level box has colour c.
+__global__ void probe_colored_kernel(int64_t N, int q, int ncols, const int32_t* __restrict__ perm,
+                                     const int32_t* __restrict__ row_box, int shift,
+                                     const int32_t* __restrict__ color, uint64_t key, double* __restrict__ Om,
+                                     double* __restrict__ Omt) {
+    const int64_t total = N * ncols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % N;
+        const int j = (int)(e / N);
+        const int c = color[row_box[i] >> shift];
+        const double v = (c >= 0 && j / q == c) ? gauss_at(key, (uint64_t)i, (uint64_t)j) : 0.0;
+        Om[perm[i] + (int64_t)j * N] = v;
+        if (Omt) Omt[i + (int64_t)j * N] = v;
+    }
+}
+
 __global__ void gaussian_vector_kernel(int64_t N, const int32_t* __restrict__ perm, uint64_t key,
                                        double* __restrict__ x) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
@@ -154,6 +170,16 @@ void probe_fill(int64_t N, int ncols, int col0, const int32_t* d_perm, const int
     probe_fill_kernel<<<grid_for(N * ncols), NT, 0, s>>>(N, ncols, col0, d_perm, d_row_box, level_shift,
                                                           rng_key(seed, stream_id, level), Om_orig, Om_tree);
     after_launch("probe_fill");
+}
+
+void probe_fill_colored(int64_t N, int q, int ncolors, const int32_t* d_perm, const int32_t* d_row_box,
+                        int level_shift, const int32_t* d_color, uint64_t seed, int stream_id, int level,
+                        double* Om_orig, double* Om_tree, cudaStream_t s) {
+    const int ncols = q * ncolors;
+    if (N * ncols == 0) return;
+    probe_colored_kernel<<<grid_for(N * ncols), NT, 0, s>>>(N, q, ncols, d_perm, d_row_box, level_shift, d_color,
+                                                             rng_key(seed, stream_id, level), Om_orig, Om_tree);
+    after_launch("probe_colored");
 }
 
 void gaussian_vector(int64_t N, const int32_t* d_perm, uint64_t seed, int stream_id, double* x_orig,
