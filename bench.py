@@ -466,6 +466,89 @@ def hybrid_section(h2, torch, stream) -> dict:
     return out
 
 
+def update_section(h2, torch, stream, G, N: int, build_s: float) -> dict:
+    """Low-rank update with recompression (Section 3.2, Eqs. 3.3-3.4) of the headline H^2 matrix:
+    A~ = A + B B^T with a Gaussian B (columns of the size of the Hessian's leading eigenvalues),
+    recompressed at tol 1e-6 without any sampling.  Reports the update's seconds (norm estimate
+    and recompression), the new ranks, and ||A~_H2 - (A + B B^T)||_2 / ||A + B B^T||_2 by power
+    iteration through the two handles' FP64 matvecs, against the construction's own seconds."""
+    st0 = G.stats()
+    out = {"workload": "heat 256x256 H^2 (the headline build) + B B^T, B Gaussian N x r scaled by "
+                       "sqrt(||H||/N)", "tol": 1e-6, "build_s_for_comparison": build_s, "runs": {}}
+    gen = torch.Generator("cuda").manual_seed(17)
+    for r in (8, 16):
+        B = torch.randn((r, N), dtype=torch.float64, device="cuda", generator=gen) * (st0["norm_est"] / N) ** 0.5
+        opts = h2.default_opts(kmax=48, stream=stream)
+        times = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Gu = G.lowrank_update(B, r, 1e-6, opts=opts)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            if rep < 2:
+                Gu.close()
+        st = Gu.stats()
+        v = torch.randn(N, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+        v /= v.norm()
+        w1, w2 = torch.empty_like(v), torch.empty_like(v)
+        lam, prev = 0.0, 0.0
+        for it in range(60):
+            G.matvec(v, w1, 1, h2.H2_FP64, stream=stream)
+            Gu.matvec(v, w2, 1, h2.H2_FP64, stream=stream)
+            torch.cuda.synchronize()
+            w = w1 + B.T @ (B @ v) - w2
+            lam = float(w.norm())
+            if lam == 0:
+                break
+            v = w / lam
+            if it > 0 and abs(lam - prev) <= 1e-2 * lam:
+                break
+            prev = lam
+        out["runs"][f"r{r}"] = {"update_s": float(np.median(times)), "t_norm": st["t_norm"],
+                                "t_recompress": st["t_assemble"], "max_rank_before": st0["max_rank"],
+                                "max_rank_after": st["max_rank"], "norm_est": st["norm_est"],
+                                "rel_err_2norm": lam / st["norm_est"], "tol_met": st["tol_met"]}
+        Gu.close()
+    return out
+
+
+def sampling_section(h2, torch, stream) -> dict:
+    """Sampling structure (Section 3.3: C_l probe blocks of k columns per level).  The weak structure
+    (sibling blocks, C_l = 2: range and projection pass, adaptive k) against strong-structure
+    coloured sampling (the destination far blocks, C_l = colours + projection slots, k = q0 = 16
+    fixed), on the heat Hessians at 64^2 and 128^2 (tol 1e-6, leaf 64, strong eta 0.7): products,
+    operator calls, build seconds and the 2-norm error of each; at 256^2 only the coloured plan's
+    counts (its products would exceed N)."""
+    out = {"q": 16, "runs": {}}
+    for n in (64, 128):
+        p = W.SMALL_N32["problem"]
+        gop = h2.HeatOperator(n, p.kappa, p.T, p.sigma, W.sensor_mask(n * n, p.m, p.sensor_seed))
+        tree = h2.Tree(W.grid_coords(n), 64, h2.H2_ADM_STRONG, 0.7)
+        res = {"plan": tree.colored_plan(16)}
+        for name, kw in (("weak", dict(q0=32, b_inc=16, q_max=256)),
+                         ("colored", dict(q0=16, sampling=h2.H2_SAMPLING_COLORED))):
+            opts = h2.default_opts(kmax=32, seed=7, stream=stream, **kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = h2.H2.build(gop, tree, 1e-6, opts)
+            torch.cuda.synchronize()
+            st = G.stats()
+            res[name] = {"samples": st["samples"], "op_calls": st["op_calls"], "build_s": time.perf_counter() - t0,
+                         "t_op": st["t_op"], "range_probes": st["range_probes"][:st["levels"] + 1],
+                         "proj_probes": st["proj_probes"][:st["levels"] + 1], "max_rank": st["max_rank"][:st["levels"] + 1],
+                         "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, n * n, st["norm_est"], stream)}
+            G.close()
+        res["products_ratio_colored_over_weak"] = res["colored"]["samples"] / res["weak"]["samples"]
+        out["runs"][f"heat{n}"] = res
+        del gop, tree
+        torch.cuda.empty_cache()
+    t256 = h2.Tree(W.grid_coords(256), 64, h2.H2_ADM_STRONG, 0.7)
+    pl = t256.colored_plan(16)
+    out["plan_256"] = dict(pl, products=16 * (sum(pl["colors"]) + sum(pl["slots"])) + 64 * pl["leaf_colors"])
+    return out
+
+
 def advdiff_section(h2, torch, stream) -> dict:
     """Second Hessian family (Section 4.3's study on a finite-difference stand-in): source
     inversion in stationary advection-diffusion on a 128 x 128 grid, v = (x, y), c = 0.5,
@@ -754,6 +837,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-inversion", action="store_true")
     ap.add_argument("--no-hybrid", action="store_true")
+    ap.add_argument("--no-update", action="store_true")
+    ap.add_argument("--no-sampling", action="store_true")
     ap.add_argument("--no-advdiff", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
@@ -846,6 +931,7 @@ def main():
     torch.cuda.synchronize()
     launches = h2.launch_count() - launches0
     gemm_ms, gemm_flops, gemm_n, gemm_bytes = h2.gemm_profile_read()
+    stack_prof = [h2.stack_profile_read(w) for w in (0, 1)]
     h2.gemm_profile(False)
     clk = clocks.stop()
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist)
@@ -894,6 +980,14 @@ def main():
                            "algorithmic_bytes_per_launch": gemm_bytes / max(gemm_n, 1),
                            "traffic_note": "per-launch DRAM bytes vary with the problem list; sampled launches "
                                            "in profiles/gemm_tiles_n128_n256.md"}
+    # the recompression's stacked Householder QR and truncated SVD (FP64-pipe bound), timed per
+    # launch with events over the timed steps; flops are those of their QR factorisations only
+    roofline_build_stacked = {}
+    for name, (ms, fl, n) in zip(("stacked_r_kernel", "stacked_svd_kernel"), stack_prof):
+        tf = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+        roofline_build_stacked[name] = {"bound": "alu", "achieved": tf, "peak": fp64_meas, "unit": "TFLOP/s",
+                                        "frac": (tf / fp64_meas) if tf else None, "launches": n,
+                                        "ms_per_step": ms / args.steps, "qr_flops_per_step": fl / args.steps}
     # FP64 near field at nrhs = 1 (the atomic scatter kernel), outside the timed region
     Gp = results[-1][0]
     Gp.profile(True)
@@ -970,6 +1064,14 @@ def main():
     if rank == 0 and not args.no_advdiff:
         advdiff = advdiff_section(h2, torch, stream)
 
+    sampling = None
+    if rank == 0 and not args.no_sampling:
+        sampling = sampling_section(h2, torch, stream)
+
+    update = None
+    if rank == 0 and not args.no_update:
+        update = update_section(h2, torch, stream, Gp2, N, float(np.mean(build_ms)) / 1e3)
+
     inversion = None
     if rank == 0 and not args.no_inversion:
         inversion = inversion_section(h2, torch, stream)
@@ -989,6 +1091,7 @@ def main():
             "stored_bytes_fp64": (st["entries_D"] + st["entries_S"] + st["entries_U"] + st["entries_E"]) * 8,
             "hbm_view": hbm_view,
             "roofline": roofline, "roofline_build_gemm": roofline_build_gemm,
+            "roofline_build_stacked": roofline_build_stacked,
             "roofline_matvec_nrhs1": roofline_matvec_nrhs1,
             "stage_ms_nrhs1": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
             "build_phase_s": {k: st[k] for k in ("t_norm", "t_op", "t_peel", "t_assemble")},
@@ -1006,6 +1109,10 @@ def main():
             line["advdiff"] = advdiff
         if inversion is not None:
             line["inversion"] = inversion
+        if update is not None:
+            line["lowrank_update"] = update
+        if sampling is not None:
+            line["sampling_structure"] = sampling
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

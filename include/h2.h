@@ -345,6 +345,13 @@ int h2_profile_read(h2_handle_t h, double* ms_out, int64_t* launches_out);
 int h2_gemm_profile(int enable);
 int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_out, double* bytes_out);
 
+/* Timing of the recompression's stacked Householder QR (which = 0) and truncated-SVD (which = 1)
+ * launches, switched on and off with h2_gemm_profile: device milliseconds, algorithmic flops of
+ * their QR factorisations (2 m n^2 - 2 n^3 / 3 per m x n stack with m >= n; the SVD adds 4 c^3 / 3
+ * for the pivoted QR of its c x c triangle and does not count its Jacobi rotations) and launches
+ * since the last read; reading resets them.  Any pointer may be NULL. */
+int h2_stack_profile_read(int which, double* ms, double* flops, int64_t* launches);
+
 /* Synchronise the device and report whether a kernel of handle h recorded a failed bounded
  * wait (H2_ERR_DEVICE_CHECK) since h was created; H2_OK otherwise. */
 int h2_device_status(h2_handle_t h);

@@ -143,6 +143,7 @@ _SIGS = {
     "h2_profile_read": (_I, [_P, _P, _P]),
     "h2_gemm_profile": (_I, [_I]),
     "h2_gemm_profile_read": (_I, [_P, _P, _P, _P]),
+    "h2_stack_profile_read": (_I, [_I, _P, _P, _P]),
     "h2_free": (None, [_P]),
     "h2_colored_plan": (_I, [_P, _I, _P]),
     "h2_lowrank_update": (_I, [_P, _P, _I64, _I, _P, _D, ctypes.POINTER(BuildOpts), ctypes.POINTER(_P)]),
@@ -538,6 +539,14 @@ def gemm_profile_read():
     ms, fl, n, by = _D(), _D(), _I64(), _D()
     _check(lib().h2_gemm_profile_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n), ctypes.byref(by)))
     return ms.value, fl.value, n.value, by.value
+
+
+def stack_profile_read(which: int):
+    """(milliseconds, algorithmic QR flops, launches) of the stacked QR (0) or truncated-SVD (1) launches
+    since the last read (recorded while gemm_profile is on)."""
+    ms, fl, n = _D(), _D(), _I64()
+    _check(lib().h2_stack_profile_read(which, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+    return ms.value, fl.value, n.value
 
 
 def build_batched(ops, trees, tol: float, opts: BuildOpts | None = None):

@@ -679,6 +679,14 @@ int h2_gemm_profile_read(double* ms_out, double* flops_out, int64_t* launches_ou
     });
 }
 
+int h2_stack_profile_read(int which, double* ms_out, double* flops_out, int64_t* launches_out) {
+    return guard([&] {
+        require(which == 0 || which == 1, "h2_stack_profile_read: which must be 0 or 1");
+        h2::stack_profile_read(which, ms_out, flops_out, launches_out);
+        return H2_OK;
+    });
+}
+
 int h2_device_status(h2_handle_t h) {
     return guard([&] {
         require(h != nullptr, "h2_device_status: NULL handle");

@@ -189,6 +189,12 @@ class GemmBatch {
 
 void gemm_profile_enable(int on);
 void gemm_profile_read(double* ms, double* flops, int64_t* launches, double* bytes);
+int gemm_profile_on();
+// The same switch times the stacked QR (which 0) and truncated-SVD (which 1) launches: device
+// milliseconds, algorithmic flops of their Householder QRs (2 m n^2 - 2 n^3 / 3 for an m x n stack,
+// m >= n; plus 4 c^3 / 3 for the pivoted QR of the SVD's triangle; the Jacobi rotations are not
+// counted) and launches since the last read.
+void stack_profile_read(int which, double* ms, double* flops, int64_t* launches);
 
 // ---- dense linear-algebra kernels (la.cu) ----------------------------------
 // Householder QR of panels in place with explicit orthonormal factor written to Q.

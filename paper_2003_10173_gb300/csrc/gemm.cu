@@ -186,6 +186,8 @@ GemmProfile g_prof;
 
 void gemm_profile_enable(int on) { g_prof.on = on; }
 
+int gemm_profile_on() { return g_prof.on; }
+
 void gemm_profile_read(double* ms, double* flops, int64_t* launches, double* bytes) {
     H2_CUDA(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lock(g_prof.mu);

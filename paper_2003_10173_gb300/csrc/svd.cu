@@ -34,9 +34,10 @@ namespace {
 
 constexpr int SQ_NT = 256;
 constexpr int SQ_NW = SQ_NT / 32;
+constexpr int QR_NT = 256;         // threads of the stacked QR kernel
+constexpr int QR_NW = QR_NT / 32;
 constexpr int SVD_MAXC = 96;
 constexpr int kSplitRows = 4096;   // a single matrix taller than this is split over several CTAs
-constexpr int kPartRows = 1024;    // rows per CTA of a split matrix
 constexpr size_t kSmemCap = 200 * 1024;
 
 constexpr int kSmemMaxC = 144;     // widest matrix of stacked_r (its working matrix in shared memory)
@@ -50,59 +51,21 @@ constexpr int kSvdChunk = 64;
 __host__ __device__ inline int work_ld(int c, int ch) { return (c + ch) | 1; }
 __host__ __device__ inline int work_ld(int c) { return work_ld(c, chunk_rows(c)); }
 
-// Householder reflector of column j of the stacked [R; chunk] (rows c .. c+ch-1 hold the
-// chunk), computed by one warp: zeroes the chunk part of column j against R[j, j].
-__device__ inline void reflector(double* A, int lda, int c, int ch, int j, double* tau, int lane) {
-    double x2 = 0.0;
-    for (int i = lane; i < ch; i += 32) {
-        const double y = A[c + i + (int64_t)j * lda];
-        x2 = fma(y, y, x2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-    const double alpha = A[j + (int64_t)j * lda];
-    double tj = 0.0, scale = 0.0, beta = alpha;
-    if (x2 > 0.0) {
-        beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
-        tj = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-    }
-    if (tj != 0.0)
-        for (int i = lane; i < ch; i += 32) A[c + i + (int64_t)j * lda] *= scale;
-    __syncwarp();
-    if (lane == 0) {
-        tau[j] = tj;
-        A[j + (int64_t)j * lda] = beta;
-    }
-    __syncwarp();
-}
-
-// Apply reflector j (v = [1 at row j; chunk rows of column j]) to column k of [R; chunk].
-__device__ inline void apply_reflector(double* A, int lda, int c, int ch, int j, int k, double tj, int lane) {
-    double w = 0.0;
-    for (int i = lane; i < ch; i += 32) w = fma(A[c + i + (int64_t)j * lda], A[c + i + (int64_t)k * lda], w);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    w += A[j + (int64_t)k * lda];
-    const double f = tj * w;
-    for (int i = lane; i < ch; i += 32)
-        A[c + i + (int64_t)k * lda] = fma(-f, A[c + i + (int64_t)j * lda], A[c + i + (int64_t)k * lda]);
-    __syncwarp();
-    if (lane == 0) A[j + (int64_t)k * lda] -= f;
-    __syncwarp();
-}
-
 // R factor (upper c x c, rows 0..c-1 of A) of the stacked row blocks segs[b..e).  The
 // segments' rows are packed into chunks of up to chunk_rows(c) rows (a chunk may span
 // segments), so that short segments cost only their own rows.  Entry state of A is
 // irrelevant; every thread returns after a barrier with R complete.
+template <int NT>
 __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __restrict__ segs, int b, int e,
                            double* tau) {
     __shared__ const double* rp[128];
     __shared__ int rld[128];
     __shared__ int hs;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int x = threadIdx.x; x < c * c; x += SQ_NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
+    __shared__ double part[NT];      // slice partial sums of the dot products
+    __shared__ double fk[kSmemMaxC];    // tau_j sc_j w_k of every trailing column
+    __shared__ double nrm[(NT / 32)];       // slice partial squared norms of y_{j+1}
+    __shared__ double refl[2];          // sc_j and beta_j
+    for (int x = threadIdx.x; x < c * c; x += NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
     int sgi = b, off = 0;   // next row: segment sgi, row off (the same in every thread)
     while (true) {
         __syncthreads();
@@ -135,21 +98,86 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
                 off += take;
             }
         }
-        for (int x = threadIdx.x; x < h * c; x += SQ_NT) {
+        for (int x = threadIdx.x; x < h * c; x += NT) {
             const int i = x % h, k = x / h;
             A[c + i + (int64_t)k * lda] = rp[i][(int64_t)k * rld[i]];
         }
         __syncthreads();
-        if (warp == 0) reflector(A, lda, c, h, 0, tau, lane);
+        // Column-by-column elimination of the chunk under R.  Reflector j is v = [e_j; sc_j y_j]
+        // (y_j: the chunk part of column j, left unscaled), so for every column k > j
+        //   w = R[j, k] + sc_j (y_j . y_k),  R[j, k] -= tau_j w,  y_k -= tau_j sc_j w y_j.
+        // Thread t works on column k = j + 1 + t % nk over the row slice t / nk (no warp
+        // reductions: the FP64 pipe is the bound), slice partial sums meet in shared memory.
+        // The squared norm of y_{j+1}, needed for reflector j + 1, is accumulated while y_{j+1}
+        // is updated.
+        if (threadIdx.x < (NT / 32)) {   // ||y_0||^2 in (NT / 32) row slices
+            const int rs0 = (h + (NT / 32) - 1) / (NT / 32);
+            double x2 = 0.0;
+            for (int r = threadIdx.x * rs0; r < min(h, (threadIdx.x + 1) * rs0); ++r) x2 = fma(A[c + r], A[c + r], x2);
+            nrm[threadIdx.x] = x2;
+        }
         __syncthreads();
         for (int j = 0; j < c; ++j) {
-            const double tj = tau[j];
-            // columns k > j, owned by warp k % SQ_NW; the owner of j + 1 forms its reflector
-            // right after updating it, so one barrier per column suffices
-            int k = j + 1 + ((warp - (j + 1)) % SQ_NW + SQ_NW) % SQ_NW;
-            for (; k < c; k += SQ_NW) {
-                if (tj != 0.0) apply_reflector(A, lda, c, h, j, k, tj, lane);
-                if (k == j + 1) reflector(A, lda, c, h, k, tau, lane);
+            const int nk = c - j - 1;
+            const int ns = nk > 0 ? min((NT / 32), NT / nk) : 0;
+            const int rs = ns > 0 ? (h + ns - 1) / ns : 0;
+            const int t = threadIdx.x;
+            const bool act = t < nk * ns;
+            const int k = act ? j + 1 + t % nk : 0;
+            const int sl = act ? t / nk : 0;
+            const int r0 = sl * rs, r1 = min(h, r0 + rs);
+            const double* yj = A + c + (int64_t)j * lda;
+            double* yk = A + c + (int64_t)k * lda;
+            if (t == 0) {   // reflector j from ||y_j||^2 and R[j, j]
+                double x2 = 0.0;
+                for (int q = 0; q < (NT / 32); ++q) x2 += nrm[q];
+                const double alpha = A[j + (int64_t)j * lda];
+                double tj = 0.0, scj = 0.0, beta = alpha;
+                if (x2 > 0.0) {
+                    beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
+                    tj = (beta - alpha) / beta;
+                    scj = 1.0 / (alpha - beta);
+                }
+                tau[j] = tj;
+                refl[0] = scj;
+                refl[1] = beta;
+            }
+            if (act) {
+                double d = 0.0;
+                for (int r = r0; r < r1; ++r) d = fma(yj[r], yk[r], d);
+                part[t] = d;
+            }
+            __syncthreads();
+            const double tj = tau[j], scj = refl[0];
+            if (t == 0) A[j + (int64_t)j * lda] = refl[1];
+            if (t < nk) {
+                const int kk = j + 1 + t;
+                double w = 0.0;
+                for (int q = 0; q < ns; ++q) w += part[t + q * nk];
+                w = fma(scj, w, A[j + (int64_t)kk * lda]);
+                const double f = tj * w;
+                A[j + (int64_t)kk * lda] -= f;
+                fk[t] = f * scj;
+            }
+            if (t < (NT / 32)) nrm[t] = 0.0;
+            __syncthreads();
+            if (act && tj != 0.0) {
+                const double g = fk[k - j - 1];
+                if (k == j + 1) {
+                    double x2 = 0.0;
+                    for (int r = r0; r < r1; ++r) {
+                        const double y = fma(-g, yj[r], yk[r]);
+                        yk[r] = y;
+                        x2 = fma(y, y, x2);
+                    }
+                    nrm[sl] = x2;
+                } else {
+                    for (int r = r0; r < r1; ++r) yk[r] = fma(-g, yj[r], yk[r]);
+                }
+            } else if (act && k == j + 1) {
+                double x2 = 0.0;
+                for (int r = r0; r < r1; ++r) x2 = fma(yk[r], yk[r], x2);
+                nrm[sl] = x2;
             }
             __syncthreads();
         }
@@ -251,7 +279,7 @@ __device__ void pivoted_qr(double* A, int lda, int c, int* perm, double* cn, dou
 // compacted: the min(c, rows) rows of largest norm are written first (R^T R, the only use of
 // R, does not depend on the order of its rows) and the remaining rows -- zero in exact
 // arithmetic -- are written as zeros.
-__global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(QR_NT) stacked_r_kernel(const StackJob* __restrict__ jobs, int njobs,
                                                           const RowSeg* __restrict__ segs) {
     extern __shared__ double smem[];
     __shared__ double tau[kSmemMaxC];
@@ -264,11 +292,11 @@ __global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __rest
         if (c <= 0) continue;
         const int lda = work_ld(c);
         double* A = smem;
-        stacked_qr(A, lda, c, chunk_rows(c), segs, jb.seg_begin, jb.seg_end, tau);
+        stacked_qr<QR_NT>(A, lda, c, chunk_rows(c), segs, jb.seg_begin, jb.seg_end, tau);
         int rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs[i].rows;
         const int reff = min(c, rows);
-        for (int j = warp; j < c; j += SQ_NW) {   // squared norms of the rows of R
+        for (int j = warp; j < c; j += QR_NW) {   // squared norms of the rows of R
             double x = 0.0;
             for (int k = j + lane; k < c; k += 32) {
                 const double a = A[j + (int64_t)k * lda];
@@ -279,7 +307,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __rest
             if (lane == 0) rn[j] = x;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < c; j += SQ_NT) {   // rank by descending norm (ties by index)
+        for (int j = threadIdx.x; j < c; j += QR_NT) {   // rank by descending norm (ties by index)
             const double x = rn[j];
             int r = 0;
             for (int i = 0; i < c; ++i) {
@@ -289,7 +317,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_r_kernel(const StackJob* __rest
             if (r < reff) src[r] = j;
         }
         __syncthreads();
-        for (int x = threadIdx.x; x < c * c; x += SQ_NT) {
+        for (int x = threadIdx.x; x < c * c; x += QR_NT) {
             const int r = x % c, k = x / c;
             jb.out[r + (int64_t)k * jb.ldo] = (r < reff) ? A[src[r] + (int64_t)k * lda] : 0.0;
         }
@@ -317,7 +345,7 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
     const int ldb = c | 1;
     double* A = smem;                         // lda x c: [R; chunk]
     double* B = smem + (int64_t)lda * c;      // ldb x np: R^T and a zero padding column
-    stacked_qr(A, lda, c, kSvdChunk, segs, jb.seg_begin, jb.seg_end, tau);
+    stacked_qr<SQ_NT>(A, lda, c, kSvdChunk, segs, jb.seg_begin, jb.seg_end, tau);
     // W^T = Q1 R1 and R1 P = Q3 R3 give W = P R3^T (Q1 Q3)^T: the left singular vectors of W
     // are those of R3^T with their rows permuted by P
     pivoted_qr(A, lda, c, perm, sig, tau);
@@ -457,35 +485,124 @@ size_t svd_smem_bytes(int c) {   // increasing in c
 
 }  // namespace
 
+namespace {
+
+// Event timing of the stacked launches (enabled with the GEMM profile).
+struct StackProfile {
+    std::mutex mu;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used;
+    std::vector<cudaEvent_t> pool;
+    double ms = 0.0, flops = 0.0;
+    int64_t launches = 0;
+    cudaEvent_t take() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            H2_CUDA(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+};
+StackProfile g_sprof[2];
+
+double qr_flops(double m, double n) {
+    return m >= n ? 2.0 * m * n * n - 2.0 * n * n * n / 3.0 : 2.0 * n * m * m - 2.0 * m * m * m / 3.0;
+}
+
+double job_rows(const StackJob& j, const std::vector<RowSeg>& segs) {
+    double r = 0.0;
+    for (int i = j.seg_begin; i < j.seg_end; ++i) r += segs[i].rows;
+    return r;
+}
+
+// Records the start event of a profiled launch; returns it (null when profiling is off).
+cudaEvent_t prof_begin(int which, double flops, cudaStream_t s) {
+    if (!gemm_profile_on()) return nullptr;
+    StackProfile& P = g_sprof[which];
+    std::lock_guard<std::mutex> lock(P.mu);
+    cudaEvent_t e = P.take();
+    H2_CUDA(cudaEventRecord(e, s));
+    P.flops += flops;
+    P.launches += 1;
+    return e;
+}
+
+void prof_end(int which, cudaEvent_t ea, cudaStream_t s) {
+    if (!ea) return;
+    StackProfile& P = g_sprof[which];
+    std::lock_guard<std::mutex> lock(P.mu);
+    cudaEvent_t eb = P.take();
+    H2_CUDA(cudaEventRecord(eb, s));
+    P.used.push_back({ea, eb});
+}
+
+}  // namespace
+
+void stack_profile_read(int which, double* ms, double* flops, int64_t* launches) {
+    H2_CUDA(cudaDeviceSynchronize());
+    StackProfile& P = g_sprof[which & 1];
+    std::lock_guard<std::mutex> lock(P.mu);
+    for (auto& u : P.used) {
+        float t = 0.f;
+        H2_CUDA(cudaEventElapsedTime(&t, u.first, u.second));
+        P.ms += t;
+        P.pool.push_back(u.first);
+        P.pool.push_back(u.second);
+    }
+    P.used.clear();
+    if (ms) *ms = P.ms;
+    if (flops) *flops = P.flops;
+    if (launches) *launches = P.launches;
+    P.ms = 0.0;
+    P.flops = 0.0;
+    P.launches = 0;
+}
+
 void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& segs_in, StackWork& w,
                cudaStream_t s) {
     if (jobs_in.empty()) return;
-    // A single matrix taller than kSplitRows is split over several CTAs (part jobs of at most
-    // kPartRows rows each, c x c R factors in w.parts); its final job stacks the part factors.
+    // A tall matrix is split over several CTAs (part jobs of about `target` rows, c x c R factors
+    // in w.parts); its final job stacks the part factors.  The target spreads the launch's rows
+    // over a few CTAs per SM, within [256, kSplitRows] rows.
     std::vector<StackJob> jobs, parts;
     std::vector<RowSeg> segs, psegs;
     struct Split { size_t job; size_t first_part; int count; };
     std::vector<Split> splits;
+    int64_t total = 0;
+    for (const StackJob& jb : jobs_in)
+        for (int i = jb.seg_begin; i < jb.seg_end; ++i) total += segs_in[i].rows;
+    const int target = (int)std::min<int64_t>(kSplitRows, std::max<int64_t>(128, total / (4 * 152)));
     for (const StackJob& jb : jobs_in) {
         if (jb.c <= 0) continue;
         if (jb.c > kSmemMaxC) fail(H2_ERR_INVALID_ARG, "stacked_r: more than 144 columns");
         int64_t rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs_in[i].rows;
         StackJob j = jb;
-        if (rows <= kSplitRows) {
+        if (rows <= 2 * (int64_t)std::max(target, jb.c)) {
             j.seg_begin = (int)segs.size();
             for (int i = jb.seg_begin; i < jb.seg_end; ++i) segs.push_back(segs_in[i]);
             j.seg_end = (int)segs.size();
             jobs.push_back(j);
             continue;
         }
+        const int prows = std::max(target, jb.c);
         Split sp{jobs.size(), parts.size(), 0};
+        int filled = prows;   // rows in the current part (start a new part first)
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) {
             const RowSeg sg = segs_in[i];
-            for (int r0 = 0; r0 < sg.rows; r0 += kPartRows) {
-                psegs.push_back(RowSeg{sg.p + r0, std::min(kPartRows, sg.rows - r0), sg.ld});
-                parts.push_back(StackJob{(int)psegs.size() - 1, (int)psegs.size(), jb.c, nullptr, jb.c, nullptr, nullptr});
-                ++sp.count;
+            for (int r0 = 0; r0 < sg.rows;) {
+                if (filled >= prows) {
+                    parts.push_back(StackJob{(int)psegs.size(), (int)psegs.size(), jb.c, nullptr, jb.c, nullptr, nullptr});
+                    ++sp.count;
+                    filled = 0;
+                }
+                const int take = std::min(prows - filled, sg.rows - r0);
+                psegs.push_back(RowSeg{sg.p + r0, take, sg.ld});
+                parts.back().seg_end = (int)psegs.size();
+                filled += take;
+                r0 += take;
             }
         }
         splits.push_back(sp);
@@ -495,17 +612,35 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     });
-    // one launch; the working matrix's size is not monotone in c (the chunk height steps down at
-    // 49, 97 and 129 columns), so the launch takes the largest requirement of its jobs
-    auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
-                      DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
+    // one launch per class of c (<= 48, 64, 96, 128, 144), so that narrow jobs are not held to the
+    // shared-memory occupancy of the widest; the working matrix's size is not monotone in c (the
+    // chunk height steps down at 49, 97 and 129 columns), so a launch takes the largest
+    // requirement of its jobs
+    auto launch1 = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
+                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
         if (js.empty()) return;
         size_t dyn = 16;
         for (auto& j : js) dyn = std::max(dyn, qr_smem_bytes(j.c));
         upload(dj, js, s, stj);
         upload(dsg, ss, s, sts);
-        stacked_r_kernel<<<(unsigned)js.size(), SQ_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p);
+        double fl = 0.0;
+        if (gemm_profile_on())
+            for (auto& j : js) fl += qr_flops(job_rows(j, ss), j.c);
+        cudaEvent_t ev = prof_begin(0, fl, s);
+        stacked_r_kernel<<<(unsigned)js.size(), QR_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p);
         after_launch("stacked_r");
+        prof_end(0, ev, s);
+    };
+    auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
+                      DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
+        constexpr int kBounds[] = {48, 64, 96, 128, kSmemMaxC};
+        std::vector<StackJob> cls[5];
+        for (const StackJob& j : js) {
+            int b = 0;
+            while (j.c > kBounds[b]) ++b;
+            cls[b].push_back(j);
+        }
+        for (auto& v : cls) launch1(v, ss, dj, dsg, stj, sts);
     };
     if (!parts.empty()) {
         int64_t elems = 0;
@@ -522,7 +657,7 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
             fj.seg_begin = (int)segs.size();
             for (int i = 0; i < sp.count; ++i) {
                 const StackJob& pj = parts[sp.first_part + i];
-                const int prow = psegs[pj.seg_begin].rows;
+                const int prow = (int)job_rows(pj, psegs);
                 segs.push_back(RowSeg{pj.out, std::min(prow, pj.c), pj.c});
             }
             fj.seg_end = (int)segs.size();
@@ -544,9 +679,14 @@ void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowS
         H2_CUDA(cudaFuncSetAttribute(stacked_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)svd_smem_bytes(SVD_MAXC)));
     });
+    double fl = 0.0;
+    if (gemm_profile_on())
+        for (auto& j : jobs) fl += qr_flops(job_rows(j, segs), j.c) + 4.0 * j.c * (double)j.c * j.c / 3.0;
+    cudaEvent_t ev = prof_begin(1, fl, s);
     stacked_svd_kernel<<<(unsigned)jobs.size(), SQ_NT, svd_smem_bytes(std::max(cm, 1)), s>>>(
         w.d_jobs.p, w.d_segs.p, thr, kmax, d_cap_flag);
     after_launch("stacked_svd");
+    prof_end(1, ev, s);
 }
 
 int svd_max_order() { return SVD_MAXC; }
