@@ -37,10 +37,11 @@ import workloads as W  # noqa: E402
 
 METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
 CFG = W.MEDIUM_N256
-# DRAM bytes (read + write) of one launch of the roofline's kernel (mv_leaf_near_kernel, FP64,
-# nrhs 256, 256 x 256 workload) from an ncu capture of that launch (profiles/); None until it
-# is captured, and reset to None whenever the kernel changes
-MATVEC_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) of one mv_leaf_near_kernel launch at nrhs = 256, from an ncu capture of
+# the same kernel on the 128 x 128 member of the bench family (profiles/ names the command), with
+# the algorithmic bytes of that launch; the full-size traffic is scaled by the algorithmic bytes
+# (near-block entries and right-hand-side rows both grow with N).  Recapture after changing the kernel.
+MATVEC_TRAFFIC_SMALL = {"dram_bytes": 692778240 + 38321664, "algorithmic_bytes": 1.610e8, "grid": "128x128"}
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (GB300 nominal 1.25 TFLOP/s)
@@ -357,9 +358,10 @@ def rel_err_2norm(h2, torch, gop, G, N: int, norm_est: float, stream) -> float:
 
 def learned_ranks_section(h2, torch, stream) -> dict:
     """Rank model trained on adaptive builds of 500 heat Hessians at 128 x 128 (kappa ~ U[0.002,
-    0.05], 5-20 % sensors; fine probing q0 16, b_inc 8), then the 256 x 256 and 512 x 512
-    Hessians built from the predicted per-level start counts (pad 8, first test 8 columns)
-    against plain adaptive peeling (q0 32, b_inc 16), each at tol 1e-6."""
+    0.05], 5-20 % sensors; fine probing q0 16, b_inc 8), then the 256 x 256 and 512 x 512 bench
+    Hessians and held-out sets (32 Hessians at 256 x 256, 8 at 512 x 512, parameters and sensor
+    sets drawn afresh) built from the predicted per-level start counts (pad 8, first test 8
+    columns) against plain adaptive peeling (q0 32, b_inc 16), each at tol 1e-6."""
     b = CFG["build"]
     probs = W.batch_problems(500, seed=2025, n_lo=128, n_hi=128)
     fine = h2.default_opts(kmax=b.kmax, q0=16, b_inc=8, q_max=b.q_max, adaptive=1, seed=b.seed)
@@ -421,6 +423,46 @@ def learned_ranks_section(h2, torch, stream) -> dict:
         res["build_speedup"] = res["adaptive"]["build_s"] / res["learned"]["build_s"]
         out["eval"][cfg["name"]] = res
         del gop, tree
+        torch.cuda.empty_cache()
+    # held-out Hessians of the family (kappa, sensor fraction and sensor sets never trained on):
+    # 32 at 256 x 256 and 8 at 512 x 512, each built plain and from the predicted starts
+    out["held_out"] = {}
+    for n, count, seed, cfg in ((256, 32, 7001, W.MEDIUM_N256), (512, 8, 7002, W.LARGE_N512)):
+        bb = cfg["build"]
+        base = dict(kmax=bb.kmax, q0=bb.q0, b_inc=bb.b_inc, q_max=bb.q_max, adaptive=1, seed=bb.seed, stream=stream)
+        rows = []
+        for i, q in enumerate(W.batch_problems(count, seed=seed, n_lo=n, n_hi=n)):
+            q = dataclasses.replace(q, sensor_seed=90000 + 100 * n + i)
+            gop = h2.HeatOperator(q.n, q.kappa, q.T, q.sigma, W.sensor_mask(q.N, q.m, q.sensor_seed))
+            tree = h2.Tree(W.grid_coords(q.n), bb.leaf, bb.adm, bb.eta)
+            ql, _ = model.q_levels(tree, q.kappa * q.T, q.m / q.N, bb.tol, pad=8, q_max=bb.q_max)
+            row = {"kappa": q.kappa, "sensor_fraction": q.m / q.N}
+            for key, opts in (("adaptive", h2.default_opts(**base)),
+                              ("learned", h2.default_opts(**base, q_level=ql, q_test=8))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                G = h2.H2.build(gop, tree, bb.tol, opts)
+                torch.cuda.synchronize()
+                bt = time.perf_counter() - t0
+                st = G.stats()
+                row[key] = {"op_calls": st["op_calls"], "samples": st["samples"], "build_s": bt,
+                            "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, q.N, st["norm_est"], stream)}
+                G.close()
+            rows.append(row)
+            del gop, tree
+        def saved(k):
+            return [1.0 - r["learned"][k] / r["adaptive"][k] for r in rows]
+        sp = [r["adaptive"]["build_s"] / r["learned"]["build_s"] for r in rows]
+        out["held_out"][f"heat{n}"] = {
+            "hessians": count, "seed": seed,
+            "op_calls_saved_mean": float(np.mean(saved("op_calls"))), "op_calls_saved_min": float(np.min(saved("op_calls"))),
+            "samples_saved_mean": float(np.mean(saved("samples"))), "samples_saved_min": float(np.min(saved("samples"))),
+            "build_speedup_mean": float(np.mean(sp)), "build_speedup_min": float(np.min(sp)),
+            "rel_err_max_adaptive": float(max(r["adaptive"]["rel_err_2norm"] for r in rows)),
+            "rel_err_max_learned": float(max(r["learned"]["rel_err_2norm"] for r in rows)),
+            "within_1e-6_learned": int(sum(r["learned"]["rel_err_2norm"] <= 1e-6 for r in rows)),
+            "within_1e-6_adaptive": int(sum(r["adaptive"]["rel_err_2norm"] <= 1e-6 for r in rows)),
+            "per_hessian": rows}
         torch.cuda.empty_cache()
     model.close()
     return out
@@ -959,15 +1001,20 @@ def main():
     ln_ms = float(np.mean(stage_ms["leaf_near"]))
     ln_flops = near_flops(st, sizes, nr_roof) + 2.0 * nr_roof * st["entries_U"]
     ln_tf = ln_flops / (ln_ms / 1e3) / 1e12
+    ln_alg_bytes = st["entries_D"] * 8 + 2 * N * nr_roof * 8
     roofline = {"bound": "alu", "achieved": ln_tf, "peak": fp64_meas, "unit": "TFLOP/s",
-                "frac": ln_tf / fp64_meas, "traffic": MATVEC_TRAFFIC_PER_LAUNCH,
+                "frac": ln_tf / fp64_meas,
+                "traffic": MATVEC_TRAFFIC_SMALL["dram_bytes"] * ln_alg_bytes / MATVEC_TRAFFIC_SMALL["algorithmic_bytes"],
                 "kernel": f"mv_leaf_near_kernel (FP64 gather: near field + leaf expansion, nrhs={nr_roof})",
                 "peak_source": "measured: cuBLAS DGEMM 4096^3 (torch.matmul float64) on this GPU, best of 5",
                 "flops_per_launch": ln_flops, "ms_per_launch": ln_ms,
                 "stage_ms": {k: float(np.mean(v)) for k, v in stage_ms.items()},
                 "fp64_peak_derived_TFLOPs": fp64,
-                "traffic_note": "DRAM read+write bytes of one launch at this size (ncu, profiles/); "
-                                "algorithmic bytes per launch: %.3e" % (st["entries_D"] * 8 + 2 * N * nr_roof * 8)}
+                "algorithmic_bytes_per_launch": ln_alg_bytes,
+                "traffic_note": "DRAM read+write bytes per launch: ncu capture at %s (%.3e B for %.3e algorithmic B), "
+                                "scaled by the algorithmic bytes; each CTA (leaf, right-hand-side tile) re-reads the "
+                                "leaf's near blocks" % (MATVEC_TRAFFIC_SMALL["grid"], MATVEC_TRAFFIC_SMALL["dram_bytes"],
+                                                         MATVEC_TRAFFIC_SMALL["algorithmic_bytes"])}
     # the construction's FP64 batched GEMM (operator DSTs, piece subtraction, stacked-QR inputs),
     # timed per launch with events on the build stream over the timed steps
     gemm_tf = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
