@@ -691,10 +691,12 @@ void Builder::assemble(h2_handle_s* h) {
                     const RInfo ri = rt[Key{l, t, lp}];
                     StackJob jb{(int)segs.size(), 0, q, Rb.p + ri.off, q, nullptr, nullptr};
                     auto par = rt.find(Key{l - 1, t >> 1, lp});
-                    if (par != rt.end() && par->second.reff) segs.push_back(RowSeg{Rb.p + par->second.off, par->second.reff, q});
+                    // a factor of a stack with at least q rows is upper triangular (tri)
+                    if (par != rt.end() && par->second.reff)
+                        segs.push_back(RowSeg{Rb.p + par->second.off, par->second.reff, q, par->second.reff == q});
                     for (int sb : ow->second) {
                         const RInfo& si = rs[Key{l, sb, lp}];
-                        if (si.reff) segs.push_back(RowSeg{Rb.p + si.off, si.reff, q});
+                        if (si.reff) segs.push_back(RowSeg{Rb.p + si.off, si.reff, q, si.reff == q});
                     }
                     jb.seg_end = (int)segs.size();
                     jobs.push_back(jb);

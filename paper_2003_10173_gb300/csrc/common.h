@@ -236,10 +236,13 @@ void panel_colnorm_max(int count, const int64_t* d_y_off, const int* d_m, int c,
 
 // ---- stacked QR and truncated SVD (svd.cu) ----------------------------------
 // One row block of a stacked matrix: rows x c at p (column-major, leading dimension ld).
+// tri = 1: the block is upper triangular (its row i is zero in the columns before i), which the
+// stacked QR uses to skip the zero part of every reflector.
 struct RowSeg {
     const double* p;
     int rows;
     int ld;
+    int tri = 0;
 };
 // A matrix given as the stack of segments [seg_begin, seg_end), each with c columns.
 struct StackJob {

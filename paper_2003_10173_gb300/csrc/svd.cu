@@ -43,7 +43,7 @@ constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kSmemMaxC = 144;     // widest matrix of stacked_r (its working matrix in shared memory)
 
 // rows of a chunk streamed under R: shared memory holds (c + chunk) x c doubles
-__host__ __device__ inline int chunk_rows(int c) { return c <= 48 ? 128 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)); }
+__host__ __device__ inline int chunk_rows(int c) { return c <= 48 ? 112 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)); }
 // chunk height of the SVD kernel: fixed, so that its shared memory grows with c (one launch per level)
 constexpr int kSvdChunk = 64;
 // leading dimension of the working matrix [R; chunk]: odd, so that the columns of a warp's
@@ -60,6 +60,9 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
                            double* tau) {
     __shared__ const double* rp[128];
     __shared__ int rld[128];
+    __shared__ const double* rp2[128];
+    __shared__ int rld2[128], fz[128];
+    __shared__ int nact[kSmemMaxC + 1];   // chunk rows whose first nonzero column is <= j (rows sorted so)
     __shared__ int hs;
     __shared__ double part[NT];      // slice partial sums of the dot products
     __shared__ double fk[kSmemMaxC];    // tau_j sc_j w_k of every trailing column
@@ -69,19 +72,35 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
     int sgi = b, off = 0;   // next row: segment sgi, row off (the same in every thread)
     while (true) {
         __syncthreads();
-        if (threadIdx.x == 0) {   // the rows of the next chunk
+        if (threadIdx.x == 0) {   // the rows of the next chunk, sorted by their first nonzero column
             int h = 0, s2 = sgi, o2 = off;
+            for (int j = 0; j <= c; ++j) nact[j] = 0;
             while (h < ch && s2 < e) {
                 const RowSeg sg = segs[s2];
                 const int take = min(ch - h, sg.rows - o2);
                 for (int i = 0; i < take; ++i) {
-                    rp[h + i] = sg.p + o2 + i;
-                    rld[h + i] = sg.ld;
+                    rp2[h + i] = sg.p + o2 + i;
+                    rld2[h + i] = sg.ld;
+                    const int f = sg.tri ? min(o2 + i, c) : 0;
+                    fz[h + i] = f;
+                    ++nact[f];
                 }
                 h += take;
                 o2 += take;
                 if (o2 >= sg.rows) { ++s2; o2 = 0; }
             }
+            int pos = 0;   // counting sort: nact[j] becomes the first position of bucket j
+            for (int j = 0; j <= c; ++j) {
+                const int n = nact[j];
+                nact[j] = pos;
+                pos += n;
+            }
+            for (int i = 0; i < h; ++i) {
+                const int q = nact[fz[i]]++;
+                rp[q] = rp2[i];
+                rld[q] = rld2[i];
+            }
+            // nact[j] is now the end of bucket j: the rows with first nonzero column <= j
             hs = h;
         }
         __syncthreads();
@@ -111,21 +130,28 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
         // The squared norm of y_{j+1}, needed for reflector j + 1, is accumulated while y_{j+1}
         // is updated.
         if (threadIdx.x < (NT / 32)) {   // ||y_0||^2 in (NT / 32) row slices
-            const int rs0 = (h + (NT / 32) - 1) / (NT / 32);
+            const int h0 = nact[0];
+            const int rs0 = (h0 + (NT / 32) - 1) / (NT / 32);
             double x2 = 0.0;
-            for (int r = threadIdx.x * rs0; r < min(h, (threadIdx.x + 1) * rs0); ++r) x2 = fma(A[c + r], A[c + r], x2);
+            for (int r = threadIdx.x * rs0; r < min(h0, (threadIdx.x + 1) * rs0); ++r) x2 = fma(A[c + r], A[c + r], x2);
             nrm[threadIdx.x] = x2;
         }
         __syncthreads();
         for (int j = 0; j < c; ++j) {
+            // rows below ha are zero in column j (first nonzero column > j): reflector j and its
+            // updates skip them; the update pass covers hc rows, where column j + 1 may be nonzero
+            const int ha = nact[j];
+            const int hc = j + 1 < c ? nact[j + 1] : ha;
             const int nk = c - j - 1;
             const int ns = nk > 0 ? min((NT / 32), NT / nk) : 0;
-            const int rs = ns > 0 ? (h + ns - 1) / ns : 0;
+            const int rs = ns > 0 ? (ha + ns - 1) / ns : 0;
+            const int rsc = ns > 0 ? (hc + ns - 1) / ns : 0;
             const int t = threadIdx.x;
             const bool act = t < nk * ns;
             const int k = act ? j + 1 + t % nk : 0;
             const int sl = act ? t / nk : 0;
-            const int r0 = sl * rs, r1 = min(h, r0 + rs);
+            const int r0 = sl * rs, r1 = min(ha, r0 + rs);
+            const int c0 = sl * rsc, c1 = min(hc, c0 + rsc);
             const double* yj = A + c + (int64_t)j * lda;
             double* yk = A + c + (int64_t)k * lda;
             if (t == 0) {   // reflector j from ||y_j||^2 and R[j, j]
@@ -163,9 +189,9 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
             __syncthreads();
             if (act && tj != 0.0) {
                 const double g = fk[k - j - 1];
-                if (k == j + 1) {
+                if (k == j + 1) {   // rows ha..hc-1 have y_j = 0: their update is exact, only the norm needs them
                     double x2 = 0.0;
-                    for (int r = r0; r < r1; ++r) {
+                    for (int r = c0; r < c1; ++r) {
                         const double y = fma(-g, yj[r], yk[r]);
                         yk[r] = y;
                         x2 = fma(y, y, x2);
@@ -176,7 +202,7 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
                 }
             } else if (act && k == j + 1) {
                 double x2 = 0.0;
-                for (int r = r0; r < r1; ++r) x2 = fma(yk[r], yk[r], x2);
+                for (int r = c0; r < c1; ++r) x2 = fma(yk[r], yk[r], x2);
                 nrm[sl] = x2;
             }
             __syncthreads();
@@ -273,12 +299,11 @@ __device__ void pivoted_qr(double* A, int lda, int c, int* perm, double* cn, dou
     __syncthreads();
 }
 
-// One CTA per job.  The c x c triangle of the incremental QR holds the
-// rank of the stack in the rows of the columns where it appears (a stack with fewer rows
-// than columns, or with leading zero columns, leaves other rows zero), so the output is
-// compacted: the min(c, rows) rows of largest norm are written first (R^T R, the only use of
-// R, does not depend on the order of its rows) and the remaining rows -- zero in exact
-// arithmetic -- are written as zeros.
+// One CTA per job.  A stack with at least c rows gives its c x c upper triangle as computed.
+// With fewer rows the triangle holds the rank of the stack in the rows of the columns where it
+// appears (leading zero columns leave other rows zero), so the output is compacted: the
+// min(c, rows) rows of largest norm are written first (R^T R, the only use of R, does not depend
+// on the order of its rows) and the remaining rows -- zero in exact arithmetic -- as zeros.
 __global__ void __launch_bounds__(QR_NT) stacked_r_kernel(const StackJob* __restrict__ jobs, int njobs,
                                                           const RowSeg* __restrict__ segs) {
     extern __shared__ double smem[];
@@ -296,6 +321,14 @@ __global__ void __launch_bounds__(QR_NT) stacked_r_kernel(const StackJob* __rest
         int rows = 0;
         for (int i = jb.seg_begin; i < jb.seg_end; ++i) rows += segs[i].rows;
         const int reff = min(c, rows);
+        if (rows >= c) {   // the triangle as computed (upper triangular: callers may mark it tri)
+            for (int x = threadIdx.x; x < c * c; x += QR_NT) {
+                const int r = x % c, k = x / c;
+                jb.out[r + (int64_t)k * jb.ldo] = r <= k ? A[r + (int64_t)k * lda] : 0.0;
+            }
+            __syncthreads();
+            continue;
+        }
         for (int j = warp; j < c; j += QR_NW) {   // squared norms of the rows of R
             double x = 0.0;
             for (int k = j + lane; k < c; k += 32) {
@@ -658,7 +691,7 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
             for (int i = 0; i < sp.count; ++i) {
                 const StackJob& pj = parts[sp.first_part + i];
                 const int prow = (int)job_rows(pj, psegs);
-                segs.push_back(RowSeg{pj.out, std::min(prow, pj.c), pj.c});
+                segs.push_back(RowSeg{pj.out, std::min(prow, pj.c), pj.c, prow >= pj.c});
             }
             fj.seg_end = (int)segs.size();
         }
