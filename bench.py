@@ -150,9 +150,10 @@ def scaled(cfg: dict, n: int) -> dict:
 
 def precision_section(h2, torch, stream, bf16_peak: float, n: int = 512) -> dict:
     """512 x 512 heat Hessian (N = 262,144, 16,384 sensors, kappa 0.005, rank cap 48): FP64
-    construction, then the matvec with nrhs = 1024 in FP64, TF32 and BF16 (FP32 accumulation,
-    near field on tcgen05).  Errors of the reduced-precision results are stated against the
-    FP64 matvec of the same H^2.  n other than 512 (profiling) keeps the sensor fraction."""
+    construction, then the matvec with nrhs = 1024 in FP64, TF32, split TF32 and BF16 (FP32
+    accumulation, near field on tcgen05) and compensated FP32 (FP32 storage, float-pair
+    arithmetic).  Errors of the reduced-precision results are stated against the FP64 matvec of
+    the same H^2.  n other than 512 (profiling) keeps the sensor fraction."""
     c = scaled(W.LARGE_N512, n)
     p, b = c["problem"], c["build"]
     N = p.N
@@ -205,6 +206,26 @@ def precision_section(h2, torch, stream, bf16_peak: float, n: int = 512) -> dict
                               "peak_TFLOPs": peak, "rel_err_vs_fp64_matvec": err,
                               "stage_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
         del X, Y
+    # compensated FP32 (FP32 storage, float-pair arithmetic on the FP32 pipe, FP64 X and Y)
+    Yc = torch.empty_like(X64)
+    G.matvec(X64, Yc, nrhs, h2.H2_FP32C, stream=stream)          # warm-up
+    torch.cuda.synchronize()
+    G.profile(True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        G.matvec(X64, Yc, nrhs, h2.H2_FP32C, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = G.profile_read()
+    G.profile(False)
+    msc = e0.elapsed_time(e1) / reps
+    errc = float((Yc - Y64).norm() / Y64.norm())
+    colc = float(((Yc - Y64).norm(dim=1) / Y64.norm(dim=1)).max())
+    out["modes"]["FP32C"] = {"ms": msc, "rel_err_vs_fp64_matvec": errc, "worst_column_rel_err": colc,
+                             "speedup_vs_fp64": out["modes"]["FP64"]["ms"] / msc,
+                             "stage_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
+    del Yc
     # FP32 storage at nrhs = 1: the HBM-bound form of the matvec
     x1 = X64[:1].float().contiguous()
     y1 = torch.empty_like(x1)

@@ -65,8 +65,13 @@ enum {
     H2_FP32 = 1,   /* X, Y float; FP32 storage and arithmetic */
     H2_TF32 = 2,   /* X float, Y float; FP32 storage, TF32 tensor-core products, FP32 accumulation */
     H2_BF16 = 3,   /* X bf16 (uint16 storage), Y float; BF16 storage, tensor-core products, FP32 accumulation */
-    H2_TF32X3 = 4  /* X float, Y float; FP32 storage, split-TF32 tensor-core products (hi*hi + hi*lo + lo*hi,
+    H2_TF32X3 = 4, /* X float, Y float; FP32 storage, split-TF32 tensor-core products (hi*hi + hi*lo + lo*hi,
                       about 22 significant bits, FP32-grade) from nrhs >= 64, FP32 arithmetic below */
+    H2_FP32C = 5   /* X, Y double; FP32 storage (the FP32 copy: keep_fp32), compensated FP32 arithmetic on
+                      the FP32 pipe: every value a pair hi + lo of floats (about 48 significant bits), products
+                      and sums by error-free transformations, so that the FP32 rounding of the stored factors
+                      (2^-24 relative per entry) is the only reduced-precision step; SIMT gather kernels at
+                      every nrhs.  Not available in h2_matvec_noalloc and the batch API. */
 };
 
 #define H2_MAX_LEVELS 32

@@ -33,6 +33,7 @@ H2_FP32 = 1
 H2_TF32 = 2
 H2_BF16 = 3
 H2_TF32X3 = 4
+H2_FP32C = 5
 H2_SAMPLING_WEAK = 0
 H2_SAMPLING_COLORED = 1
 

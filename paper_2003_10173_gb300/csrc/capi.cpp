@@ -615,7 +615,7 @@ int h2_matvec(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_t ldy, i
         if (nrhs == 0) return H2_OK;
         require(X != nullptr && Y != nullptr, "h2_matvec: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec: leading dimension smaller than n");
-        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_FP32C, "h2_matvec: unknown mode");
         h2::run_matvec(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });
@@ -629,7 +629,7 @@ int h2_matvec_host(h2_handle_t h, const void* X_host, int64_t ldx, void* Y_host,
         if (nrhs == 0) return H2_OK;
         require(X_host != nullptr && Y_host != nullptr, "h2_matvec_host: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec_host: leading dimension smaller than n");
-        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec_host: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_FP32C, "h2_matvec_host: unknown mode");
         h2::run_matvec_host(h, X_host, ldx, Y_host, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });
@@ -643,7 +643,7 @@ int h2_matvec_noalloc(h2_handle_t h, const void* X, int64_t ldx, void* Y, int64_
         if (nrhs == 0) return H2_OK;
         require(X != nullptr && Y != nullptr, "h2_matvec_noalloc: NULL X or Y");
         require(ldx >= h->N && ldy >= h->N, "h2_matvec_noalloc: leading dimension smaller than n");
-        require(mode >= H2_FP64 && mode <= H2_TF32X3, "h2_matvec_noalloc: unknown mode");
+        require(mode >= H2_FP64 && mode <= H2_FP32C, "h2_matvec_noalloc: unknown mode");
         h2::run_matvec_noalloc(h, X, ldx, Y, ldy, nrhs, mode, (cudaStream_t)stream);
         return H2_OK;
     });

@@ -12,6 +12,7 @@
 //   5. leaf expansion    Y_t = U_t yh_t + sum_s D_ts X_s       (written through the permutation)
 // Only the lower triangle of S and D is stored; upper blocks are used as
 // transposes of the stored ones.
+#include <type_traits>
 #include <algorithm>
 #include <functional>
 #include <mutex>
@@ -35,6 +36,50 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 template <class TA, class T> __device__ __forceinline__ TA cvt(T x) { return (TA)to_f<T>(x); }
 template <> __device__ __forceinline__ double cvt<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
+
+// Compensated FP32 value hi + lo (an unevaluated pair of floats): about 48 significant bits
+// computed on the FP32 pipe (H2_FP32C).  Products and sums use the error-free transformations
+// of Dekker and Knuth (the product's rounding error from one FMA, the sum's from the two-sum
+// sequence), so that the stored factors' FP32 rounding is the only reduced-precision step.
+struct CF {
+    float hi, lo;
+    CF() = default;
+    __host__ __device__ constexpr CF(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit constexpr CF(int x) : hi((float)x), lo(0.f) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ CF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return CF(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ CF fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return CF(s, b - (s - a));
+}
+// c + a b (an overload beside the library's fma, which stays visible for the other types).  The
+// high part takes the exact two-sum of c.hi and the rounded product; the product's rounding
+// error, the cross terms and the sum's error go to the low part, which is not renormalised here:
+// hi + lo stays an unevaluated pair whose low part accumulates terms of about 2^-24 of the
+// products, so its own rounding costs about 2^-48 of them.
+using ::fma;
+__device__ __forceinline__ CF fma(CF a, CF b, CF c) {
+    const float p = a.hi * b.hi;
+    const float pe = fmaf(a.hi, b.hi, -p);
+    const float err = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pe));
+    const CF t = two_sum(c.hi, p);
+    return CF(t.hi, c.lo + (t.lo + err));
+}
+__device__ __forceinline__ CF operator+(CF a, CF b) {
+    const CF t = two_sum(a.hi, b.hi);
+    return fast_two_sum(t.hi, t.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ double operator+(double a, CF b) { return a + (double)b; }
+template <> __device__ __forceinline__ CF cvt<CF, float>(float x) { return CF(x, 0.f); }
+template <> __device__ __forceinline__ CF cvt<CF, double>(double x) {
+    const float h = __double2float_rn(x);
+    return CF(h, __double2float_rn(x - (double)h));
+}
 
 // TS: factor storage type, TX: type of X, TY: type of Y, TA: arithmetic / workspace type.
 template <class TS, class TX, class TY, class TA, bool OUT_Y, int RTT>
@@ -652,10 +697,12 @@ void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, 
 template <class TS, class TX, class TY, class TA>
 void run_all(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, TY* Y, int64_t ldy,
              int nrhs, cudaStream_t s, bool allow_prof = true) {
-    if (nrhs <= kSmallNrhs) {
-        // the no-allocation entry point (allow_prof false) creates no second stream
-        run_small<TS, TX, TY, TA>(h, fac, ws, X, ldx, Y, ldy, nrhs, s, allow_prof && h->prof, allow_prof);
-        return;
+    if constexpr (!std::is_same<TA, CF>::value) {   // the compensated form has no atomics: gather at every nrhs
+        if (nrhs <= kSmallNrhs) {
+            // the no-allocation entry point (allow_prof false) creates no second stream
+            run_small<TS, TX, TY, TA>(h, fac, ws, X, ldx, Y, ldy, nrhs, s, allow_prof && h->prof, allow_prof);
+            return;
+        }
     }
     for (const MvStage& st : h->plan.stages) {
         if (allow_prof && h->prof && !st.outs.empty()) {
@@ -748,6 +795,7 @@ void run_matvec_noalloc(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int
                         cudaStream_t s) {
     if (nrhs <= 0) return;
     if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: nrhs above 2,000,000");
+    if (mode == H2_FP32C) fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: H2_FP32C is not available here");
     if (mode == H2_TF32 || mode == H2_TF32X3)
         fail(H2_ERR_INVALID_ARG, "h2_matvec_noalloc: H2_TF32 and H2_TF32X3 need the tensor-core path's operand "
                                  "workspace; use H2_FP32, H2_BF16 or h2_matvec");
@@ -1146,6 +1194,14 @@ std::function<void(cudaStream_t)> matvec_launches(h2_handle_s* h, const void* X,
                                                     (int)nrhs, s);
             };
         }
+        case H2_FP32C: {
+            if (!h->fac32.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: FP32 copy of the factors was not kept");
+            h->ws.f64.reserve((size_t)need);   // one CF (two floats) per coefficient
+            return [=](cudaStream_t s) {
+                run_all<float, double, double, CF>(h, h->fac32.p, reinterpret_cast<CF*>(h->ws.f64.p), (const double*)X,
+                                                   ldx, (double*)Y, ldy, (int)nrhs, s);
+            };
+        }
         case H2_BF16: {
             if (!h->fac16.p) fail(H2_ERR_INVALID_ARG, "h2_matvec: BF16 copy of the factors was not kept");
             h->ws.f32.reserve((size_t)need);
@@ -1177,8 +1233,9 @@ void run_matvec_host(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_
                      cudaStream_t s) {
     if (nrhs <= 0) return;
     if (nrhs > kMaxNrhs) fail(H2_ERR_INVALID_ARG, "h2_matvec_host: nrhs above 2,000,000");
-    const size_t ex = mode == H2_FP64 ? 8 : (mode == H2_BF16 ? 2 : 4);
-    const size_t ey = mode == H2_FP64 ? 8 : 4;
+    const bool f64io = mode == H2_FP64 || mode == H2_FP32C;
+    const size_t ex = f64io ? 8 : (mode == H2_BF16 ? 2 : 4);
+    const size_t ey = f64io ? 8 : 4;
     const size_t n = (size_t)h->N;
     h->host_x.reserve(n * ex * (size_t)nrhs);
     h->host_y.reserve(n * ey * (size_t)nrhs);
@@ -1197,7 +1254,7 @@ void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy
         launch(s);
         return;
     }
-    const void* ws = (mode == H2_FP64) ? (const void*)h->ws.f64.p : (const void*)h->ws.f32.p;
+    const void* ws = (mode == H2_FP64 || mode == H2_FP32C) ? (const void*)h->ws.f64.p : (const void*)h->ws.f32.p;
     const void* opnd = h->tc.opnd.p;
     MvGraph* g = nullptr;
     for (auto& e : h->graphs)

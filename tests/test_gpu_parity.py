@@ -140,6 +140,27 @@ def test_matvec_fp64_matches_oracle(h2, kind, nrhs):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind", ["heat32_strong", "heat32_weak", "ragged", "tiny", "weak_k48"])
+@pytest.mark.parametrize("nrhs", [1, 7, 33, 130])
+def test_matvec_compensated_fp32_matches_oracle(h2, kind, nrhs):
+    """H2_FP32C: FP32 factor storage, every value carried as a float pair hi + lo.  The stored
+    factors' rounding (2^-24 relative per entry) is the only reduced-precision step, so each
+    stage's output errs by a few 2^-24 of the sum of its terms' magnitudes; bound 1e-6 relative
+    (element-wise, per column and per leaf block) against the FP64 oracle's product of the
+    FP64 factors, the accuracy the FP64 construction itself is built to."""
+    h, n, leaf, adm = _oracle_h2(kind)
+    tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
+    G = h2.H2.from_factors(tree, *factors.oracle_to_import(h), keep_fp32=True)
+    X = W.rhs(n * n, nrhs, 19)
+    want = O.matvec(h, X)
+    Xd = dev(X)
+    Yd = torch.full_like(Xd, float("nan"))
+    G.matvec(Xd, Yd, nrhs, h2.H2_FP32C)
+    torch.cuda.synchronize()
+    c, b = assert_elementwise(host(Yd), want, leaf_index_sets(h.tree), 1e-6, "FP32C")
+    print(f"FP32C {kind} nrhs {nrhs}: worst column {c:.1e}, worst leaf block {b:.1e}")
+
+
 @pytest.mark.parametrize("nrhs", [64, 130, 300])
 def test_matvec_wide_transfer_blocks(h2, nrhs):
     """Ranks above 32 in the tree sweeps (transfer blocks up to 48 x 48) with many right-hand
