@@ -130,6 +130,9 @@ typedef struct {
      * comparison mode (it needs far more products): q0 <= 16 fixed probes (adaptive, q_level and
      * global_rank are not used; global_rank must be 0), q0 below every box size with far blocks. */
     int sampling;
+    /* h2_build_batched only: host worker threads, each with its own stream (0: min(count, 8)); the
+     * per-level launches of different Hessians overlap on the GPU across workers. */
+    int batch_workers;
 } h2_build_opts;
 
 enum { H2_SAMPLING_WEAK = 0, H2_SAMPLING_COLORED = 1 };

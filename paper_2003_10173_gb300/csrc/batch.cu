@@ -219,7 +219,7 @@ void launch_tc(h2_batch_s* b, int mode, int md, int rt, int nrhs, const void* co
 int build_batched(int count, const h2_op_fn* ops, void* const* ctxs, const h2_tree_t* trees, double tol,
                   const h2_build_opts& o, h2_handle_t* outs) {
     for (int i = 0; i < count; ++i) outs[i] = nullptr;
-    const int nw = std::max(1, std::min(count, 8));
+    const int nw = std::max(1, std::min(count, o.batch_workers > 0 ? o.batch_workers : 8));
     int worst = H2_OK;
     std::mutex mu;
     std::string first_err;

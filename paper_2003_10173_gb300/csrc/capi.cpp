@@ -92,6 +92,7 @@ h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
     require(o.q_test >= 1 && o.q_test <= 16, "h2_build: q_test must be in 1..16");
     require(o.q_level_stride >= 0, "h2_build: q_level_stride must be >= 0");
     require(o.global_rank >= 0, "h2_build: global_rank must be >= 0");
+    require(o.batch_workers >= 0 && o.batch_workers <= 256, "h2_build: batch_workers must be in 0..256");
     require(o.sampling == H2_SAMPLING_WEAK || o.sampling == H2_SAMPLING_COLORED, "h2_build: unknown sampling");
     require(o.sampling != H2_SAMPLING_COLORED || (o.q0 <= 16 && o.global_rank == 0),
             "h2_build: coloured sampling needs q0 <= 16 and global_rank 0");
