@@ -65,7 +65,7 @@ class Builder {
     int L_;
 
     DevBuf<int32_t> d_perm_, d_row_leaf_;
-    DevBuf<double> Om_, Yo_, Yt_, Ot_, Tw_, Cw_, Ysv_;
+    DevBuf<double> Om_, Yo_, Yt_, Ot_, Tw_, Cw_, Ysv_, Tp_;
     DevBuf<SignItem> d_sign_;
     DevBuf<double> Pcap_;
     std::vector<int64_t> pcol_;      // capacity column offset per level
@@ -94,7 +94,7 @@ class Builder {
     void call_op(const double* X, double* Y, int ncols, bool count_sample);
     void check_flag(const char* where, int level);
     double norm_estimate();
-    void subtract(const double* Omt, double* Yt, int c, int lmax);
+    void subtract(const double* Omt, double* Yt, int c, int lmax, int lsel = -1, int in_par = 0);
     void project(int l, const std::vector<int>& pairs, int c, int c0, int passes);
     std::vector<double> colnorm(int l, const std::vector<int>& pairs, int c, int c0);
     void panel(int l, const std::vector<int>& pairs, int c0, int w);
@@ -186,8 +186,12 @@ void Builder::blocks(int kind, const std::vector<BlkDesc>& d, const double* src,
     block_op(kind, (int)d.size(), dev_list(d_blk_, d, 0), src, dst, s_);
 }
 
-// Y -= K Omega for the pieces of levels 1..lmax (tree order, N x c, ld N).
-void Builder::subtract(const double* Omt, double* Yt, int c, int lmax) {
+// Y -= K Omega for the pieces of levels 1..lmax (tree order, N x c, ld N).  With lsel > 0 the
+// probe block is nonzero only on the rows of the level-lsel boxes whose child index is in_par, and
+// only the rows of the other children are needed (the range pass reads child-1 rows of probes on
+// child-0 rows; the projection pass the reverse): both products then run over those boxes only,
+// the first as per-box partial products summed per level-lp box, so that each does half the work.
+void Builder::subtract(const double* Omt, double* Yt, int c, int lmax, int lsel, int in_par) {
     if (qw_[0] > 0 && lmax >= 0) {
         // the global piece: Y -= B (B^T Om)
         const int q = qw_[0];
@@ -201,6 +205,31 @@ void Builder::subtract(const double* Omt, double* Yt, int c, int lmax) {
         if (q == 0) continue;
         const double* P = Pl(lp);
         const int nb = 1 << lp;
+        if (lsel > lp) {
+            const int sh = lsel - lp;
+            const int64_t blk = (int64_t)q * c;   // one q x c block (leading dimension q)
+            Tp_.reserve((size_t)((int64_t)1 << (lsel - 1)) * blk);
+            Tw_.reserve((size_t)nb * blk);
+            for (int cb = in_par; cb < (1 << lsel); cb += 2)
+                gb_.add(P + bstart(lsel, cb), (int)N_, 1, Omt + bstart(lsel, cb), (int)N_, 0, Tp_.p + (cb >> 1) * blk, q,
+                        q, c, bsize(lsel, cb), 1.0, 0.0);
+            gb_.run(s_);
+            std::vector<int64_t> oo(nb), io;
+            std::vector<int> len(nb, (int)blk), bg(nb), en(nb);
+            for (int b = 0; b < nb; ++b) {
+                oo[b] = b * blk;
+                bg[b] = (int)io.size();
+                for (int cb = (b << sh) + in_par; cb < ((b + 1) << sh); cb += 2) io.push_back((cb >> 1) * blk);
+                en[b] = (int)io.size();
+            }
+            sum_lists(nb, dev_list(d_i64a_, oo, 0), dev_list(d_i32a_, len, 1), dev_list(d_i32b_, bg, 2),
+                      dev_list(d_i32c_, en, 3), dev_list(d_i64b_, io, 0), Tp_.p, Tw_.p, 0, s_);
+            for (int d = 1 - in_par; d < (1 << lsel); d += 2)
+                gb_.add(P + bstart(lsel, d), (int)N_, 0, Tw_.p + ((d >> sh) ^ 1) * blk, q, 0, Yt + bstart(lsel, d),
+                        (int)N_, bsize(lsel, d), c, q, -1.0, 1.0);
+            gb_.run(s_);
+            continue;
+        }
         const int ldt = nb * q;
         for (int b = 0; b < nb; ++b)
             gb_.add(P + bstart(lp, b), (int)N_, 1, Omt + bstart(lp, b), (int)N_, 0, Tw_.p + (int64_t)b * q, ldt, q,
@@ -325,7 +354,7 @@ void Builder::peel_level(int l) {
         probe_fill(N_, c, col0, d_perm_.p, d_row_leaf_.p, L_ - l, o_.seed, STREAM_PROBE, l, Om_.p, Ot_.p, s_);
         call_op(Om_.p, Yo_.p, c, true);
         gather_rows(N_, c, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
-        subtract(Ot_.p, Yt_.p, c, l - 1);
+        subtract(Ot_.p, Yt_.p, c, l - 1, l, 0);
     };
     // orthonormalise the c new columns [off, off + c) of Yt into the bases; returns the max
     // residual of the test
@@ -402,7 +431,7 @@ void Builder::peel_level(int l) {
     scatter_rows(N_, qp, d_perm_.p, P, N_, Om_.p, N_, s_);
     call_op(Om_.p, Yo_.p, qp, true);
     gather_rows(N_, qp, d_perm_.p, Yo_.p, N_, Yt_.p, N_, s_);
-    subtract(P, Yt_.p, qp, l - 1);
+    subtract(P, Yt_.p, qp, l - 1, l, 1);
     std::vector<BlkDesc> d;
     for (int i : all) {
         const int64_t st = bstart(l, 2 * i);
