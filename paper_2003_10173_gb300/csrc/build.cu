@@ -183,6 +183,11 @@ double Builder::norm_estimate() {
 
 void Builder::blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst) {
     if (d.empty()) return;
+    if (kind == BLK_COPY) {
+        const std::vector<BlkDesc> ds = split_copies(d);
+        block_op(kind, (int)ds.size(), dev_list(d_blk_, ds, 0), src, dst, s_);
+        return;
+    }
     block_op(kind, (int)d.size(), dev_list(d_blk_, d, 0), src, dst, s_);
 }
 

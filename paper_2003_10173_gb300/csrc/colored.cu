@@ -198,7 +198,8 @@ class ColoredBuilder {
     }
     void blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst) {
         if (d.empty()) return;
-        block_op(kind, (int)d.size(), dev_list(d_blk_, d, 0), src, dst, s_);
+        const std::vector<BlkDesc> ds = kind == BLK_COPY ? split_copies(d) : d;
+        block_op(kind, (int)ds.size(), dev_list(d_blk_, ds, 0), src, dst, s_);
     }
     const double* Qp(int l, int p) const {
         return Q_[l].p + bstart(l, P_[l].pairs[p].first) + (int64_t)P_[l].jq[p] * q_ * N_;

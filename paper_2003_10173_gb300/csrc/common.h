@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <stdexcept>
 #include <string>
@@ -330,6 +331,23 @@ struct BlkDesc {
 enum { BLK_COPY = 0, BLK_IDENTITY = 1, BLK_SYMMETRIZE = 2 };
 // COPY: dst = src; IDENTITY: dst = I (src unused); SYMMETRIZE: dst = (src + src^T)/2 (square)
 void block_op(int kind, int count, const BlkDesc* d_desc, const double* src, double* dst, cudaStream_t s);
+// Copies of more than kSplitEntries entries split into row chunks, so that one CTA per descriptor
+// copies a bounded piece (identity and symmetrisation blocks are left whole).
+constexpr int kSplitEntries = 1 << 16;
+inline std::vector<BlkDesc> split_copies(const std::vector<BlkDesc>& d) {
+    std::vector<BlkDesc> out;
+    out.reserve(d.size());
+    for (const BlkDesc& b : d) {
+        if ((int64_t)b.rows * b.cols <= kSplitEntries || b.rows < 2) {
+            out.push_back(b);
+            continue;
+        }
+        const int chunk = std::max(1, kSplitEntries / std::max(b.cols, 1));
+        for (int r = 0; r < b.rows; r += chunk)
+            out.push_back(BlkDesc{b.src_off + r, b.dst_off + r, std::min(chunk, b.rows - r), b.cols, b.lds, b.ldd});
+    }
+    return out;
+}
 uint64_t rng_key(uint64_t seed, int stream_id, int level);
 // C (n x n, lower, ld n) with C C^T = A for a symmetric positive semidefinite A (ld n, lower
 // triangle used and overwritten); pivots at rounding level leave their column of C zero.

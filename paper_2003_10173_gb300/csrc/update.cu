@@ -80,8 +80,9 @@ class Updater {
     }
     void blocks(int kind, const std::vector<BlkDesc>& d, const double* src, double* dst) {
         if (d.empty()) return;
-        upload(d_blk_, d, s_, stg_[0]);
-        block_op(kind, (int)d.size(), d_blk_.p, src, dst, s_);
+        const std::vector<BlkDesc> ds = kind == BLK_COPY ? split_copies(d) : d;
+        upload(d_blk_, ds, s_, stg_[0]);
+        block_op(kind, (int)ds.size(), d_blk_.p, src, dst, s_);
     }
     std::vector<int> read_ints(const int* d, int count) {
         std::vector<int> v(count);
