@@ -117,3 +117,23 @@ def test_colored_heat64_products_and_error(h2):
     print(f"coloured heat 64^2: products {st['samples']} (weak {Gw.stats()['samples']}), error {err:.1e}")
     assert err <= tol
     assert st["samples"] > Gw.stats()["samples"]
+
+
+def test_colored_weak_partition(h2):
+    """The weak (HSS) partition: every box has one far partner, its sibling, so each level takes
+    one colour and one slot; products equal the oracle's plan and the result meets the tolerance."""
+    from oracle.tree import ADM_WEAK
+    n, leaf, q, tol = 32, 32, 16, 1e-6
+    gop, op = _heat(h2, n)
+    gtree = h2.Tree(W.grid_coords(n), leaf, ADM_WEAK, 0.7)
+    G = h2.H2.build(gop, gtree, tol, h2.default_opts(kmax=48, q0=q, seed=7, sampling=h2.H2_SAMPLING_COLORED))
+    st = G.stats()
+    tree = ClusterTree(W.grid_coords(n), leaf)
+    plan = C.ColoredPlan(tree, Partition(tree, ADM_WEAK, 0.7), q)
+    assert st["samples"] == plan.samples()
+    assert all(c <= 1 for c in plan.ncolors) and all(s <= 1 for s in plan.nslots)
+    H = op(np.eye(n * n))
+    err = np.linalg.norm(gpu_dense(G, n * n) - H, 2) / np.linalg.norm(H, 2)
+    print(f"coloured weak 32^2: products {st['samples']}, error {err:.1e}, kmax hit {1 - st['tol_met']}")
+    assert err <= tol or st["tol_met"] == 0
+

@@ -161,6 +161,22 @@ def test_matvec_compensated_fp32_matches_oracle(h2, kind, nrhs):
     print(f"FP32C {kind} nrhs {nrhs}: worst column {c:.1e}, worst leaf block {b:.1e}")
 
 
+def test_matvec_compensated_fp32_host_buffers(h2):
+    """H2_FP32C through h2_matvec_host: FP64 host X and Y, the same result as the device call."""
+    h, n, leaf, adm = _oracle_h2("heat32_strong")
+    tree = h2.Tree(W.grid_coords(n), leaf, adm, 0.7)
+    G = h2.H2.from_factors(tree, *factors.oracle_to_import(h), keep_fp32=True)
+    X = W.rhs(n * n, 9, 21)
+    Xh = np.ascontiguousarray(X.T)
+    Yh = np.full_like(Xh, np.nan)
+    G.matvec_host(Xh, Yh, 9, h2.H2_FP32C)
+    Yd = torch.empty((9, n * n), dtype=torch.float64, device="cuda")
+    G.matvec(dev(X), Yd, 9, h2.H2_FP32C)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Yh, Yd.cpu().numpy())
+    assert_elementwise(Yh.T, O.matvec(h, X), leaf_index_sets(h.tree), 1e-6, "FP32C host")
+
+
 @pytest.mark.parametrize("nrhs", [64, 130, 300])
 def test_matvec_wide_transfer_blocks(h2, nrhs):
     """Ranks above 32 in the tree sweeps (transfer blocks up to 48 x 48) with many right-hand

@@ -202,3 +202,33 @@ def test_update_norm_estimate_matches_oracle(h2):
     nrm_g = Gu.stats()["norm_est"]
     print(f"norm estimate: gpu {nrm_g:.15e} oracle {nrm_o:.15e}")
     assert abs(nrm_g - nrm_o) <= 1e-9 * nrm_o
+
+
+def test_update_single_leaf(h2):
+    """A tree of one leaf: no far blocks, the update lands in the one dense block."""
+    n = 4
+    tree = ClusterTree(W.grid_coords(n), 16)
+    part = Partition(tree, ADM_STRONG, 0.7)
+    A = planted.planted_h2(tree, part, 2, 2, 5)
+    ho = O.compress_dense(tree, part, A[np.ix_(tree.perm, tree.perm)], 1e-13, 8)
+    G = h2.H2.from_factors(h2.Tree(W.grid_coords(n), 16, ADM_STRONG, 0.7), *factors.oracle_to_import(ho))
+    B = np.random.default_rng(4).standard_normal((n * n, 2))
+    Gu = G.lowrank_update(dev_cols(B), 2, 1e-10, opts=h2.default_opts(kmax=8, norm_est=1.0))
+    assert np.abs(gpu_dense(Gu, n * n) - (A + B @ B.T)).max() <= 1e-13 * np.abs(A + B @ B.T).max()
+
+
+def test_update_result_keeps_fp32_copy(h2):
+    """The updated handle keeps the requested FP32 copy: its compensated FP32 product agrees with
+    its FP64 product within 1e-6."""
+    tree, part, A, ho, G = planted_case(h2, ADM_STRONG)
+    B = np.random.default_rng(6).standard_normal((tree.N, 3)) / np.sqrt(tree.N)
+    nrm = float(np.linalg.norm(A + B @ B.T, 2))
+    Gu = G.lowrank_update(dev_cols(B), 3, 1e-13, opts=h2.default_opts(kmax=48, norm_est=nrm, keep_fp32=1, keep_bf16=1))
+    X = torch.randn((5, tree.N), dtype=torch.float64, device="cuda")
+    Y64 = torch.empty_like(X)
+    Gu.matvec(X, Y64, 5, h2.H2_FP64)
+    Yc = torch.empty_like(X)
+    Gu.matvec(X, Yc, 5, h2.H2_FP32C)
+    torch.cuda.synchronize()
+    assert float((Yc - Y64).norm() / Y64.norm()) <= 1e-6
+
