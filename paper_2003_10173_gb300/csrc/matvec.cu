@@ -99,6 +99,21 @@ __device__ __forceinline__ void mv_stage_body(const MvOut& o, const MvItem* __re
     TA acc[OPTT];
 #pragma unroll
     for (int q = 0; q < OPTT; ++q) acc[q] = (TA)0;
+    // FP32 arithmetic is bound by the shared-memory reads of its operands rather than by the FMA
+    // pipe: there every thread computes a TI x TR block of the output, so that each staged factor
+    // entry and input value feeds several products (batched FP32 matvec of 64 Hessians, nrhs 64:
+    // 62 -> 39 ms).  FP64 and the compensated form keep one output per thread and step: their
+    // arithmetic per product is the bound (the compensated form measured 388 -> 448 ms tiled).
+    constexpr bool TILED = std::is_same<TA, float>::value;
+    constexpr int TI = 3, TR = 4;
+    const int ngr = (rows + TI - 1) / TI;
+    const bool tile_live = threadIdx.x < ngr * (RTT / TR);
+    const int ti0 = TI * (threadIdx.x % max(ngr, 1)), tr0 = TR * (threadIdx.x / max(ngr, 1));
+    TA tacc[TI][TR];
+#pragma unroll
+    for (int u = 0; u < TI; ++u)
+#pragma unroll
+        for (int v = 0; v < TR; ++v) tacc[u][v] = (TA)0;
 
     for (int it = o.beg; it < o.end; ++it) {
         const MvItem m = items[it];
@@ -126,30 +141,55 @@ __device__ __forceinline__ void mv_stage_body(const MvOut& o, const MvItem* __re
             }
         }
         __syncthreads();
+        if constexpr (TILED) {
+            if (tile_live) {
+                for (int j = 0; j < cols; ++j) {
+                    TA mv[TI], xv[TR];
 #pragma unroll
-        for (int q = 0; q < OPTT; ++q) {
-            const int e = threadIdx.x + q * NT;
-            if (e < nel) {
-                const int i = e % rows, r = e / rows;
-                TA s = acc[q];
-                for (int j = 0; j < cols; ++j) s = fma(Ms[j * (RMAX + 1) + i], IN[j * RTT + r], s);
-                acc[q] = s;
+                    for (int u = 0; u < TI; ++u) mv[u] = Ms[j * (RMAX + 1) + ti0 + u];
+#pragma unroll
+                    for (int v = 0; v < TR; ++v) xv[v] = IN[j * RTT + tr0 + v];
+#pragma unroll
+                    for (int u = 0; u < TI; ++u)
+#pragma unroll
+                        for (int v = 0; v < TR; ++v) tacc[u][v] = fma(mv[u], xv[v], tacc[u][v]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < OPTT; ++q) {
+                const int e = threadIdx.x + q * NT;
+                if (e < nel) {
+                    const int i = e % rows, r = e / rows;
+                    TA s = acc[q];
+                    for (int j = 0; j < cols; ++j) s = fma(Ms[j * (RMAX + 1) + i], IN[j * RTT + r], s);
+                    acc[q] = s;
+                }
             }
         }
         __syncthreads();
     }
+    auto store = [&](int i, int r, TA v) {
+        if (OUT_Y) {
+            TY* y = Y + perm[o.out_off + i] + (int64_t)(r0 + r) * ldy;
+            *y = accumulate ? (TY)(*y + v) : (TY)v;
+        } else {
+            TA* y = ws + o.out_off + i + (int64_t)(r0 + r) * ws_ld;
+            *y = accumulate ? (TA)(*y + v) : v;
+        }
+    };
+    if constexpr (TILED) {
+        if (tile_live)
 #pragma unroll
-    for (int q = 0; q < OPTT; ++q) {
-        const int e = threadIdx.x + q * NT;
-        if (e < nel) {
-            const int i = e % rows, r = e / rows;
-            if (OUT_Y) {
-                TY* y = Y + perm[o.out_off + i] + (int64_t)(r0 + r) * ldy;
-                *y = accumulate ? (TY)(*y + acc[q]) : (TY)acc[q];
-            } else {
-                TA* y = ws + o.out_off + i + (int64_t)(r0 + r) * ws_ld;
-                *y = accumulate ? (TA)(*y + acc[q]) : acc[q];
-            }
+            for (int u = 0; u < TI; ++u)
+#pragma unroll
+                for (int v = 0; v < TR; ++v)
+                    if (ti0 + u < rows && tr0 + v < nr) store(ti0 + u, tr0 + v, tacc[u][v]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < OPTT; ++q) {
+            const int e = threadIdx.x + q * NT;
+            if (e < nel) store(e % rows, e / rows, acc[q]);
         }
     }
 }
