@@ -576,6 +576,49 @@ def update_section(h2, torch, stream, G, N: int, build_s: float) -> dict:
     return out
 
 
+def small_section(h2, torch, stream) -> dict:
+    """The 32 x 32 configuration (N = 1,024, 200 sensors, leaf 32, 64 fixed probes per level, rank
+    cap 16, nrhs 16 in FP64), with the weak (HSS) partition it names and the strong one beside it:
+    build seconds, products, ranks, 2-norm error, matvec time and algorithmic GB/s (median of 20)."""
+    c = W.SMALL_N32
+    p, b = c["problem"], c["build"]
+    nrhs = c["nrhs"][0]
+    gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+    out = {"workload": c["name"], "N": p.N, "nrhs": nrhs, "runs": {}}
+    gen = torch.Generator(device="cuda").manual_seed(c["rhs_seed"])
+    X = torch.randn((nrhs, p.N), dtype=torch.float64, device="cuda", generator=gen)
+    Y = torch.empty_like(X)
+    for name, adm in (("weak", h2.H2_ADM_WEAK), ("strong", h2.H2_ADM_STRONG)):
+        tree = h2.Tree(W.grid_coords(p.n), b.leaf, adm, b.eta)
+        opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
+                               seed=b.seed, stream=stream)
+        times = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = h2.H2.build(gop, tree, b.tol, opts)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            G.close()
+        G = h2.H2.build(gop, tree, b.tol, opts)
+        st = G.stats()
+        ms = []
+        for _ in range(20):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.matvec(X, Y, nrhs, h2.H2_FP64, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        mv = float(np.median(ms))
+        out["runs"][name] = {"build_s": float(np.median(times)), "samples": st["samples"], "max_rank": st["max_rank"],
+                             "tol_met": st["tol_met"], "matvec_ms": mv,
+                             "matvec_GBps": matvec_bytes(st, p.N, nrhs) / (mv / 1e3) / 1e9,
+                             "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, p.N, st["norm_est"], stream)}
+        G.close()
+    return out
+
+
 def sampling_section(h2, torch, stream) -> dict:
     """Sampling structure (Section 3.3: C_l probe blocks of k columns per level).  The weak structure
     (sibling blocks, C_l = 2: range and projection pass, adaptive k) against strong-structure
@@ -902,6 +945,7 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true")
     ap.add_argument("--no-update", action="store_true")
     ap.add_argument("--no-sampling", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-advdiff", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
@@ -1132,6 +1176,10 @@ def main():
     if rank == 0 and not args.no_advdiff:
         advdiff = advdiff_section(h2, torch, stream)
 
+    small = None
+    if rank == 0 and not args.no_small:
+        small = small_section(h2, torch, stream)
+
     sampling = None
     if rank == 0 and not args.no_sampling:
         sampling = sampling_section(h2, torch, stream)
@@ -1181,6 +1229,8 @@ def main():
             line["lowrank_update"] = update
         if sampling is not None:
             line["sampling_structure"] = sampling
+        if small is not None:
+            line["small_n32"] = small
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
