@@ -121,19 +121,32 @@ def test_colored_heat64_products_and_error(h2):
 
 def test_colored_weak_partition(h2):
     """The weak (HSS) partition: every box has one far partner, its sibling, so each level takes
-    one colour and one slot; products equal the oracle's plan and the result meets the tolerance."""
+    one colour and one slot, and the products equal the oracle's plan.  Sampling with q fixed
+    probes per pair caps every sibling block at rank q: at q = 16 the 32^2 sibling blocks need
+    more (the oracle's construction gives the same 3e-3 error), so the GPU is held to the
+    oracle's result with its ranks replayed, not to the tolerance."""
     from oracle.tree import ADM_WEAK
     n, leaf, q, tol = 32, 32, 16, 1e-6
     gop, op = _heat(h2, n)
     gtree = h2.Tree(W.grid_coords(n), leaf, ADM_WEAK, 0.7)
     G = h2.H2.build(gop, gtree, tol, h2.default_opts(kmax=48, q0=q, seed=7, sampling=h2.H2_SAMPLING_COLORED))
     st = G.stats()
+    L = st["levels"]
     tree = ClusterTree(W.grid_coords(n), leaf)
     plan = C.ColoredPlan(tree, Partition(tree, ADM_WEAK, 0.7), q)
     assert st["samples"] == plan.samples()
     assert all(c <= 1 for c in plan.ncolors) and all(s <= 1 for s in plan.nslots)
+    ho, res, _ = C.build_colored(op, W.grid_coords(n), leaf, ADM_WEAK, 0.7, tol, 48, q, 7,
+                                 norm_est=st["norm_est"], ranks=ranks_of(G, L))
+    assert res.samples == st["samples"]
+    Ag = gpu_dense(G, n * n)
+    Ao = O.expand_dense(ho)
+    d = np.linalg.norm(Ag - Ao, 2) / st["norm_est"]
     H = op(np.eye(n * n))
-    err = np.linalg.norm(gpu_dense(G, n * n) - H, 2) / np.linalg.norm(H, 2)
-    print(f"coloured weak 32^2: products {st['samples']}, error {err:.1e}, kmax hit {1 - st['tol_met']}")
-    assert err <= tol or st["tol_met"] == 0
-
+    nh = np.linalg.norm(H, 2)
+    err_g = np.linalg.norm(Ag - H, 2) / nh
+    err_o = np.linalg.norm(Ao - H, 2) / nh
+    print(f"coloured weak 32^2: products {st['samples']}, ||H2_gpu - H2_oracle|| / ||H|| = {d:.1e} "
+          f"(ranks replayed), error {err_g:.1e} (oracle {err_o:.1e})")
+    assert d <= 1e-10
+    assert abs(err_g - err_o) <= 1e-10
