@@ -51,72 +51,99 @@ constexpr int kSvdChunk = 64;
 __host__ __device__ inline int work_ld(int c, int ch) { return (c + ch) | 1; }
 __host__ __device__ inline int work_ld(int c) { return work_ld(c, chunk_rows(c)); }
 
-// R factor (upper c x c, rows 0..c-1 of A) of the stacked row blocks segs[b..e).  The
-// segments' rows are packed into chunks of up to chunk_rows(c) rows (a chunk may span
-// segments), so that short segments cost only their own rows.  Entry state of A is
-// irrelevant; every thread returns after a barrier with R complete.
+// Reflector j (LAPACK dlarfg convention) from alpha = R[j, j] and x2 = ||y_j||^2: tau[j], the
+// scale sc_j = 1 / (alpha - beta) of the chunk part (slot j & 1 of sc), and R[j, j] = beta.
+__device__ inline void householder(double* A, int lda, int j, double x2, double* tau, double* sc) {
+    const double alpha = A[j + (int64_t)j * lda];
+    double tj = 0.0, scj = 0.0, beta = alpha;
+    if (x2 > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
+        tj = (beta - alpha) / beta;
+        scj = 1.0 / (alpha - beta);
+    }
+    tau[j] = tj;
+    sc[j & 1] = scj;
+    A[j + (int64_t)j * lda] = beta;
+}
+
+// R factor (upper c x c, rows 0..c-1 of A) of the stacked row blocks segs[b..e).  The rows
+// stream through shared memory in chunks of up to chunk_rows(c) rows, taken in the order of
+// their first possibly nonzero column f: level 0 holds every row of a dense segment and row 0 of
+// each triangular one (RowSeg::tri), level f > 0 row f of each triangular segment.  A chunk
+// whose rows all start at column f0 or later skips reflectors 0..f0-1 (they are the identity on
+// it), and each reflector it applies meets rows that are nonzero in its column; a stack of
+// triangles (the downsweep's R factors) so costs about half the reflector steps of a
+// segment-by-segment order, each with full rows.  Entry state of A is irrelevant; every
+// thread returns after a barrier with R complete.
 template <int NT>
 __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __restrict__ segs, int b, int e,
                            double* tau) {
     __shared__ const double* rp[128];
     __shared__ int rld[128];
-    __shared__ const double* rp2[128];
-    __shared__ int rld2[128], fz[128];
-    __shared__ int nact[kSmemMaxC + 1];   // chunk rows whose first nonzero column is <= j (rows sorted so)
-    __shared__ int hs;
-    __shared__ double part[NT];      // slice partial sums of the dot products
-    __shared__ double fk[kSmemMaxC];    // tau_j sc_j w_k of every trailing column
-    __shared__ double nrm[(NT / 32)];       // slice partial squared norms of y_{j+1}
-    __shared__ double refl[2];          // sc_j and beta_j
+    __shared__ int nact[kSmemMaxC + 1];   // chunk rows whose first nonzero column is <= j
+    __shared__ int hs, j0s;
+    __shared__ int wf, ws, wo, anytri;    // walk over the stack: level, segment, row offset
+    __shared__ double scl[2];           // sc_j of the current and of the next reflector
     for (int x = threadIdx.x; x < c * c; x += NT) A[x % c + (int64_t)(x / c) * lda] = 0.0;
-    int sgi = b, off = 0;   // next row: segment sgi, row off (the same in every thread)
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int s = b; s < e; ++s) any |= segs[s].tri;
+        anytri = any;
+        wf = 0;
+        ws = b;
+        wo = 0;
+    }
     while (true) {
         __syncthreads();
-        if (threadIdx.x == 0) {   // the rows of the next chunk, sorted by their first nonzero column
-            int h = 0, s2 = sgi, o2 = off;
-            for (int j = 0; j <= c; ++j) nact[j] = 0;
-            while (h < ch && s2 < e) {
-                const RowSeg sg = segs[s2];
-                const int take = min(ch - h, sg.rows - o2);
-                for (int i = 0; i < take; ++i) {
-                    rp2[h + i] = sg.p + o2 + i;
-                    rld2[h + i] = sg.ld;
-                    const int f = sg.tri ? min(o2 + i, c) : 0;
-                    fz[h + i] = f;
-                    ++nact[f];
+        if (threadIdx.x == 0) {   // the rows of the next chunk, in nondecreasing f
+            int h = 0, f = wf, s = ws, o = wo;
+            for (int jj = 0; jj <= c; ++jj) nact[jj] = 0;
+            while (h < ch && f < c) {
+                if (s >= e) {   // next level (none after level 0 without triangular segments)
+                    f = anytri ? f + 1 : c;
+                    s = b;
+                    o = 0;
+                    continue;
                 }
-                h += take;
-                o2 += take;
-                if (o2 >= sg.rows) { ++s2; o2 = 0; }
+                const RowSeg sg = segs[s];
+                if (sg.tri) {
+                    if (f < sg.rows) {
+                        rp[h] = sg.p + f;
+                        rld[h] = sg.ld;
+                        ++nact[f];
+                        ++h;
+                    }
+                    ++s;
+                } else if (f == 0) {
+                    const int take = min(ch - h, sg.rows - o);
+                    for (int i = 0; i < take; ++i) {
+                        rp[h + i] = sg.p + o + i;
+                        rld[h + i] = sg.ld;
+                    }
+                    nact[0] += take;
+                    h += take;
+                    o += take;
+                    if (o >= sg.rows) {
+                        ++s;
+                        o = 0;
+                    }
+                } else {
+                    ++s;
+                }
             }
-            int pos = 0;   // counting sort: nact[j] becomes the first position of bucket j
-            for (int j = 0; j <= c; ++j) {
-                const int n = nact[j];
-                nact[j] = pos;
-                pos += n;
-            }
-            for (int i = 0; i < h; ++i) {
-                const int q = nact[fz[i]]++;
-                rp[q] = rp2[i];
-                rld[q] = rld2[i];
-            }
-            // nact[j] is now the end of bucket j: the rows with first nonzero column <= j
+            wf = f;
+            ws = s;
+            wo = o;
+            for (int jj = 1; jj <= c; ++jj) nact[jj] += nact[jj - 1];
+            int j0 = 0;
+            while (j0 < c && nact[j0] == 0) ++j0;
+            j0s = j0;
             hs = h;
         }
         __syncthreads();
         const int h = hs;
         if (h == 0) break;
-        // the same walk in every thread keeps (sgi, off) uniform
-        {
-            int hh = 0;
-            while (hh < ch && sgi < e) {
-                const int rows = segs[sgi].rows;
-                if (off >= rows) { ++sgi; off = 0; continue; }
-                const int take = min(ch - hh, rows - off);
-                hh += take;
-                off += take;
-            }
-        }
+        const int j0 = j0s;
         for (int x = threadIdx.x; x < h * c; x += NT) {
             const int i = x % h, k = x / h;
             A[c + i + (int64_t)k * lda] = rp[i][(int64_t)k * rld[i]];
@@ -125,85 +152,94 @@ __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __re
         // Column-by-column elimination of the chunk under R.  Reflector j is v = [e_j; sc_j y_j]
         // (y_j: the chunk part of column j, left unscaled), so for every column k > j
         //   w = R[j, k] + sc_j (y_j . y_k),  R[j, k] -= tau_j w,  y_k -= tau_j sc_j w y_j.
-        // Thread t works on column k = j + 1 + t % nk over the row slice t / nk (no warp
-        // reductions: the FP64 pipe is the bound), slice partial sums meet in shared memory.
-        // The squared norm of y_{j+1}, needed for reflector j + 1, is accumulated while y_{j+1}
-        // is updated.
-        if (threadIdx.x < (NT / 32)) {   // ||y_0||^2 in (NT / 32) row slices
-            const int h0 = nact[0];
-            const int rs0 = (h0 + (NT / 32) - 1) / (NT / 32);
-            double x2 = 0.0;
-            for (int r = threadIdx.x * rs0; r < min(h0, (threadIdx.x + 1) * rs0); ++r) x2 = fma(A[c + r], A[c + r], x2);
-            nrm[threadIdx.x] = x2;
+        // A group of ns consecutive lanes (ns a power of two <= 8) works on column k = j + 1 + t / ns,
+        // lane t % ns on the rows t % ns, t % ns + ns, ...; the group's partial dot products meet by
+        // warp shuffles.  Reflector j + 1 only needs y_{j+1} after reflector j and R[j+1, j+1]
+        // (which reflector j does not touch), and the group of column j + 1 is the first lanes of
+        // warp 0: it reduces the squared norm of y_{j+1} while updating it, and lane 0 forms
+        // reflector j + 1 while the other warps still apply reflector j (look-ahead).  A column
+        // costs two block barriers, and the serial reflector stays off the critical path.
+        if (threadIdx.x < 32 && j0 < c) {   // the chunk's first reflector
+            const int h0 = nact[j0];
+            const double* y0 = A + c + (int64_t)j0 * lda;
+            double x0 = 0.0, x1 = 0.0;
+            int r = threadIdx.x;
+            for (; r + 32 < h0; r += 64) {
+                x0 = fma(y0[r], y0[r], x0);
+                x1 = fma(y0[r + 32], y0[r + 32], x1);
+            }
+            if (r < h0) x0 = fma(y0[r], y0[r], x0);
+            double x2 = x0 + x1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            if (threadIdx.x == 0) householder(A, lda, j0, x2, tau, scl);
         }
         __syncthreads();
-        for (int j = 0; j < c; ++j) {
+        for (int j = j0; j < c; ++j) {
             // rows below ha are zero in column j (first nonzero column > j): reflector j and its
-            // updates skip them; the update pass covers hc rows, where column j + 1 may be nonzero
+            // updates skip them; the update of column j + 1 covers hc rows for its norm
             const int ha = nact[j];
             const int hc = j + 1 < c ? nact[j + 1] : ha;
             const int nk = c - j - 1;
-            const int ns = nk > 0 ? min((NT / 32), NT / nk) : 0;
-            const int rs = ns > 0 ? (ha + ns - 1) / ns : 0;
-            const int rsc = ns > 0 ? (hc + ns - 1) / ns : 0;
+            const int m = nk > 0 ? min(8, NT / nk) : 1;
+            const int ns = m >= 8 ? 8 : (m >= 4 ? 4 : (m >= 2 ? 2 : 1));
             const int t = threadIdx.x;
-            const bool act = t < nk * ns;
-            const int k = act ? j + 1 + t % nk : 0;
-            const int sl = act ? t / nk : 0;
-            const int r0 = sl * rs, r1 = min(ha, r0 + rs);
-            const int c0 = sl * rsc, c1 = min(hc, c0 + rsc);
+            const int ci = t / ns, sl = t - ci * ns;
+            const bool act = ci < nk;
             const double* yj = A + c + (int64_t)j * lda;
-            double* yk = A + c + (int64_t)k * lda;
-            if (t == 0) {   // reflector j from ||y_j||^2 and R[j, j]
-                double x2 = 0.0;
-                for (int q = 0; q < (NT / 32); ++q) x2 += nrm[q];
-                const double alpha = A[j + (int64_t)j * lda];
-                double tj = 0.0, scj = 0.0, beta = alpha;
-                if (x2 > 0.0) {
-                    beta = -copysign(sqrt(fma(alpha, alpha, x2)), alpha);
-                    tj = (beta - alpha) / beta;
-                    scj = 1.0 / (alpha - beta);
+            double* yk = A + c + (int64_t)(act ? j + 1 + ci : j) * lda;
+            double d = 0.0;
+            if (act) {   // four independent partial sums per lane
+                double d1 = 0.0, d2 = 0.0, d3 = 0.0;
+                int r = sl;
+                for (; r + 3 * ns < ha; r += 4 * ns) {
+                    d = fma(yj[r], yk[r], d);
+                    d1 = fma(yj[r + ns], yk[r + ns], d1);
+                    d2 = fma(yj[r + 2 * ns], yk[r + 2 * ns], d2);
+                    d3 = fma(yj[r + 3 * ns], yk[r + 3 * ns], d3);
                 }
-                tau[j] = tj;
-                refl[0] = scj;
-                refl[1] = beta;
+                for (; r < ha; r += ns) d = fma(yj[r], yk[r], d);
+                d = (d + d1) + (d2 + d3);
             }
-            if (act) {
-                double d = 0.0;
-                for (int r = r0; r < r1; ++r) d = fma(yj[r], yk[r], d);
-                part[t] = d;
-            }
+            for (int o = ns >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
             __syncthreads();
-            const double tj = tau[j], scj = refl[0];
-            if (t == 0) A[j + (int64_t)j * lda] = refl[1];
-            if (t < nk) {
-                const int kk = j + 1 + t;
-                double w = 0.0;
-                for (int q = 0; q < ns; ++q) w += part[t + q * nk];
-                w = fma(scj, w, A[j + (int64_t)kk * lda]);
-                const double f = tj * w;
-                A[j + (int64_t)kk * lda] -= f;
-                fk[t] = f * scj;
-            }
-            if (t < (NT / 32)) nrm[t] = 0.0;
-            __syncthreads();
-            if (act && tj != 0.0) {
-                const double g = fk[k - j - 1];
-                if (k == j + 1) {   // rows ha..hc-1 have y_j = 0: their update is exact, only the norm needs them
-                    double x2 = 0.0;
-                    for (int r = c0; r < c1; ++r) {
-                        const double y = fma(-g, yj[r], yk[r]);
-                        yk[r] = y;
-                        x2 = fma(y, y, x2);
+            if (nk > 0) {
+                const double tj = tau[j], scj = scl[j & 1];
+                double g = 0.0;
+                if (act && sl == 0 && tj != 0.0) {   // the group's first lane updates R[j, k]
+                    double* rjk = A + j + (int64_t)(j + 1 + ci) * lda;
+                    const double w = fma(scj, d, *rjk);
+                    const double f = tj * w;
+                    *rjk -= f;
+                    g = f * scj;
+                }
+                g = __shfl_sync(0xffffffffu, g, (t & 31) & ~(ns - 1));
+                double xn = 0.0;
+                if (act && ci == 0) {   // y_{j+1}: rows ha..hc-1 have y_j = 0 (exact), only the norm needs them
+                    double x1 = 0.0;
+                    int r = sl;
+                    for (; r + ns < hc; r += 2 * ns) {
+                        const double y0 = fma(-g, yj[r], yk[r]);
+                        const double y1 = fma(-g, yj[r + ns], yk[r + ns]);
+                        yk[r] = y0;
+                        yk[r + ns] = y1;
+                        xn = fma(y0, y0, xn);
+                        x1 = fma(y1, y1, x1);
                     }
-                    nrm[sl] = x2;
-                } else {
-                    for (int r = r0; r < r1; ++r) yk[r] = fma(-g, yj[r], yk[r]);
+                    if (r < hc) {
+                        const double y0 = fma(-g, yj[r], yk[r]);
+                        yk[r] = y0;
+                        xn = fma(y0, y0, xn);
+                    }
+                    xn += x1;
+                } else if (act && tj != 0.0) {
+#pragma unroll 4
+                    for (int r = sl; r < ha; r += ns) yk[r] = fma(-g, yj[r], yk[r]);
                 }
-            } else if (act && k == j + 1) {
-                double x2 = 0.0;
-                for (int r = c0; r < c1; ++r) x2 = fma(yk[r], yk[r], x2);
-                nrm[sl] = x2;
+                if (t < 32) {   // warp 0: the norm of y_{j+1} over its group, then reflector j + 1
+                    for (int o = ns >> 1; o > 0; o >>= 1) xn += __shfl_xor_sync(0xffffffffu, xn, o);
+                    if (t == 0) householder(A, lda, j + 1, xn, tau, scl);
+                }
             }
             __syncthreads();
         }
