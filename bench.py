@@ -37,6 +37,10 @@ import workloads as W  # noqa: E402
 
 METRIC = "H² matvec GB/s (% HBM peak) & peeling build s at 1e-6 rel err vs FP64 plain"
 CFG = W.MEDIUM_N256
+# The stepped construction keeps each level's range basis to the columns its passing a-posteriori
+# test certified (the adaptive range finder's textbook form); the certified_bases section sets
+# it against bases that span every probe drawn.  The oracle legs build the same way.
+HEADLINE_CERTIFIED = True
 # DRAM bytes (read + write) of one mv_leaf_near_kernel launch at nrhs = 256, from an ncu capture of
 # the same kernel on the 128 x 128 member of the bench family (profiles/ names the command), with
 # the algorithmic bytes of that launch; the full-size traffic is scaled by the algorithmic bytes
@@ -529,6 +533,48 @@ def hybrid_section(h2, torch, stream) -> dict:
     return out
 
 
+def certified_section(h2, torch, stream) -> dict:
+    """Certified range bases (the passing range test's columns left out of each level's basis,
+    the adaptive range finder's textbook form) against the default bases on the 256 x 256 and
+    512 x 512 heat Hessians at tol 1e-6: products, operator calls, build seconds (best of two),
+    projection probes, ranks and the 2-norm error of each."""
+    out = {}
+    for cfg in (W.MEDIUM_N256, W.LARGE_N512):
+        p, bb = cfg["problem"], cfg["build"]
+        gop = h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed))
+        tree = h2.Tree(W.grid_coords(p.n), bb.leaf, bb.adm, bb.eta)
+        res = {}
+        for key, c in (("default", 0), ("certified", 1)):
+            opts = h2.default_opts(kmax=bb.kmax, q0=bb.q0, b_inc=bb.b_inc, q_max=bb.q_max, adaptive=1, seed=bb.seed,
+                                   stream=stream, certified=c)
+            best = None
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                G = h2.H2.build(gop, tree, bb.tol, opts)
+                torch.cuda.synchronize()
+                bt = time.perf_counter() - t0
+                if best is None or bt < best[0]:
+                    if best is not None:
+                        best[1].close()
+                    best = (bt, G)
+                else:
+                    G.close()
+            bt, G = best
+            st = G.stats()
+            res[key] = {"samples": st["samples"], "op_calls": st["op_calls"], "build_s": bt, "t_peel": st["t_peel"],
+                        "t_assemble": st["t_assemble"], "proj_probes": st["proj_probes"],
+                        "range_probes": st["range_probes"], "max_rank": st["max_rank"], "tol_met": st["tol_met"],
+                        "rel_err_2norm": rel_err_2norm(h2, torch, gop, G, p.N, st["norm_est"], stream)}
+            G.close()
+        res["samples_saved"] = 1.0 - res["certified"]["samples"] / res["default"]["samples"]
+        res["build_speedup"] = res["default"]["build_s"] / res["certified"]["build_s"]
+        out[cfg["name"]] = res
+        del gop, tree
+        torch.cuda.empty_cache()
+    return out
+
+
 def update_section(h2, torch, stream, G, N: int, build_s: float) -> dict:
     """Low-rank update with recompression (Section 3.2, Eqs. 3.3-3.4) of the headline H^2 matrix:
     A~ = A + B B^T with a Gaussian B (columns of the size of the Hessian's leading eigenvalues),
@@ -761,7 +807,8 @@ def _spec(cfg: dict, nrhs) -> dict:
     p, b = cfg["problem"], cfg["build"]
     return {"n": p.n, "m": p.m, "kappa": p.kappa, "T": p.T, "sigma": p.sigma, "sensor_seed": p.sensor_seed,
             "leaf": b.leaf, "adm": b.adm, "eta": b.eta, "tol": b.tol, "kmax": b.kmax, "q0": b.q0, "b_inc": b.b_inc,
-            "q_max": b.q_max, "adaptive": bool(b.adaptive), "seed": b.seed, "nrhs": list(nrhs), "rhs_seed": 5}
+            "q_max": b.q_max, "adaptive": bool(b.adaptive), "seed": b.seed, "nrhs": list(nrhs), "rhs_seed": 5,
+            "certified": HEADLINE_CERTIFIED}
 
 
 def oracle_worker(spec: dict) -> dict:
@@ -784,7 +831,8 @@ def oracle_worker(spec: dict) -> dict:
         op = O.HeatHessian(n, spec["kappa"], spec["T"], spec["sigma"], mask)
         t0 = time.perf_counter()
         h, res = O.build(op, W.grid_coords(n), spec["leaf"], spec["adm"], spec["eta"], spec["tol"], spec["kmax"],
-                         spec["q0"], spec["b_inc"], spec["q_max"], spec["adaptive"], spec["seed"])
+                         spec["q0"], spec["b_inc"], spec["q_max"], spec["adaptive"], spec["seed"],
+                         certified=bool(spec.get("certified", False)))
         out["build_s"] = time.perf_counter() - t0
         out["samples"] = int(res.samples - res.norm_its)
         if spec.get("dump"):
@@ -874,7 +922,7 @@ def run_reference(args) -> None:
     op = O.HeatHessian(p.n, p.kappa, p.T, p.sigma, mask)
     t0 = time.perf_counter()
     h, res = O.build(op, W.grid_coords(p.n), b.leaf, b.adm, b.eta, b.tol, b.kmax, b.q0, b.b_inc, b.q_max,
-                     b.adaptive, b.seed)
+                     b.adaptive, b.seed, certified=HEADLINE_CERTIFIED)
     build_s = time.perf_counter() - t0
     ent = O.storage_entries(h)
     st = {"entries_D": ent["D"], "entries_S": ent["S"], "entries_U": ent["U"], "entries_E": ent["E"]}
@@ -927,6 +975,7 @@ def config_of(cfg: dict) -> dict:
     p, b = cfg["problem"], cfg["build"]
     return {"workload": cfg["name"], "N": p.N, "grid": f"{p.n}x{p.n}", "sensors": p.m, "kappa": p.kappa,
             "leaf": b.leaf, "adm": "strong", "eta": b.eta, "kmax": b.kmax, "tol": b.tol,
+            "range_bases": "certified" if HEADLINE_CERTIFIED else "all probes",
             "nrhs": list(cfg["nrhs"]), "mode": "FP64",
             "l2": "H2 factors larger than L2 (no flush needed)", "parallelism": "replicas"}
 
@@ -947,6 +996,7 @@ def main():
     ap.add_argument("--no-sampling", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-advdiff", action="store_true")
+    ap.add_argument("--no-certified", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="grid size of the stepped Hessian (profiling captures on smaller cases; bench lines use the default)")
     ap.add_argument("--precision-n", type=int, default=512, help="grid size of the precision section")
@@ -990,7 +1040,7 @@ def main():
     tree = h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta)
     stream = torch.cuda.current_stream()
     opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
-                           seed=b.seed, stream=stream)
+                           seed=b.seed, stream=stream, certified=int(HEADLINE_CERTIFIED))
     nrhs_list = list(CFG["nrhs"])
     Xd = {nr: torch.from_numpy(np.ascontiguousarray(W.rhs(N, nr, CFG["rhs_seed"] + nr).T)).cuda()
           for nr in nrhs_list}
@@ -1188,6 +1238,10 @@ def main():
     if rank == 0 and not args.no_update:
         update = update_section(h2, torch, stream, Gp2, N, float(np.mean(build_ms)) / 1e3)
 
+    certified = None
+    if rank == 0 and not args.no_certified:
+        certified = certified_section(h2, torch, stream)
+
     inversion = None
     if rank == 0 and not args.no_inversion:
         inversion = inversion_section(h2, torch, stream)
@@ -1231,6 +1285,8 @@ def main():
             line["sampling_structure"] = sampling
         if small is not None:
             line["small_n32"] = small
+        if certified is not None:
+            line["certified_bases"] = certified
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -133,6 +133,13 @@ typedef struct {
     /* h2_build_batched only: host worker threads, each with its own stream (0: min(count, 8)); the
      * per-level launches of different Hessians overlap on the GPU across workers. */
     int batch_workers;
+    /* Certified range bases (weak sampling structure; Section 3.3's adaptive range finder in the
+     * textbook form of Halko, Martinsson and Tropp, Algorithm 4.2): 1 keeps the columns of the
+     * range test that passes out of the level's bases, since that test certifies the basis it
+     * was run against; the projection pass and the recompression then work with need columns
+     * (h2_build_stats.range_need) instead of every range probe drawn.  0 (default): the bases
+     * span every range probe, the passing test's columns included.  Only 0 or 1. */
+    int certified;
 } h2_build_opts;
 
 enum { H2_SAMPLING_WEAK = 0, H2_SAMPLING_COLORED = 1 };

@@ -18,13 +18,14 @@ from .update import compress_dense, far_columns, lowrank_update
 
 
 def build(op, coords, leaf, adm, eta, tol, kmax, q0, b_inc, q_max, adaptive, seed, norm_est=None,
-          q_level=None, q_test=8, global_rank=0, ranks=None, q_exact=None):
+          q_level=None, q_test=8, global_rank=0, ranks=None, q_exact=None, certified=False):
     """Full construction: tree, partition, peeling, assembly.  Returns (h2, peel_result).
-    ranks, q_exact: optional basis ranks and range-probe counts to replay (see assemble, peel)."""
+    ranks, q_exact: optional basis ranks and range-probe counts to replay (see assemble, peel).
+    certified: range bases without the passing test's columns (see peel)."""
     tree = ClusterTree(coords, leaf)
     part = Partition(tree, adm, eta)
     res = peel(op, tree, tol, q0, b_inc, q_max, adaptive, seed, norm_est=norm_est, q_level=q_level,
-               q_test=q_test, global_rank=global_rank, q_exact=q_exact)
+               q_test=q_test, global_rank=global_rank, q_exact=q_exact, certified=certified)
     res.tau_basis = basis_threshold(tol, res.norm_est, 1 << tree.L)
     h = assemble(tree, part, res, res.tau_basis, kmax, ranks=ranks)
     return h, res

@@ -21,6 +21,12 @@ the paper's implementation uses:
   until the new columns' residuals (I - Q Q^T) y are all below
   tau / (10 sqrt(2/pi)) (the a-posteriori range test of the randomized
   range finder, halko11, cited in Section 3.3).
+* Certified basis (option `certified`): the test columns of the test that passes
+  are not added to Q_b.  The passing test certifies the basis it was run against
+  (the adaptive range finder in its textbook form, halko11 Algorithm 4.2: test
+  vectors join the basis only while the test fails), so the projection pass and
+  every later step use that basis; with certified=False (the default) Q_b spans
+  every range probe drawn, the passing test columns included.
 * If a level's boxes are no larger than the probe count, the range of H[b, a]
   is the whole of R^|b| and Q_b = I (no range pass is spent).
 * Finally identity probes on every leaf give the dense diagonal leaf blocks,
@@ -218,14 +224,15 @@ class PeelResult:
 
 def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, adaptive: bool,
          seed: int, norm_est: float | None = None, q_level=None, q_test: int = 8,
-         global_rank: int = 0, q_exact=None) -> PeelResult:
+         global_rank: int = 0, q_exact=None, certified: bool = False) -> PeelResult:
     """Construct the sibling pieces and the leaf diagonal blocks from products with op.
 
     q_level: optional sequence indexed by level (entries <= 0 mean q0) of start counts.
     global_rank: budget of the global low-rank piece (0: none).
     q_exact (replay of another run's decisions): sequence indexed by level; level l draws
     exactly q_exact[l] range probes without any test, and takes the identity range when
-    q_exact[l] == 0.  Overrides q0, q_level and adaptive."""
+    q_exact[l] == 0.  Overrides q0, q_level and adaptive.
+    certified: the passing test's columns stay out of the basis (see the module notes)."""
     N = tree.N
     opt = TreeOperator(op, tree)
     res = PeelResult()
@@ -307,12 +314,15 @@ def peel(op, tree: ClusterTree, tol: float, q0: int, b_inc: int, q_max: int, ada
                     else:
                         r = yb - Qs[i] @ (Qs[i].T @ yb)
                         errs.append(float(np.linalg.norm(r, axis=0).max()))
-                    Ys[i] = np.hstack([Ys[i], yb])
-                    Qs[i] = range_basis(Ys[i])
                 res.test_err[l].append(errs)
                 res.need[l] = q
                 q += c
-                if max(errs) <= thr:
+                ok = max(errs) <= thr
+                if not (ok and certified):
+                    for i, b in enumerate(B):
+                        Ys[i] = np.hstack([Ys[i], Yn[b]])
+                        Qs[i] = range_basis(Ys[i])
+                if ok:
                     res.passed[l] = 1
                     break
             if res.passed[l] != 1:

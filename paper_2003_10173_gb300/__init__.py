@@ -51,6 +51,7 @@ class BuildOpts(ctypes.Structure):
         ("keep_bf16", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("q_level", ctypes.c_void_p), ("q_level_stride", ctypes.c_int), ("q_test", ctypes.c_int),
         ("global_rank", ctypes.c_int), ("sampling", ctypes.c_int), ("batch_workers", ctypes.c_int),
+        ("certified", ctypes.c_int),
     ]
 
 

@@ -377,6 +377,8 @@ void Builder::peel_level(int l) {
             tp.insert(tp.end(), full.begin(), full.end());
             project(l, tp, c, off, 2);
             for (double e : colnorm(l, tp, c, off)) err = std::max(err, e);
+            // certified bases: a passing test's columns stay out of the basis it certified
+            if (o_.certified && err <= thr) return err;
         }
         identity(l, full);
         for (int c0 = 0; c0 < c; c0 += PANEL) {

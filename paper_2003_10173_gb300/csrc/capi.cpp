@@ -94,6 +94,7 @@ h2_build_opts checked_opts(double tol, const h2_build_opts* opts) {
     require(o.global_rank >= 0, "h2_build: global_rank must be >= 0");
     require(o.batch_workers >= 0 && o.batch_workers <= 256, "h2_build: batch_workers must be in 0..256");
     require(o.sampling == H2_SAMPLING_WEAK || o.sampling == H2_SAMPLING_COLORED, "h2_build: unknown sampling");
+    require(o.certified == 0 || o.certified == 1, "h2_build: certified must be 0 or 1");
     require(o.sampling != H2_SAMPLING_COLORED || (o.q0 <= 16 && o.global_rank == 0),
             "h2_build: coloured sampling needs q0 <= 16 and global_rank 0");
     require(o.norm_maxit >= 1 && o.norm_rtol > 0.0, "h2_build: bad power-iteration settings");

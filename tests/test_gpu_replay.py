@@ -136,3 +136,41 @@ def test_tight_tolerance_heat32(h2):
     print(f"heat 32^2, tol 1e-9: ||H - H2_gpu||_2 / ||H||_2 = {err:.2e}")
     assert G.stats()["tol_met"] == 1
     assert err <= 1e-9
+
+
+@pytest.mark.parametrize("n,m,sseed,leaf,q0,bound", [(32, 200, 17, 32, 16, 1e-12), (64, 256, 1002, 64, 32, 2e-11)])
+def test_certified_bases_parity(h2, n, m, sseed, leaf, q0, bound):
+    """Certified range bases (the passing test's columns left out): the GPU takes the oracle's
+    decisions (range and projection probes per level), and with its decisions replayed -- the
+    certified basis sizes as the probe counts, since the probes are indexed by column -- the two
+    H^2 matrices agree to the replay bounds above; the construction meets the tolerance with
+    fewer products than the default bases."""
+    N, kappa, tol = n * n, 0.01, 1e-6
+    mask = W.sensor_mask(N, m, sseed)
+    gop = h2.HeatOperator(n, kappa, 0.5, 0.01, mask)
+    tree = h2.Tree(W.grid_coords(n), leaf, ADM_STRONG, 0.7)
+    mk = lambda c: h2.default_opts(kmax=32, q0=q0, b_inc=16, q_max=256, seed=7, certified=c)
+    G = h2.H2.build(gop, tree, tol, mk(1))
+    st = G.stats()
+    L = st["levels"]
+    G0 = h2.H2.build(gop, tree, tol, mk(0))
+    op = O.HeatHessian(n, kappa, 0.5, 0.01, mask)
+    _, r0 = O.build(op, W.grid_coords(n), leaf, ADM_STRONG, 0.7, tol, 32, q0, 16, 256, True, 7,
+                    norm_est=st["norm_est"], certified=True)
+    for l in range(1, L + 1):
+        assert st["range_probes"][l] == r0.range_probes[l]
+        assert st["proj_probes"][l] == r0.proj_probes[l]
+    assert st["samples"] < G0.stats()["samples"]
+    ranks = split_ranks(G.export()[0], L)
+    probes = [0 if st["range_probes"][l] == 0 else st["proj_probes"][l] for l in range(L + 1)]
+    ho, _ = O.replay_build(op, W.grid_coords(n), leaf, ADM_STRONG, 0.7, tol, 32, 7, st["norm_est"], probes, ranks)
+    for l in range(L + 1):
+        np.testing.assert_array_equal(ho.k[l], ranks[l])
+    A_gpu = gpu_dense(h2, G, N)
+    d = np.linalg.norm(A_gpu - O.expand_dense(ho), 2) / st["norm_est"]
+    H = op(np.eye(N))
+    err = np.linalg.norm(A_gpu - H, 2) / np.linalg.norm(H, 2)
+    print(f"certified {n}^2: products {st['samples']} (default {G0.stats()['samples']}), "
+          f"||H2_gpu - H2_oracle|| / ||H|| = {d:.1e} (replayed), error {err:.1e}")
+    assert d <= bound
+    assert err <= tol
