@@ -1142,8 +1142,10 @@ def main():
                            "algorithmic_bytes_per_launch": gemm_bytes / max(gemm_n, 1),
                            "traffic_note": "per-launch DRAM bytes vary with the problem list; sampled launches "
                                            "in profiles/gemm_tiles_n128_n256.md"}
-    # the recompression's stacked Householder QR and truncated SVD (FP64-pipe bound), timed per
-    # launch with events over the timed steps; flops are those of their QR factorisations only
+    # the recompression's stacked Householder QR and truncated SVD (FP64-pipe bound), timed with
+    # events over the timed steps (the stacked QR per pass: its width classes run concurrently on
+    # side streams, one span from the fork to the join); flops are those of their QR
+    # factorisations only
     roofline_build_stacked = {}
     for name, (ms, fl, n) in zip(("stacked_r_kernel", "stacked_svd_kernel"), stack_prof):
         tf = fl / (ms / 1e3) / 1e12 if ms > 0 else None

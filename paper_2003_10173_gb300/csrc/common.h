@@ -262,6 +262,15 @@ struct StackWork {
     DevBuf<RowSeg> d_segs, d_segs2;
     DevBuf<double> parts;
     Stager st_jobs, st_jobs2, st_segs, st_segs2;
+    // side streams of the width classes of one stacked_r pass (created on first use), so that
+    // the classes' launches overlap instead of each waiting for the previous one's tail
+    cudaStream_t side[5] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[5] = {};
+    StackWork() = default;
+    StackWork(const StackWork&) = delete;
+    StackWork& operator=(const StackWork&) = delete;
+    ~StackWork();
 };
 // R factors (Householder) of every job's stacked matrix (c <= 144 columns; any row count:
 // matrices above a few thousand rows are split over several CTAs).  The stacked matrices must

@@ -586,15 +586,16 @@ double job_rows(const StackJob& j, const std::vector<RowSeg>& segs) {
     return r;
 }
 
-// Records the start event of a profiled launch; returns it (null when profiling is off).
-cudaEvent_t prof_begin(int which, double flops, cudaStream_t s) {
+// Records the start event of a profiled span of `launches` kernel launches (timed from this
+// event on s to the one prof_end records on s); returns it (null when profiling is off).
+cudaEvent_t prof_begin(int which, double flops, cudaStream_t s, int launches = 1) {
     if (!gemm_profile_on()) return nullptr;
     StackProfile& P = g_sprof[which];
     std::lock_guard<std::mutex> lock(P.mu);
     cudaEvent_t e = P.take();
     H2_CUDA(cudaEventRecord(e, s));
     P.flops += flops;
-    P.launches += 1;
+    P.launches += launches;
     return e;
 }
 
@@ -685,31 +686,63 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     // shared-memory occupancy of the widest; the working matrix's size is not monotone in c (the
     // chunk height steps down at 49, 97 and 129 columns), so a launch takes the largest
     // requirement of its jobs
-    auto launch1 = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
-                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
-        if (js.empty()) return;
-        size_t dyn = 16;
-        for (auto& j : js) dyn = std::max(dyn, qr_smem_bytes(j.c));
-        upload(dj, js, s, stj);
-        upload(dsg, ss, s, sts);
-        double fl = 0.0;
-        if (gemm_profile_on())
-            for (auto& j : js) fl += qr_flops(job_rows(j, ss), j.c);
-        cudaEvent_t ev = prof_begin(0, fl, s);
-        stacked_r_kernel<<<(unsigned)js.size(), QR_NT, dyn, s>>>(dj.p, (int)js.size(), dsg.p);
-        after_launch("stacked_r");
-        prof_end(0, ev, s);
-    };
+    // One launch per width class, each on its own side stream after the jobs are uploaded, so
+    // that the classes overlap; within a class the jobs run longest first (CTAs start in job
+    // order, so the launch's tail holds the short ones).
     auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
         constexpr int kBounds[] = {48, 64, 96, 128, kSmemMaxC};
-        std::vector<StackJob> cls[5];
-        for (const StackJob& j : js) {
+        std::vector<std::pair<double, int>> cls[5];
+        for (int i = 0; i < (int)js.size(); ++i) {
+            const StackJob& j = js[i];
             int b = 0;
             while (j.c > kBounds[b]) ++b;
-            cls[b].push_back(j);
+            cls[b].push_back({job_rows(j, ss) * j.c * j.c, i});
         }
-        for (auto& v : cls) launch1(v, ss, dj, dsg, stj, sts);
+        std::vector<StackJob> all;
+        int off[6], nonempty = 0;
+        for (int b = 0; b < 5; ++b) {
+            std::stable_sort(cls[b].begin(), cls[b].end(),
+                             [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+            off[b] = (int)all.size();
+            for (auto& ci : cls[b]) all.push_back(js[ci.second]);
+            nonempty += cls[b].empty() ? 0 : 1;
+        }
+        off[5] = (int)all.size();
+        if (all.empty()) return;
+        upload(dj, all, s, stj);
+        upload(dsg, ss, s, sts);
+        // profiling: one span on s around all the classes' launches (they overlap)
+        double fl = 0.0;
+        if (gemm_profile_on())
+            for (auto& j : all) fl += qr_flops(job_rows(j, ss), j.c);
+        cudaEvent_t ev = prof_begin(0, fl, s, nonempty);
+        const bool fork = nonempty > 1;
+        if (fork) {
+            if (!w.ev_fork) {
+                H2_CUDA(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
+                for (int b = 0; b < 5; ++b) {
+                    H2_CUDA(cudaStreamCreateWithFlags(&w.side[b], cudaStreamNonBlocking));
+                    H2_CUDA(cudaEventCreateWithFlags(&w.ev_join[b], cudaEventDisableTiming));
+                }
+            }
+            H2_CUDA(cudaEventRecord(w.ev_fork, s));
+        }
+        for (int b = 0; b < 5; ++b) {
+            const int n = off[b + 1] - off[b];
+            if (!n) continue;
+            cudaStream_t sb = fork ? w.side[b] : s;
+            if (fork) H2_CUDA(cudaStreamWaitEvent(sb, w.ev_fork, 0));
+            size_t dyn = 16;
+            for (int i = off[b]; i < off[b + 1]; ++i) dyn = std::max(dyn, qr_smem_bytes(all[i].c));
+            stacked_r_kernel<<<(unsigned)n, QR_NT, dyn, sb>>>(dj.p + off[b], n, dsg.p);
+            after_launch("stacked_r");
+            if (fork) {
+                H2_CUDA(cudaEventRecord(w.ev_join[b], sb));
+                H2_CUDA(cudaStreamWaitEvent(s, w.ev_join[b], 0));
+            }
+        }
+        prof_end(0, ev, s);
     };
     if (!parts.empty()) {
         int64_t elems = 0;
@@ -735,9 +768,29 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     launch(jobs, segs, w.d_jobs, w.d_segs, w.st_jobs, w.st_segs);
 }
 
-void stacked_svd_trunc(const std::vector<StackJob>& jobs, const std::vector<RowSeg>& segs, StackWork& w, double thr,
-                       int kmax, int* d_cap_flag, cudaStream_t s) {
-    if (jobs.empty()) return;
+StackWork::~StackWork() {
+    // teardown: errors are ignored (the context may already be gone at process exit)
+    for (int b = 0; b < 5; ++b) {
+        if (side[b]) cudaStreamDestroy(side[b]);
+        if (ev_join[b]) cudaEventDestroy(ev_join[b]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+}
+
+void stacked_svd_trunc(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& segs, StackWork& w,
+                       double thr, int kmax, int* d_cap_flag, cudaStream_t s) {
+    if (jobs_in.empty()) return;
+    // longest first (QR of the stack plus the Jacobi sweeps): CTAs start in job order
+    std::vector<std::pair<double, int>> cost;
+    for (int i = 0; i < (int)jobs_in.size(); ++i) {
+        const double c = jobs_in[i].c;
+        cost.push_back({job_rows(jobs_in[i], segs) * c * c + 4.0 * c * c * c, i});
+    }
+    std::stable_sort(cost.begin(), cost.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+    std::vector<StackJob> jobs;
+    jobs.reserve(jobs_in.size());
+    for (auto& ci : cost) jobs.push_back(jobs_in[ci.second]);
     int cm = 0;
     for (auto& j : jobs) cm = std::max(cm, j.c);
     if (cm > SVD_MAXC) fail(H2_ERR_INVALID_ARG, "stacked_svd: matrix order above 96");
