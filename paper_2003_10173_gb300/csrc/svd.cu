@@ -402,7 +402,8 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
     __shared__ double sig[SVD_MAXC + 1];
     __shared__ int rank[SVD_MAXC];
     __shared__ int perm[SVD_MAXC];
-    __shared__ int kk;
+    __shared__ int cols[SVD_MAXC + 2];
+    __shared__ int kk, mcols;
     const StackJob jb = jobs[blockIdx.x];
     const int c = jb.c;
     if (c <= 0) {
@@ -451,22 +452,34 @@ __global__ void __launch_bounds__(SQ_NT) stacked_svd_kernel(const StackJob* __re
         const int i = x % c, k = x / c;
         if (sig[k] <= floor2) B[i + (int64_t)k * ldb] = 0.0;
     }
+    // the sweeps run over the columns above the floor only (a rotation against a zero column is
+    // the identity), padded to an even count with a zero column, which exists since np is even
+    if (threadIdx.x == 0) {
+        int m = 0, z = -1;
+        for (int j = 0; j < np; ++j) {
+            if (sig[j] > floor2) cols[m++] = j;
+            else if (z < 0) z = j;
+        }
+        if (m & 1) cols[m++] = z;
+        mcols = m;
+    }
     __syncthreads();
     // one-sided Jacobi on the columns of B = R^T (W = B Q^T): 8 threads per column pair,
     // 32 pairs at a time; at convergence the columns of B V are orthogonal and their
     // normalised values are the left singular vectors of W
-    const int half = np / 2;
+    const int mp = mcols;
+    const int half = mp / 2;
     const double tol = 2.0 * (double)c * DBL_EPSILON;   // orthogonality reached (rounding of the dot products)
-    for (int sweep = 0; sweep < 60; ++sweep) {
+    for (int sweep = 0; sweep < 60 && mp > 0; ++sweep) {
         int rotated = 0;
-        for (int r = 0; r < np - 1; ++r) {
+        for (int r = 0; r < mp - 1; ++r) {
             for (int k0 = 0; k0 < half; k0 += 32) {
                 const int k = k0 + g;
                 const bool act = k < half;
                 int p = 0, q = 0;
-                if (act) {
-                    if (k == 0) { p = np - 1; q = r; }
-                    else { p = (r + k) % (np - 1); q = (r - k + (np - 1)) % (np - 1); }
+                if (act) {   // round-robin pair k of round r over the listed columns
+                    if (k == 0) { p = cols[mp - 1]; q = cols[r]; }
+                    else { p = cols[(r + k) % (mp - 1)]; q = cols[(r - k + (mp - 1)) % (mp - 1)]; }
                     if (p > q) { const int t = p; p = q; q = t; }
                 }
                 double al = 0.0, be = 0.0, ga = 0.0;
