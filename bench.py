@@ -257,21 +257,22 @@ def batching_section(h2, torch, stream) -> dict:
     """64 heat Hessians of uneven sizes (n ~ U{64..256}, kappa ~ U[0.002, 0.05], 5-20 % sensors):
     batched FP64 construction and the merged, autotuned, graph-captured FP32 matvec with
     nrhs = 64, against the plain FP64 form (one h2_build and one FP64 h2_matvec per Hessian);
-    the batched tensor-core forms in TF32 and split TF32 (FP32-grade) beside it."""
+    the batched tensor-core forms in TF32 and split TF32 (FP32-grade) beside it.  Both
+    constructions use the stepped construction's range bases (certified or not)."""
     probs = W.batch_problems(64)
     b = CFG["build"]
     nrhs = 64
     ops = [h2.HeatOperator(p.n, p.kappa, p.T, p.sigma, W.sensor_mask(p.N, p.m, p.sensor_seed)) for p in probs]
     trees = [h2.Tree(W.grid_coords(p.n), b.leaf, b.adm, b.eta) for p in probs]
     opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
-                           seed=b.seed, keep_fp32=1)
+                           seed=b.seed, keep_fp32=1, certified=int(HEADLINE_CERTIFIED))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Gs = h2.build_batched(ops, trees, b.tol, opts)
     torch.cuda.synchronize()
     t_batched = time.perf_counter() - t0
     plain_opts = h2.default_opts(kmax=b.kmax, q0=b.q0, b_inc=b.b_inc, q_max=b.q_max, adaptive=int(b.adaptive),
-                                 seed=b.seed, stream=stream)
+                                 seed=b.seed, stream=stream, certified=int(HEADLINE_CERTIFIED))
     t0 = time.perf_counter()
     plain = [h2.H2.build(op, t, b.tol, plain_opts) for op, t in zip(ops, trees)]
     torch.cuda.synchronize()
@@ -326,6 +327,7 @@ def batching_section(h2, torch, stream) -> dict:
     by64 = sum(matvec_bytes(G.stats(), p.N, nrhs, 8) for G, p in zip(plain, probs))
     hbm = peaks()[0]
     out = {"workload": "heat2d_batch64_n64-256", "hessians": len(probs), "N_total": sum(p.N for p in probs),
+           "range_bases": "certified" if HEADLINE_CERTIFIED else "all probes",
            "nrhs": nrhs, "build_batched_s": t_batched, "build_plain_fp64_s": t_plain,
            "build_speedup": t_plain / t_batched,
            "matvec_batched_fp32_ms": t_bmv, "matvec_plain_fp64_ms": t_pmv, "matvec_speedup": t_pmv / t_bmv,
