@@ -706,31 +706,30 @@ void run_small(h2_handle_s* h, const TS* fac, TA* ws, const TX* X, int64_t ldx, 
     H2_CUDA(cudaMemset2DAsync(Y, ldy * sizeof(TY), 0, h->N * sizeof(TY), nrhs, s));
     if (wld > P.yh_row0)
         H2_CUDA(cudaMemset2DAsync(ws + P.yh_row0, wld * sizeof(TA), 0, (wld - P.yh_row0) * sizeof(TA), nrhs, s));
-    // The near field (the bulk of the arithmetic, independent of the coefficient sweeps) runs on a
-    // second stream beside the latency-bound chain of tree stages; both add into Y atomically.
-    // Profiled calls keep one stream so that every stage is timed on its own.
+    // The near field (the bulk of the arithmetic, independent of the coefficient sweeps) runs
+    // beside the latency-bound chain of tree stages; both add into Y atomically.  The chain goes
+    // to a second stream of the highest priority, so that each of its small launches takes SMs
+    // ahead of the near field's remaining CTAs instead of queueing behind them; the near field
+    // stays on the caller's stream.  Profiled calls keep one stream so that every stage is timed
+    // on its own.
     const bool overlap = may_fork && !prof && !P.near.items.empty();
+    cudaStream_t cs = s;   // the chain's stream
     if (overlap) {
-        if (!h->side) {
-            H2_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-            H2_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-            H2_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        }
+        if (!h->side) fail(H2_ERR_CUDA, "matvec: the handle's second stream is missing");
         H2_CUDA(cudaEventRecord(h->ev_fork, s));
         H2_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, h->side);
-        H2_CUDA(cudaEventRecord(h->ev_join, h->side));
-    } else {
-        timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+        cs = h->side;
     }
     for (const MvStage& st : P.small_up)
-        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
-    timed(H2_STAGE_COUPLE, [&] { launch_scatter<TS, TX, TY, TA>(P.couple, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, cs); });
+    timed(H2_STAGE_COUPLE, [&] { launch_scatter<TS, TX, TY, TA>(P.couple, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, cs); });
     for (const MvStage& st : P.small_down)
-        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
+        timed(st.kind, [&] { launch_small_stage<TS, TX, TY, TA>(st, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, cs); });
     timed(H2_STAGE_LEAF_NEAR, [&] {
-        launch_small_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s);
+        launch_small_stage<TS, TX, TY, TA>(P.small_expand, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, cs);
     });
+    if (overlap) H2_CUDA(cudaEventRecord(h->ev_join, cs));
+    timed(H2_STAGE_NEAR, [&] { launch_scatter<TS, TX, TY, TA>(P.near, fac, ws, wld, h->d_perm.p, X, ldx, Y, ldy, nrhs, s); });
     if (overlap) H2_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
 }
 
@@ -995,9 +994,12 @@ void build_plan(h2_handle_s* h, cudaStream_t s) {
     // the FP64 coefficient workspace for up to kReserveNrhs right-hand sides is reserved with the
     // handle, so that a first h2_matvec with few right-hand sides does not allocate
     h->ws.f64.reserve((size_t)P.ws_rows * kReserveNrhs);
-    // the second stream of the small-nrhs matvec and its events, created with the handle
+    // the second stream of the small-nrhs matvec (highest priority: it carries the tree-stage
+    // chain beside the near field) and its events, created with the handle
     if (!h->side) {
-        H2_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        H2_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        H2_CUDA(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
         H2_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         H2_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     }
@@ -1336,7 +1338,8 @@ void run_matvec(h2_handle_s* h, const void* X, int64_t ldx, void* Y, int64_t ldy
             throw;
         }
         H2_CUDA(cudaStreamEndCapture(h->cap, &g->graph));
-        H2_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+        // node priorities kept: the small-nrhs chain's launches come from its high-priority stream
+        H2_CUDA(cudaGraphInstantiate(&g->exec, g->graph, cudaGraphInstantiateFlagUseNodePriority));
         g->launches = g_launches.load() - l0;
         g_launches.fetch_sub(g->launches);   // counted again at every replay
     }
