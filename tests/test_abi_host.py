@@ -93,6 +93,33 @@ def test_argument_validation(h2):
     o = h2.default_opts()
     assert (o.kmax, o.q0, o.b_inc, o.q_max, o.adaptive) == (32, 32, 16, 256, 1)
     assert (o.q_level, o.q_level_stride, o.q_test, o.global_rank) == (None, 0, 8, 0)
+    assert (o.sampling, o.batch_workers, o.certified) == (0, 0, 0)
+
+
+def test_build_option_validation(h2):
+    """Build options are checked before any device work: every bad value is rejected with
+    H2_ERR_INVALID_ARG and a message naming it (no GPU needed)."""
+    L = h2.lib()
+    coords = W.grid_coords(8)
+    tree = ctypes.c_void_p()
+    assert L.h2_tree_create(coords.ctypes.data, 64, 2, 16, 1, 0.7, ctypes.byref(tree)) == 0
+    never = h2.OP_FN(lambda *a: 1)   # not called: validation fails first
+    cases = [(dict(certified=2), b"certified"), (dict(sampling=5), b"sampling"),
+             (dict(batch_workers=-1), b"batch_workers"), (dict(b_inc=17), b"b_inc"),
+             (dict(q_test=0), b"q_test"), (dict(kmax=0), b"kmax"),
+             (dict(sampling=h2.H2_SAMPLING_COLORED, q0=32), b"coloured")]
+    try:
+        for kw, word in cases:
+            o = h2.default_opts(**kw)
+            out = ctypes.c_void_p()
+            st = L.h2_build(never, None, tree, 1e-6, ctypes.byref(o), ctypes.byref(out))
+            assert st == h2.H2_ERR_INVALID_ARG, kw
+            assert word in L.h2_last_error(), (kw, L.h2_last_error())
+            assert not out.value
+        out = ctypes.c_void_p()
+        assert L.h2_build(never, None, tree, -1.0, None, ctypes.byref(out)) == h2.H2_ERR_INVALID_ARG
+    finally:
+        L.h2_tree_free(tree)
 
 
 @pytest.mark.parametrize("n,leaf,adm", [(4, 4, ADM_WEAK), (37, 16, ADM_STRONG), (64, 64, ADM_STRONG)])
