@@ -192,3 +192,24 @@ def test_batched_matvec_matches_oracle(oracle_batch, mode, nrhs):
         assert_elementwise(Y.double().cpu().numpy().T, want, leaf_index_sets(ho.tree),
                            1e-12 if mode == h2.H2_FP64 else 1e-5, f"n={p.n}")
     B.close()
+
+
+def test_batched_certified_build_equals_individual_builds(setup):
+    """Certified range bases through the batched construction: each Hessian equals its own
+    certified construction, and spends fewer products than with the default bases."""
+    h2, probs, ops, trees, batched, single = setup
+    opts = h2.default_opts(kmax=32, q0=32, b_inc=16, q_max=128, adaptive=1, seed=3, certified=1)
+    cb = h2.build_batched(ops, trees, 1e-6, opts)
+    cs = [h2.H2.build(op, t, 1e-6, opts) for op, t in zip(ops, trees)]
+    fewer = 0
+    for b, s, d in zip(cb, cs, single):
+        sb, ss = b.stats(), s.stats()
+        for k in ("samples", "range_probes", "proj_probes", "max_rank", "entries_D", "entries_S"):
+            assert sb[k] == ss[k], k
+        for xb, xs in zip(b.export(), s.export()):
+            np.testing.assert_array_equal(xb, xs)
+        assert sb["samples"] <= d.stats()["samples"]
+        fewer += sb["samples"] < d.stats()["samples"]
+    assert fewer > 0
+    for G in cb + cs:
+        G.close()
