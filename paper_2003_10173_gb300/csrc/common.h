@@ -264,9 +264,10 @@ struct StackWork {
     Stager st_jobs, st_jobs2, st_segs, st_segs2;
     // side streams of the width classes of one stacked_r pass (created on first use), so that
     // the classes' launches overlap instead of each waiting for the previous one's tail
-    cudaStream_t side[5] = {};
+    static constexpr int kClasses = 6;
+    cudaStream_t side[kClasses] = {};
     cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[5] = {};
+    cudaEvent_t ev_join[kClasses] = {};
     StackWork() = default;
     StackWork(const StackWork&) = delete;
     StackWork& operator=(const StackWork&) = delete;

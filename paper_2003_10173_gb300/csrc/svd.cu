@@ -43,7 +43,11 @@ constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kSmemMaxC = 144;     // widest matrix of stacked_r (its working matrix in shared memory)
 
 // rows of a chunk streamed under R: shared memory holds (c + chunk) x c doubles
-__host__ __device__ inline int chunk_rows(int c) { return c <= 48 ? 112 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)); }
+__host__ __device__ inline int chunk_rows(int c) {
+    return c <= 32 ? 224 : (c <= 48 ? 112 : (c <= 96 ? 64 : (c <= 128 ? 32 : 16)));
+}
+constexpr int kMaxChunk = 224;   // the largest chunk_rows
+constexpr int kStackClasses = StackWork::kClasses;   // width classes of a stacked_r pass
 // chunk height of the SVD kernel: fixed, so that its shared memory grows with c (one launch per level)
 constexpr int kSvdChunk = 64;
 // leading dimension of the working matrix [R; chunk]: odd, so that the columns of a warp's
@@ -78,8 +82,8 @@ __device__ inline void householder(double* A, int lda, int j, double x2, double*
 template <int NT>
 __device__ void stacked_qr(double* A, int lda, int c, int ch, const RowSeg* __restrict__ segs, int b, int e,
                            double* tau) {
-    __shared__ const double* rp[128];
-    __shared__ int rld[128];
+    __shared__ const double* rp[kMaxChunk];
+    __shared__ int rld[kMaxChunk];
     __shared__ int nact[kSmemMaxC + 1];   // chunk rows whose first nonzero column is <= j
     __shared__ int hs, j0s;
     __shared__ int wf, ws, wo, anytri;    // walk over the stack: level, segment, row offset
@@ -695,17 +699,17 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
     std::call_once(attr, [&] {
         H2_CUDA(cudaFuncSetAttribute(stacked_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
     });
-    // one launch per class of c (<= 48, 64, 96, 128, 144), so that narrow jobs are not held to the
-    // shared-memory occupancy of the widest; the working matrix's size is not monotone in c (the
-    // chunk height steps down at 49, 97 and 129 columns), so a launch takes the largest
+    // one launch per class of c (<= 32, 48, 64, 96, 128, 144), so that narrow jobs are not held to
+    // the shared-memory occupancy of the widest; the working matrix's size is not monotone in c
+    // (the chunk height steps down at 33, 49, 97 and 129 columns), so a launch takes the largest
     // requirement of its jobs
     // One launch per width class, each on its own side stream after the jobs are uploaded, so
     // that the classes overlap; within a class the jobs run longest first (CTAs start in job
     // order, so the launch's tail holds the short ones).
     auto launch = [&](const std::vector<StackJob>& js, const std::vector<RowSeg>& ss, DevBuf<StackJob>& dj,
                       DevBuf<RowSeg>& dsg, Stager& stj, Stager& sts) {
-        constexpr int kBounds[] = {48, 64, 96, 128, kSmemMaxC};
-        std::vector<std::pair<double, int>> cls[5];
+        constexpr int kBounds[kStackClasses] = {32, 48, 64, 96, 128, kSmemMaxC};
+        std::vector<std::pair<double, int>> cls[kStackClasses];
         for (int i = 0; i < (int)js.size(); ++i) {
             const StackJob& j = js[i];
             int b = 0;
@@ -713,15 +717,15 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
             cls[b].push_back({job_rows(j, ss) * j.c * j.c, i});
         }
         std::vector<StackJob> all;
-        int off[6], nonempty = 0;
-        for (int b = 0; b < 5; ++b) {
+        int off[kStackClasses + 1], nonempty = 0;
+        for (int b = 0; b < kStackClasses; ++b) {
             std::stable_sort(cls[b].begin(), cls[b].end(),
                              [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
             off[b] = (int)all.size();
             for (auto& ci : cls[b]) all.push_back(js[ci.second]);
             nonempty += cls[b].empty() ? 0 : 1;
         }
-        off[5] = (int)all.size();
+        off[kStackClasses] = (int)all.size();
         if (all.empty()) return;
         upload(dj, all, s, stj);
         upload(dsg, ss, s, sts);
@@ -734,14 +738,14 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
         if (fork) {
             if (!w.ev_fork) {
                 H2_CUDA(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
-                for (int b = 0; b < 5; ++b) {
+                for (int b = 0; b < kStackClasses; ++b) {
                     H2_CUDA(cudaStreamCreateWithFlags(&w.side[b], cudaStreamNonBlocking));
                     H2_CUDA(cudaEventCreateWithFlags(&w.ev_join[b], cudaEventDisableTiming));
                 }
             }
             H2_CUDA(cudaEventRecord(w.ev_fork, s));
         }
-        for (int b = 0; b < 5; ++b) {
+        for (int b = 0; b < kStackClasses; ++b) {
             const int n = off[b + 1] - off[b];
             if (!n) continue;
             cudaStream_t sb = fork ? w.side[b] : s;
@@ -783,7 +787,7 @@ void stacked_r(const std::vector<StackJob>& jobs_in, const std::vector<RowSeg>& 
 
 StackWork::~StackWork() {
     // teardown: errors are ignored (the context may already be gone at process exit)
-    for (int b = 0; b < 5; ++b) {
+    for (int b = 0; b < kStackClasses; ++b) {
         if (side[b]) cudaStreamDestroy(side[b]);
         if (ev_join[b]) cudaEventDestroy(ev_join[b]);
     }
