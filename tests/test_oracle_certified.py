@@ -92,3 +92,28 @@ def test_certified_replay_reproduces():
         np.testing.assert_array_equal(hr.k[l], h.k[l])
     d = np.linalg.norm(O.expand_dense(h) - O.expand_dense(hr), 2) / res.norm_est
     assert d <= 1e-13
+
+
+def test_certified_after_predicted_starts():
+    """With predicted start counts (the learned-rank path: start q_level[l], first test of q_test
+    columns) the certified basis keeps the start block when that first test passes, so the
+    projection pass uses exactly the predicted count; the construction meets the tolerance."""
+    n, m = 32, 200
+    op = _heat(n, m, 31)
+    H = op.dense()
+    h0, r0 = O.build(op, W.grid_coords(n), 32, ADM_STRONG, 0.7, 1e-6, 32, 16, 16, 256, True, 3)
+    L = h0.tree.L
+    # start each level from what the adaptive finder needed (a perfect prediction)
+    q_level = [0] + [int(r0.need[l]) if r0.passed[l] == 1 else 0 for l in range(1, L + 1)]
+    h1, r1 = O.build(op, W.grid_coords(n), 32, ADM_STRONG, 0.7, 1e-6, 32, 16, 16, 256, True, 3,
+                     norm_est=r0.norm_est, q_level=q_level, q_test=8, certified=True)
+    checked = 0
+    for l in range(1, L + 1):
+        if q_level[l] and r1.passed[l] == 1 and r1.range_calls[l] == 1:   # the first test passed
+            assert r1.proj_probes[l] == q_level[l] == r1.need[l]
+            assert r1.range_probes[l] == q_level[l] + 8
+            checked += 1
+    assert checked > 0
+    e = np.linalg.norm(O.expand_dense(h1) - H, 2) / np.linalg.norm(H, 2)
+    assert e <= 1e-6
+    assert r1.samples < r0.samples
